@@ -1,0 +1,773 @@
+/*
+ * Reference oracle for PLP / PLM / PLMR / EPP community detection
+ * (Staudt & Meyerhenke, "Engineering Parallel Algorithms for Community
+ * Detection in Massive Networks").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, sequential CPU
+ * statement of what the GPU library computes.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may build, load or call it; the
+ * product path never does.  It shares no code with the CUDA library.
+ *
+ * Arithmetic is exact: weights, volumes and sums in int64, every product of
+ * the modularity gain and of the modularity numerator in __int128, and one
+ * final IEEE double division for modularity.
+ *
+ * Readings of the paper that the code fixes (the paper is silent or the
+ * parallel schedule is nondeterministic there):
+ *   - vol(u) sums the weights to neighbours other than u plus twice the
+ *     self-loop (Section III-B, volume definition; read so that sum vol = 2W).
+ *   - Schedule: colour classes of a hash-priority Jones-Plassmann distance-1
+ *     colouring, processed in ascending colour; inside a class every vertex
+ *     decides on the labels and community volumes as they stood when the
+ *     class began, then all decisions of the class are applied.
+ *   - Ties in the argmax of the move rule go to the smallest community id;
+ *     a move needs a strictly positive gain (Algorithm 2).  A move phase
+ *     ends when no vertex wants to move; from its 17th sweep on, a vertex
+ *     that wants to move does so only on a hash coin (see move_phase).
+ *   - PLP adopts the dominant label only if its weight strictly exceeds the
+ *     weight of the current label; ties between dominant labels follow a
+ *     per-iteration pseudo-random order of the labels (fmix32 of the label
+ *     xor a salt drawn from the seed and the iteration number).
+ *   - Every recursive PLM/PLMR call returns a compacted labelling (dense
+ *     ranks in ascending order of raw label); prolongation works in that
+ *     space.
+ *   - EPP base run i colours with seed+i; the combination is the exact
+ *     core-community partition of Eq. (2) (pairwise key compaction), not a
+ *     hash.
+ *   - Caps: 256 sweeps per move phase, 64 levels, 1000 PLP iterations.
+ *   - Modularity of an edgeless graph is 0.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef __int128 i128;
+
+/* ---------------------------------------------------------------------- */
+/* Graph: adjacency without self-loops, self-loop weights kept apart.       */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int64_t n;
+    int64_t *rp;    /* [n+1] row offsets into adj/wt */
+    int32_t *adj;   /* neighbours v != u */
+    int64_t *wt;    /* weight of {u, v} */
+    int64_t *loop;  /* [n] self-loop weight omega(u, u) */
+    int64_t *vol;   /* [n] vol(u) */
+    int64_t W;      /* omega(E): every edge once, self-loops once */
+} OG;
+
+static void og_free(OG *g)
+{
+    free(g->rp); free(g->adj); free(g->wt); free(g->loop); free(g->vol);
+    memset(g, 0, sizeof(*g));
+}
+
+/* vol(u) and omega(E) from their definitions (Section III-B). */
+static void og_volumes(OG *g)
+{
+    int64_t twice = 0;
+    for (int64_t u = 0; u < g->n; u++) {
+        int64_t s = 2 * g->loop[u];
+        for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) s += g->wt[e];
+        g->vol[u] = s;
+        twice += s;
+    }
+    g->W = twice / 2;
+}
+
+/* Input CSR (self-loop stored once in its row) -> OG.  w == NULL: unit. */
+static int og_from_input(OG *g, int64_t n, const int64_t *row_ptr,
+                         const int32_t *col, const int64_t *w)
+{
+    memset(g, 0, sizeof(*g));
+    g->n = n;
+    g->rp = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    g->loop = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    g->vol = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t nnz = row_ptr[n];
+    g->adj = (int32_t *)malloc(((size_t)nnz + 1) * sizeof(int32_t));
+    g->wt = (int64_t *)malloc(((size_t)nnz + 1) * sizeof(int64_t));
+    if (!g->rp || !g->loop || !g->vol || !g->adj || !g->wt) { og_free(g); return -1; }
+    int64_t k = 0;
+    for (int64_t u = 0; u < n; u++) {
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; e++) {
+            int64_t wt = w ? w[e] : 1;
+            if (col[e] == u) g->loop[u] += wt;
+            else { g->adj[k] = col[e]; g->wt[k] = wt; k++; }
+        }
+        g->rp[u + 1] = k;
+    }
+    og_volumes(g);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Modularity, Eq. (1):                                                     */
+/*   mod = sum_C omega(C)/W - vol(C)^2/(4 W^2)                              */
+/* written over the common denominator 4W^2:                                */
+/*   N = 2W * sum_C 2 omega(C) - sum_C vol(C)^2,  D = 4 W^2.                */
+/* ---------------------------------------------------------------------- */
+static void og_mod_num(const OG *g, const int32_t *z, i128 *N, i128 *D)
+{
+    int64_t in2 = 0;  /* sum_C 2 omega(C) */
+    int64_t *volc = (int64_t *)calloc((size_t)g->n + 1, sizeof(int64_t));
+    for (int64_t u = 0; u < g->n; u++) {
+        in2 += 2 * g->loop[u];
+        for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++)
+            if (z[g->adj[e]] == z[u]) in2 += g->wt[e];
+        volc[z[u]] += g->vol[u];
+    }
+    i128 sq = 0;
+    for (int64_t c = 0; c < g->n; c++) sq += (i128)volc[c] * volc[c];
+    free(volc);
+    *N = (i128)(2 * g->W) * in2 - sq;
+    *D = (i128)4 * g->W * g->W;
+}
+
+static double og_modularity(const OG *g, const int32_t *z)
+{
+    if (g->W == 0) return 0.0;
+    i128 N, D;
+    og_mod_num(g, z, &N, &D);
+    return (double)N / (double)D;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Compaction: dense rank of each label in ascending order of raw label.    */
+/* Labels are in [0, n).                                                     */
+/* ---------------------------------------------------------------------- */
+static int64_t dense_rank(int64_t n, const int32_t *z, int32_t *rank_of_label)
+{
+    char *used = (char *)calloc((size_t)n + 1, 1);
+    for (int64_t u = 0; u < n; u++) used[z[u]] = 1;
+    int64_t k = 0;
+    for (int64_t l = 0; l < n; l++) rank_of_label[l] = used[l] ? (int32_t)k++ : -1;
+    free(used);
+    return k;
+}
+
+static int64_t compact(int64_t n, int32_t *z)
+{
+    int32_t *rk = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int64_t k = dense_rank(n, z, rk);
+    for (int64_t u = 0; u < n; u++) z[u] = rk[z[u]];
+    free(rk);
+    return k;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Colouring: first-fit Jones-Plassmann with hash priorities.               */
+/* Priority of v: (fmix32(v ^ fmix32(seed_lo ^ seed_hi)), v), larger wins.  */
+/* fmix32 is the MurmurHash3 32-bit finaliser (Appleby).                    */
+/* ---------------------------------------------------------------------- */
+static uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16; h *= 0x85ebca6bu;
+    h ^= h >> 13; h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+static int prio_greater(const uint32_t *h, int32_t a, int32_t b)
+{
+    return h[a] > h[b] || (h[a] == h[b] && a > b);
+}
+
+static int32_t color_jp(const OG *g, uint64_t seed, int32_t *color)
+{
+    int64_t n = g->n;
+    uint32_t s = fmix32((uint32_t)seed ^ (uint32_t)(seed >> 32));
+    uint32_t *h = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    int32_t *pick = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    char *taken = NULL;
+    int64_t taken_cap = 0;
+    for (int64_t v = 0; v < n; v++) { h[v] = fmix32((uint32_t)v ^ s); color[v] = -1; }
+    int64_t left = n;
+    int32_t ncol = 0;
+    while (left > 0) {
+        /* 1. every uncoloured vertex that beats all uncoloured neighbours */
+        int64_t np = 0;
+        for (int64_t v = 0; v < n; v++) {
+            if (color[v] >= 0) continue;
+            int best = 1;
+            for (int64_t e = g->rp[v]; e < g->rp[v + 1] && best; e++) {
+                int32_t x = g->adj[e];
+                if (color[x] < 0 && prio_greater(h, x, (int32_t)v)) best = 0;
+            }
+            if (best) pick[np++] = (int32_t)v;
+        }
+        /* 2. they are pairwise non-adjacent: give each the smallest colour
+         *    not used by its neighbours coloured in earlier rounds */
+        for (int64_t i = 0; i < np; i++) {
+            int32_t v = pick[i];
+            int64_t deg = g->rp[v + 1] - g->rp[v];
+            if (deg + 1 > taken_cap) {
+                taken_cap = deg + 1;
+                taken = (char *)realloc(taken, (size_t)taken_cap);
+            }
+            memset(taken, 0, (size_t)deg + 1);
+            for (int64_t e = g->rp[v]; e < g->rp[v + 1]; e++) {
+                int32_t c = color[g->adj[e]];
+                if (c >= 0 && c <= deg) taken[c] = 1;
+            }
+            int32_t c = 0;
+            while (taken[c]) c++;
+            color[v] = c;
+            if (c + 1 > ncol) ncol = c + 1;
+        }
+        left -= np;
+    }
+    free(h); free(pick); free(taken);
+    return ncol;
+}
+
+/* Vertices grouped by colour, ascending id inside a class (or descending
+ * when rev != 0: the result must not depend on it). */
+typedef struct { int32_t ncol; int64_t *off; int32_t *v; } Classes;
+
+static void classes_build(const OG *g, uint64_t seed, int rev, Classes *cl)
+{
+    int64_t n = g->n;
+    int32_t *color = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    cl->ncol = n ? color_jp(g, seed, color) : 0;
+    cl->off = (int64_t *)calloc((size_t)cl->ncol + 2, sizeof(int64_t));
+    cl->v = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    for (int64_t u = 0; u < n; u++) cl->off[color[u] + 1]++;
+    for (int32_t c = 0; c < cl->ncol; c++) cl->off[c + 1] += cl->off[c];
+    int64_t *pos = (int64_t *)malloc(((size_t)cl->ncol + 1) * sizeof(int64_t));
+    memcpy(pos, cl->off, (size_t)cl->ncol * sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++) {
+        int64_t u = rev ? n - 1 - i : i;
+        cl->v[pos[color[u]]++] = (int32_t)u;
+    }
+    free(pos); free(color);
+}
+
+static void classes_free(Classes *cl) { free(cl->off); free(cl->v); }
+
+/* ---------------------------------------------------------------------- */
+/* Statistics                                                                */
+/* ---------------------------------------------------------------------- */
+enum {
+    ST_LEVELS = 0, ST_SWEEPS, ST_MOVES, ST_COLORS0, ST_CONVERGED, ST_ENTRIES,
+    ST_CANDIDATES, ST_DECISIONS, ST_ITERS, ST_NCOMM, ST_SWEEPS0, ST_ENTRIES0,
+    ST_CANDIDATES0, ST_N
+};
+
+/* ---------------------------------------------------------------------- */
+/* Local moving, Algorithm 2, under the colour-class schedule.               */
+/* ---------------------------------------------------------------------- */
+typedef struct { int64_t *acc; int32_t *touched; } Scratch;
+
+/* omega(u, c) for every community c adjacent to u (u itself excluded);
+ * returns the number of distinct communities, listed in s->touched. */
+static int64_t gather_weights(const OG *g, const int32_t *z, int64_t u, Scratch *s)
+{
+    int64_t nt = 0;
+    for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
+        int32_t c = z[g->adj[e]];
+        if (s->acc[c] == 0) s->touched[nt++] = c;
+        s->acc[c] += g->wt[e];
+    }
+    return nt;
+}
+
+static void clear_weights(Scratch *s, int64_t nt)
+{
+    for (int64_t i = 0; i < nt; i++) s->acc[s->touched[i]] = 0;
+}
+
+/* Gain of moving u from C = z[u] to D != C, multiplied by 2W^2 > 0
+ * (Section III-B, Delta mod):
+ *   g = 2W (omega(u,D) - omega(u,C\u)) - vol(u) (vol(D) - vol(C\u)).     */
+static i128 gain(int64_t W, int64_t w_uD, int64_t w_uC, int64_t vol_u,
+                 int64_t vol_D, int64_t vol_C)
+{
+    return (i128)(2 * W) * (w_uD - w_uC) - (i128)vol_u * (vol_D - (vol_C - vol_u));
+}
+
+/* Best target community for u, or z[u] if no candidate has positive gain. */
+static int32_t decide_move(const OG *g, const int32_t *z, const int64_t *volc,
+                           int64_t u, Scratch *s, int64_t st[ST_N], int level0)
+{
+    int64_t nt = gather_weights(g, z, u, s);
+    int32_t C = z[u];
+    int64_t w_uC = s->acc[C];
+    int32_t best = C;
+    i128 bestg = 0;
+    int have = 0;
+    for (int64_t i = 0; i < nt; i++) {
+        int32_t D = s->touched[i];
+        if (D == C) continue;
+        i128 gD = gain(g->W, s->acc[D], w_uC, g->vol[u], volc[D], volc[C]);
+        if (!have || gD > bestg || (gD == bestg && D < best)) { best = D; bestg = gD; have = 1; }
+    }
+    st[ST_ENTRIES] += g->rp[u + 1] - g->rp[u];
+    st[ST_CANDIDATES] += nt;
+    st[ST_DECISIONS] += 1;
+    if (level0) {
+        st[ST_ENTRIES0] += g->rp[u + 1] - g->rp[u];
+        st[ST_CANDIDATES0] += nt;
+    }
+    clear_weights(s, nt);
+    return (have && bestg > 0) ? best : C;
+}
+
+/* Sweeps over the colour classes until no vertex wants to move (zeta is
+ * stable, Algorithm 2) or max_sweeps is reached.  Returns the number of
+ * moves made.
+ *
+ * Damping: all vertices of a class decide on the same volume snapshot, so
+ * vertices of one class can keep leaving and re-entering a community
+ * together (a period-2 cycle).  The paper's asynchronous updates avoid such
+ * cycles (Section III-A); here, from sweep DAMP_FROM on, a vertex that wants
+ * to move does so only when a hash coin of (vertex, sweep, seed) is heads.
+ * The phase still ends only when no vertex wants to move. */
+#define DAMP_FROM 16
+
+static uint32_t move_salt(uint64_t seed, int32_t sw)
+{
+    uint32_t s = fmix32((uint32_t)seed ^ (uint32_t)(seed >> 32));
+    return fmix32(s ^ 0x7F4A7C15u ^ (0x9E3779B9u * (uint32_t)(sw + 1)));
+}
+
+static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t seed,
+                          int32_t max_sweeps, int64_t st[ST_N], int level0)
+{
+    int64_t n = g->n;
+    int64_t *volc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int32_t *prop = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    Scratch s;
+    s.acc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    s.touched = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    for (int64_t u = 0; u < n; u++) volc[z[u]] += g->vol[u];
+    int64_t total = 0;
+    int converged = 0;
+    for (int32_t sw = 0; sw < max_sweeps; sw++) {
+        int64_t wanted = 0, moved = 0;
+        uint32_t salt = move_salt(seed, sw);
+        for (int32_t k = 0; k < cl->ncol; k++) {
+            int64_t a = cl->off[k], b = cl->off[k + 1];
+            for (int64_t i = a; i < b; i++) {            /* decide */
+                int32_t u = cl->v[i];
+                prop[u] = decide_move(g, z, volc, u, &s, st, level0);
+            }
+            for (int64_t i = a; i < b; i++) {            /* apply */
+                int32_t u = cl->v[i];
+                if (prop[u] == z[u]) continue;
+                wanted++;
+                if (sw >= DAMP_FROM && (fmix32((uint32_t)u ^ salt) & 1u)) continue;
+                volc[z[u]] -= g->vol[u];
+                volc[prop[u]] += g->vol[u];
+                z[u] = prop[u];
+                moved++;
+            }
+        }
+        st[ST_SWEEPS]++;
+        if (level0) st[ST_SWEEPS0]++;
+        total += moved;
+        if (wanted == 0) { converged = 1; break; }
+    }
+    if (!converged) st[ST_CONVERGED] = 0;
+    st[ST_MOVES] += total;
+    free(volc); free(prop); free(s.acc); free(s.touched);
+    return total;
+}
+
+/* ---------------------------------------------------------------------- */
+/* coarsen (Section III-B): one coarse node per community, inter-community   */
+/* weights summed, intra-community weight kept as the coarse self-loop.      */
+/* pi(u) = dense rank of z[u].                                               */
+/* ---------------------------------------------------------------------- */
+static void coarsen(const OG *g, const int32_t *z, OG *cg, int32_t *pi)
+{
+    int64_t n = g->n;
+    int32_t *rk = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int64_t nc = dense_rank(n, z, rk);
+    for (int64_t u = 0; u < n; u++) pi[u] = rk[z[u]];
+    free(rk);
+    /* members of each coarse node */
+    int64_t *moff = (int64_t *)calloc((size_t)nc + 2, sizeof(int64_t));
+    int32_t *mem = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    for (int64_t u = 0; u < n; u++) moff[pi[u] + 1]++;
+    for (int64_t c = 0; c < nc; c++) moff[c + 1] += moff[c];
+    int64_t *pos = (int64_t *)malloc(((size_t)nc + 1) * sizeof(int64_t));
+    memcpy(pos, moff, (size_t)nc * sizeof(int64_t));
+    for (int64_t u = 0; u < n; u++) mem[pos[pi[u]]++] = (int32_t)u;
+    free(pos);
+
+    memset(cg, 0, sizeof(*cg));
+    cg->n = nc;
+    cg->rp = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    cg->loop = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    cg->vol = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    int64_t cap = g->rp[n] + 1;
+    cg->adj = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    cg->wt = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+    int64_t *acc = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+    int32_t *touched = (int32_t *)malloc(((size_t)nc + 1) * sizeof(int32_t));
+    int64_t k = 0;
+    for (int64_t c = 0; c < nc; c++) {
+        int64_t nt = 0, intra = 0, loops = 0;
+        for (int64_t i = moff[c]; i < moff[c + 1]; i++) {
+            int32_t u = mem[i];
+            loops += g->loop[u];
+            for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
+                int32_t d = pi[g->adj[e]];
+                if (d == c) { intra += g->wt[e]; continue; }
+                if (acc[d] == 0) touched[nt++] = d;
+                acc[d] += g->wt[e];
+            }
+        }
+        /* each intra-community edge was seen from both ends */
+        cg->loop[c] = loops + intra / 2;
+        /* sorted neighbour list of the coarse node (insertion sort: plain) */
+        for (int64_t i = 1; i < nt; i++) {
+            int32_t x = touched[i];
+            int64_t j = i - 1;
+            while (j >= 0 && touched[j] > x) { touched[j + 1] = touched[j]; j--; }
+            touched[j + 1] = x;
+        }
+        for (int64_t i = 0; i < nt; i++) {
+            cg->adj[k] = touched[i];
+            cg->wt[k] = acc[touched[i]];
+            acc[touched[i]] = 0;
+            k++;
+        }
+        cg->rp[c + 1] = k;
+    }
+    free(acc); free(touched); free(moff); free(mem);
+    og_volumes(cg);
+}
+
+/* ---------------------------------------------------------------------- */
+/* PLM (Algorithm 3) and PLMR (Algorithm 4), recursively.                    */
+/* Returns a compacted labelling of g in z (length g->n).                    */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    uint64_t seed; int32_t max_sweeps; int32_t max_levels; int rev;
+} Opts;
+
+static void plm_rec(const OG *g, int refine, const Opts *o, int depth,
+                    int32_t *z, int64_t st[ST_N])
+{
+    int64_t n = g->n;
+    if (depth + 1 > st[ST_LEVELS]) st[ST_LEVELS] = depth + 1;
+    for (int64_t u = 0; u < n; u++) z[u] = (int32_t)u;          /* singletons */
+    Classes cl;
+    classes_build(g, o->seed, o->rev, &cl);
+    if (depth == 0) st[ST_COLORS0] = cl.ncol;
+    int64_t moved = move_phase(g, z, &cl, o->seed, o->max_sweeps, st, depth == 0);
+    if (moved > 0 && depth + 1 < o->max_levels) {               /* zeta changed */
+        OG cg;
+        int32_t *pi = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+        coarsen(g, z, &cg, pi);
+        int32_t *zc = (int32_t *)malloc(((size_t)cg.n + 1) * sizeof(int32_t));
+        plm_rec(&cg, refine, o, depth + 1, zc, st);
+        for (int64_t u = 0; u < n; u++) z[u] = zc[pi[u]];      /* prolong */
+        if (refine) move_phase(g, z, &cl, o->seed, o->max_sweeps, st, depth == 0);
+        free(zc); free(pi);
+        og_free(&cg);
+    }
+    compact(n, z);
+    classes_free(&cl);
+}
+
+/* ---------------------------------------------------------------------- */
+/* PLP (Algorithm 1) under the colour-class schedule.                        */
+/* The paper breaks ties between dominant labels arbitrarily (Section        */
+/* III-A); here the tie goes to the label with the smallest                  */
+/* fmix32(l ^ salt), a pseudo-random order that changes every iteration.     */
+/* fmix32 is a bijection, so two labels never share a key.                   */
+/* ---------------------------------------------------------------------- */
+static uint32_t plp_salt(uint64_t seed, int32_t it)
+{
+    uint32_t s = fmix32((uint32_t)seed ^ (uint32_t)(seed >> 32));
+    return fmix32(s ^ (0x9E3779B9u * (uint32_t)(it + 1)));
+}
+
+static void plp_run(const OG *g, uint64_t seed, double theta, int32_t max_iter,
+                    int use_active, int rev, int32_t *z, int64_t st[ST_N])
+{
+    int64_t n = g->n;
+    Classes cl;
+    classes_build(g, seed, rev, &cl);
+    st[ST_COLORS0] = cl.ncol;
+    char *active = (char *)malloc((size_t)n + 1);
+    char *adopt = (char *)calloc((size_t)n + 1, 1);
+    int32_t *prop = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    Scratch s;
+    s.acc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    s.touched = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    for (int64_t v = 0; v < n; v++) { z[v] = (int32_t)v; active[v] = 1; }
+    int64_t updated = n;
+    int32_t it = 0;
+    while ((double)updated > theta && it < max_iter) {
+        updated = 0;
+        uint32_t salt = plp_salt(seed, it);
+        for (int32_t k = 0; k < cl.ncol; k++) {
+            int64_t a = cl.off[k], b = cl.off[k + 1];
+            for (int64_t i = a; i < b; i++) {
+                int32_t v = cl.v[i];
+                adopt[v] = 0;
+                if (!(use_active ? active[v] : 1)) continue;
+                if (g->rp[v + 1] == g->rp[v]) continue;           /* deg(v) = 0 */
+                int64_t nt = gather_weights(g, z, v, &s);
+                int32_t bestl = -1;
+                int64_t bestw = 0;
+                for (int64_t j = 0; j < nt; j++) {                /* dominant label */
+                    int32_t l = s.touched[j];
+                    if (bestl < 0 || s.acc[l] > bestw ||
+                        (s.acc[l] == bestw && fmix32((uint32_t)l ^ salt) < fmix32((uint32_t)bestl ^ salt))) {
+                        bestl = l; bestw = s.acc[l];
+                    }
+                }
+                int64_t wcur = s.acc[z[v]];
+                st[ST_ENTRIES] += g->rp[v + 1] - g->rp[v];
+                st[ST_CANDIDATES] += nt;
+                st[ST_DECISIONS] += 1;
+                clear_weights(&s, nt);
+                if (bestw > wcur) { adopt[v] = 1; prop[v] = bestl; }
+                else adopt[v] = 2;
+            }
+            for (int64_t i = a; i < b; i++) {
+                int32_t v = cl.v[i];
+                if (adopt[v] == 1) {
+                    z[v] = prop[v];
+                    updated++;
+                    for (int64_t e = g->rp[v]; e < g->rp[v + 1]; e++) active[g->adj[e]] = 1;
+                } else if (adopt[v] == 2) {
+                    active[v] = 0;
+                }
+            }
+        }
+        st[ST_MOVES] += updated;
+        it++;
+    }
+    st[ST_ITERS] = it;
+    st[ST_CONVERGED] = ((double)updated > theta) ? 0 : 1;
+    compact(n, z);
+    classes_free(&cl);
+    free(active); free(adopt); free(prop); free(s.acc); free(s.touched);
+}
+
+/* ---------------------------------------------------------------------- */
+/* combine (Section III-D, Eq. (2)): u and v share a core community iff     */
+/* they share a community in every base solution.  Folded pairwise: the     */
+/* running core id and the next base label form a 64-bit key; keys are      */
+/* replaced by their dense rank.                                            */
+/* ---------------------------------------------------------------------- */
+static int cmp_u64(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+
+static int64_t combine(int64_t n, int b, const int32_t *labels, int32_t *core)
+{
+    for (int64_t v = 0; v < n; v++) core[v] = labels[v];
+    int64_t k = compact(n, core);
+    uint64_t *key = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    uint64_t *srt = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    for (int i = 1; i < b; i++) {
+        const int32_t *zi = labels + (size_t)i * n;
+        for (int64_t v = 0; v < n; v++) key[v] = ((uint64_t)(uint32_t)core[v] << 32) | (uint32_t)zi[v];
+        memcpy(srt, key, (size_t)n * sizeof(uint64_t));
+        qsort(srt, (size_t)n, sizeof(uint64_t), cmp_u64);
+        int64_t nu = 0;
+        for (int64_t j = 0; j < n; j++) if (j == 0 || srt[j] != srt[j - 1]) srt[nu++] = srt[j];
+        for (int64_t v = 0; v < n; v++) {                       /* rank by binary search */
+            int64_t lo = 0, hi = nu - 1;
+            while (lo < hi) { int64_t mid = (lo + hi) / 2; if (srt[mid] < key[v]) lo = mid + 1; else hi = mid; }
+            core[v] = (int32_t)lo;
+        }
+        k = nu;
+    }
+    free(key); free(srt);
+    return k;
+}
+
+/* ====================================================================== */
+/* Exported entry points (called through ctypes by the test suite).        */
+/* Input CSR: row_ptr int64[n+1], col int32[nnz] (symmetric, self-loop once */
+/* in its row), w int64[nnz] or NULL for unit weights.  Labels in [0, n).  */
+/* Return 0 on success, -1 on allocation failure.                          */
+/* ====================================================================== */
+
+static void put128(i128 x, int64_t *out)
+{
+    out[0] = (int64_t)(x >> 64);
+    out[1] = (int64_t)(uint64_t)x;
+}
+
+/* modularity; num_den (optional) receives N and D as (hi, lo) int64 pairs */
+int or_modularity(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+                  const int32_t *labels, double *mod, int64_t *num_den)
+{
+    OG g;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    i128 N = 0, D = 0;
+    if (n > 0) og_mod_num(&g, labels, &N, &D);
+    *mod = og_modularity(&g, labels);
+    if (num_den) { put128(N, num_den); put128(D, num_den + 2); }
+    og_free(&g);
+    return 0;
+}
+
+/* gain numerator g (x 2W^2) of moving u from labels[u] to community D */
+int or_gain(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+            const int32_t *labels, int32_t u, int32_t D, int64_t *g_out)
+{
+    OG g;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    int64_t *volc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int64_t x = 0; x < n; x++) volc[labels[x]] += g.vol[x];
+    int64_t wD = 0, wC = 0;
+    for (int64_t e = g.rp[u]; e < g.rp[u + 1]; e++) {
+        if (labels[g.adj[e]] == D) wD += g.wt[e];
+        if (labels[g.adj[e]] == labels[u]) wC += g.wt[e];
+    }
+    put128(gain(g.W, wD, wC, g.vol[u], volc[D], volc[labels[u]]), g_out);
+    free(volc);
+    og_free(&g);
+    return 0;
+}
+
+int32_t or_color(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+                 uint64_t seed, int32_t *color)
+{
+    OG g;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    int32_t k = n ? color_jp(&g, seed, color) : 0;
+    og_free(&g);
+    return k;
+}
+
+/* one move phase at the input level, starting from labels (in/out) */
+int or_move_phase(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+                  uint64_t seed, int32_t max_sweeps, int rev, int32_t *labels, int64_t *stats)
+{
+    OG g;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    int64_t st[ST_N] = {0};
+    st[ST_CONVERGED] = 1;
+    Classes cl;
+    classes_build(&g, seed, rev, &cl);
+    st[ST_COLORS0] = cl.ncol;
+    move_phase(&g, labels, &cl, seed, max_sweeps, st, 1);
+    classes_free(&cl);
+    og_free(&g);
+    memcpy(stats, st, sizeof(st));
+    return 0;
+}
+
+int or_plm(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+           int refine, uint64_t seed, int32_t max_sweeps, int32_t max_levels, int rev,
+           int32_t *labels, double *mod, int64_t *stats)
+{
+    OG g;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    int64_t st[ST_N] = {0};
+    st[ST_CONVERGED] = 1;
+    Opts o = { seed, max_sweeps, max_levels, rev };
+    if (n > 0) plm_rec(&g, refine, &o, 0, labels, st);
+    *mod = og_modularity(&g, labels);
+    int64_t k = 0;
+    for (int64_t u = 0; u < n; u++) if (labels[u] + 1 > k) k = labels[u] + 1;
+    st[ST_NCOMM] = k;
+    memcpy(stats, st, sizeof(st));
+    og_free(&g);
+    return 0;
+}
+
+int or_plp(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+           uint64_t seed, double theta, int32_t max_iter, int use_active, int rev,
+           int32_t *labels, double *mod, int64_t *stats)
+{
+    OG g;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    int64_t st[ST_N] = {0};
+    if (n > 0) plp_run(&g, seed, theta, max_iter, use_active, rev, labels, st);
+    else st[ST_CONVERGED] = 1;
+    *mod = og_modularity(&g, labels);
+    int64_t k = 0;
+    for (int64_t u = 0; u < n; u++) if (labels[u] + 1 > k) k = labels[u] + 1;
+    st[ST_NCOMM] = k;
+    memcpy(stats, st, sizeof(st));
+    og_free(&g);
+    return 0;
+}
+
+int64_t or_combine(int64_t n, int b, const int32_t *labels, int32_t *core)
+{
+    return combine(n, b, labels, core);
+}
+
+/* Coarse graph of (input graph, labels) in input-CSR form (self-loop once
+ * in its row).  Output buffers: rp_out [n+1], col_out / w_out [nnz + n],
+ * pi_out [n].  Returns the number of coarse nodes. */
+int64_t or_coarsen(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+                   const int32_t *labels, int64_t *rp_out, int32_t *col_out,
+                   int64_t *w_out, int32_t *pi_out)
+{
+    OG g, cg;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    coarsen(&g, labels, &cg, pi_out);
+    int64_t k = 0;
+    rp_out[0] = 0;
+    for (int64_t c = 0; c < cg.n; c++) {
+        int loop_done = 0;
+        for (int64_t e = cg.rp[c]; e <= cg.rp[c + 1]; e++) {
+            int32_t d = e < cg.rp[c + 1] ? cg.adj[e] : INT32_MAX;
+            if (!loop_done && cg.loop[c] > 0 && d > c) {
+                col_out[k] = (int32_t)c; w_out[k] = cg.loop[c]; k++;
+                loop_done = 1;
+            }
+            if (e < cg.rp[c + 1]) { col_out[k] = d; w_out[k] = cg.wt[e]; k++; }
+        }
+        rp_out[c + 1] = k;
+    }
+    int64_t nc = cg.n;
+    og_free(&g); og_free(&cg);
+    return nc;
+}
+
+/* EPP (Algorithm 5): b PLP base runs (seed + i), exact core communities,
+ * coarsen, final PLM or PLMR (final_refine) on the core graph, prolong.
+ * base_out [b*n] and core_out [n] are optional. */
+int or_epp(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+           int b, int final_refine, uint64_t seed, int32_t max_sweeps, int32_t max_levels,
+           double theta, int32_t max_iter, int32_t *labels, int32_t *base_out,
+           int32_t *core_out, double *mod, int64_t *stats)
+{
+    OG g;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    int64_t st[ST_N] = {0};
+    st[ST_CONVERGED] = 1;
+    int32_t *base = (int32_t *)malloc(((size_t)b * n + 1) * sizeof(int32_t));
+    int32_t *core = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    for (int i = 0; i < b; i++) {
+        int64_t sb[ST_N] = {0};
+        plp_run(&g, seed + (uint64_t)i, theta, max_iter, 1, 0, base + (size_t)i * n, sb);
+        st[ST_ITERS] += sb[ST_ITERS];
+    }
+    if (n > 0) combine(n, b, base, core);
+    OG cg;
+    int32_t *pi = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    coarsen(&g, core, &cg, pi);
+    int32_t *zc = (int32_t *)malloc(((size_t)cg.n + 1) * sizeof(int32_t));
+    Opts o = { seed, max_sweeps, max_levels, 0 };
+    if (cg.n > 0) plm_rec(&cg, final_refine, &o, 0, zc, st);
+    for (int64_t u = 0; u < n; u++) labels[u] = zc[pi[u]];          /* prolong */
+    compact(n, labels);
+    *mod = og_modularity(&g, labels);
+    int64_t k = 0;
+    for (int64_t u = 0; u < n; u++) if (labels[u] + 1 > k) k = labels[u] + 1;
+    st[ST_NCOMM] = k;
+    if (base_out) memcpy(base_out, base, (size_t)b * n * sizeof(int32_t));
+    if (core_out) memcpy(core_out, core, (size_t)n * sizeof(int32_t));
+    memcpy(stats, st, sizeof(st));
+    free(base); free(core); free(pi); free(zc);
+    og_free(&cg); og_free(&g);
+    return 0;
+}
