@@ -254,8 +254,9 @@ def _sequential_louvain_complete(n, wmat, order):
             return lab
 
 
-@pytest.mark.parametrize("seed", range(3))
-def test_move_phase_on_complete_graph_is_sequential_louvain(oracle_mod, seed):
+@pytest.mark.parametrize("seed,wmax", [(0, 20), (1, 20), (2, 20), (3, 1), (4, 2), (5, 2)])
+def test_move_phase_on_complete_graph_is_sequential_louvain(oracle_mod, seed, wmax):
+    """wmax 1 or 2 makes equal gains common, pinning the smallest-id tie rule."""
     import torch
     n = 9
     r = synth.rand_u53(seed, 77, torch.arange(n * n)).tolist()
@@ -263,7 +264,7 @@ def test_move_phase_on_complete_graph_is_sequential_louvain(oracle_mod, seed):
     edges, ws = [], []
     for u in range(n):
         for v in range(u + 1, n):
-            wm[u][v] = wm[v][u] = 1 + r[u * n + v] % 20
+            wm[u][v] = wm[v][u] = 1 + r[u * n + v] % wmax
             edges.append((u, v))
             ws.append(wm[u][v])
     g = synth.from_edge_list(n, edges, ws)
