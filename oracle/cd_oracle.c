@@ -304,7 +304,7 @@ static int32_t decide_move(const OG *g, const int32_t *z, const int64_t *volc,
     }
     st[ST_ENTRIES] += g->rp[u + 1] - g->rp[u];
     st[ST_CANDIDATES] += nt;
-    st[ST_DECISIONS] += 1;
+    st[ST_DECISIONS] += (g->rp[u + 1] > g->rp[u]);   /* vertices with neighbours */
     if (level0) {
         st[ST_ENTRIES0] += g->rp[u + 1] - g->rp[u];
         st[ST_CANDIDATES0] += nt;
@@ -770,4 +770,36 @@ int or_epp(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
     free(base); free(core); free(pi); free(zc);
     og_free(&cg); og_free(&g);
     return 0;
+}
+
+/* Number of vertices that have a neighbour community with positive gain
+ * under `labels` (the convergence condition of Algorithm 2); the largest
+ * such gain numerator goes to max_gain as (hi, lo). */
+int64_t or_positive_moves(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+                          const int32_t *labels, int64_t *max_gain)
+{
+    OG g;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    int64_t *volc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    for (int64_t x = 0; x < n; x++) volc[labels[x]] += g.vol[x];
+    Scratch s;
+    s.acc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    s.touched = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int64_t cnt = 0;
+    i128 mx = 0;
+    for (int64_t u = 0; u < n; u++) {
+        int64_t nt = gather_weights(&g, labels, u, &s);
+        int32_t C = labels[u];
+        for (int64_t i = 0; i < nt; i++) {
+            int32_t D = s.touched[i];
+            if (D == C) continue;
+            i128 gD = gain(g.W, s.acc[D], s.acc[C], g.vol[u], volc[D], volc[C]);
+            if (gD > 0) { cnt++; if (gD > mx) mx = gD; break; }
+        }
+        clear_weights(&s, nt);
+    }
+    if (max_gain) put128(mx, max_gain);
+    free(volc); free(s.acc); free(s.touched);
+    og_free(&g);
+    return cnt;
 }

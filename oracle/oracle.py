@@ -65,6 +65,8 @@ def lib():
             L.or_coarsen.restype = i64
             L.or_epp.argtypes = [i64, P, P, P, ctypes.c_int, ctypes.c_int, u64, i32, i32,
                                  dbl, i32, P, P, P, P, P]
+            L.or_positive_moves.argtypes = [i64, P, P, P, P, P]
+            L.or_positive_moves.restype = i64
             _lib = L
     return _lib
 
@@ -214,3 +216,11 @@ def epp(row_ptr, col, w, b=4, final_refine=True, seed=1, theta=None,
     if want_parts:
         return r, base[:b * g.n].reshape(b, g.n), core[:g.n]
     return r
+
+
+def positive_moves(row_ptr, col, w, labels):
+    """Vertices with a positive-gain move under ``labels`` (0 at convergence)."""
+    g = _CSR(row_ptr, col, w)
+    z = _np(labels, np.int32)
+    mg = np.zeros(2, np.int64)
+    return int(lib().or_positive_moves(*g.args(), _ptr(z), _ptr(mg)))

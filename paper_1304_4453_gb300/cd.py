@@ -1,0 +1,297 @@
+"""Python binding of the C ABI in include/cd.h (argument marshalling only).
+
+Functions keep the C names (``cd_graph_create``, ``cd_plp``, ``cd_plm``,
+``cd_epp``, ``cd_modularity``, ...).  Arrays may be torch tensors (CPU or CUDA)
+or numpy arrays; CUDA tensors are passed as device pointers, everything else
+as host pointers.  PyTorch supplies device memory and the CUDA stream; all
+computation happens in libcdgpu.so.  If the library is not built, every call
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_ENOTCONV, CD_EBUSY, CD_ETIMEOUT = range(7)
+CD_MEM_HOST, CD_MEM_DEVICE = 0, 1
+
+
+class CDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS = {0: "CD_OK", 1: "CD_EINVAL", 2: "CD_ENOMEM", 3: "CD_ECUDA", 4: "CD_ENOTCONV",
+           5: "CD_EBUSY", 6: "CD_ETIMEOUT"}
+
+
+class cd_opts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("max_sweeps", ctypes.c_int32),
+                ("max_levels", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("profile", ctypes.c_int32)]
+
+
+class cd_stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("colors0", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("ncomm", ctypes.c_int32),
+                ("sweeps", ctypes.c_int64), ("moves", ctypes.c_int64),
+                ("iters", ctypes.c_int64), ("entries", ctypes.c_int64),
+                ("candidates", ctypes.c_int64), ("decisions", ctypes.c_int64),
+                ("ms_color", ctypes.c_double), ("ms_move", ctypes.c_double),
+                ("ms_coarsen", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("k_launches", ctypes.c_int64), ("k_ms", ctypes.c_double),
+                ("k_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+SYMBOLS = ["cd_opts_default", "cd_status_str", "cd_last_error", "cd_graph_create",
+           "cd_graph_destroy", "cd_graph_info", "cd_modularity", "cd_plp", "cd_plm",
+           "cd_epp", "cd_color", "cd_coarsen", "cd_graph_export", "cd_debug_fail_alloc"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libcdgpu.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library missing: {path} (run paper_1304_4453_gb300.build.build())")
+            L = ctypes.CDLL(path)
+            P, i64, i32, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+            L.cd_status_str.restype = ctypes.c_char_p
+            L.cd_last_error.restype = ctypes.c_char_p
+            L.cd_opts_default.argtypes = [P]
+            L.cd_graph_create.argtypes = [i64, P, P, P, c_int, P, P]
+            L.cd_graph_destroy.argtypes = [P]
+            L.cd_graph_info.argtypes = [P, P, P, P]
+            L.cd_modularity.argtypes = [P, P, c_int, P]
+            L.cd_plp.argtypes = [P, P, ctypes.c_double, P, c_int, P, P]
+            L.cd_plm.argtypes = [P, c_int, P, P, c_int, P, P]
+            L.cd_epp.argtypes = [P, c_int, c_int, P, P, c_int, P, P]
+            L.cd_color.argtypes = [P, ctypes.c_uint64, P, c_int, P]
+            L.cd_coarsen.argtypes = [P, P, c_int, P]
+            L.cd_graph_export.argtypes = [P, P, P, P, c_int, P]
+            L.cd_debug_fail_alloc.argtypes = [c_int]
+            L.cd_debug_fail_alloc.restype = None
+            for name in SYMBOLS:
+                if name not in ("cd_status_str", "cd_last_error", "cd_opts_default", "cd_debug_fail_alloc"):
+                    getattr(L, name).restype = c_int
+            _lib = L
+    return _lib
+
+
+def _check(st: int, allow_notconv: bool = True) -> int:
+    if st == CD_OK or (allow_notconv and st == CD_ENOTCONV):
+        return st
+    raise CDError(st, lib().cd_last_error().decode(errors="replace"))
+
+
+def _arr(x, dtype):
+    """(pointer, mem flag, keepalive) for a tensor / array / None."""
+    if x is None:
+        return None, CD_MEM_HOST, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            tdt = {np.int32: torch.int32, np.int64: torch.int64, np.float64: torch.float64}[dtype]
+            if x.dtype != tdt or not x.is_contiguous():
+                x = x.to(tdt).contiguous()
+            return ctypes.c_void_p(x.data_ptr()), (CD_MEM_DEVICE if x.is_cuda else CD_MEM_HOST), x
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(np.asarray(x), dtype=dtype)
+    return a.ctypes.data_as(ctypes.c_void_p), CD_MEM_HOST, a
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def default_opts(seed: int = 1, max_sweeps: int = 256, max_levels: int = 64,
+                 max_iters: int = 1000, profile: bool = False) -> cd_opts:
+    o = cd_opts()
+    lib().cd_opts_default(ctypes.byref(o))
+    o.seed, o.max_sweeps, o.max_levels, o.max_iters, o.profile = seed, max_sweeps, max_levels, max_iters, int(profile)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+
+def cd_graph_create(row_ptr, col, w=None, stream=None):
+    """Returns an opaque handle (ctypes pointer).  All three arrays must live
+    in the same memory (host or one CUDA device)."""
+    rp, m1, k1 = _arr(row_ptr, np.int64)
+    cp, m2, k2 = _arr(col, np.int32)
+    wp, m3, k3 = _arr(w, np.int32)
+    n = (k1.numel() if hasattr(k1, "numel") else len(k1)) - 1
+    if w is not None and m3 != m1 or m2 != m1:
+        raise CDError(CD_EINVAL, "row_ptr, col and w must live in the same memory")
+    h = ctypes.c_void_p()
+    _check(lib().cd_graph_create(n, rp, cp, wp, m1, _stream(stream), ctypes.byref(h)), False)
+    return h
+
+
+def cd_graph_destroy(h):
+    _check(lib().cd_graph_destroy(h), False)
+
+
+def cd_graph_info(h):
+    n, m, W = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().cd_graph_info(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(W)), False)
+    return n.value, m.value, W.value
+
+
+def cd_modularity(h, labels) -> float:
+    lp, mem, keep = _arr(labels, np.int32)
+    out = ctypes.c_double()
+    _check(lib().cd_modularity(h, lp, mem, ctypes.byref(out)), False)
+    return out.value
+
+
+def _run(fn, h, args, labels_out):
+    lp, mem, keep = _arr(labels_out, np.int32)
+    mod = ctypes.c_double()
+    st = cd_stats()
+    status = fn(h, *args(lp, mem, ctypes.byref(mod), ctypes.byref(st)))
+    _check(status)
+    return mod.value, st.as_dict(), status
+
+
+def cd_plp(h, labels_out, opts=None, theta: float = -1.0):
+    o = opts or default_opts()
+    return _run(lib().cd_plp, h, lambda lp, mem, mp, sp: (ctypes.byref(o), theta, lp, mem, mp, sp), labels_out)
+
+
+def cd_plm(h, labels_out, refine: bool = False, opts=None):
+    o = opts or default_opts()
+    return _run(lib().cd_plm, h, lambda lp, mem, mp, sp: (int(refine), ctypes.byref(o), lp, mem, mp, sp),
+                labels_out)
+
+
+def cd_epp(h, labels_out, ensemble_size: int = 4, final_refine: bool = True, opts=None):
+    o = opts or default_opts()
+    return _run(lib().cd_epp, h,
+                lambda lp, mem, mp, sp: (int(ensemble_size), int(final_refine), ctypes.byref(o), lp, mem, mp, sp),
+                labels_out)
+
+
+def cd_color(h, colors_out, seed: int = 1) -> int:
+    cp, mem, keep = _arr(colors_out, np.int32)
+    k = ctypes.c_int32()
+    _check(lib().cd_color(h, seed, cp, mem, ctypes.byref(k)), False)
+    return k.value
+
+
+def cd_coarsen(h, labels):
+    lp, mem, keep = _arr(labels, np.int32)
+    out = ctypes.c_void_p()
+    _check(lib().cd_coarsen(h, lp, mem, ctypes.byref(out)), False)
+    return out
+
+
+def cd_graph_export(h):
+    """(row_ptr int64, col int32, w int64) numpy arrays in input form."""
+    n, _, _ = cd_graph_info(h)
+    nnz = ctypes.c_int64()
+    _check(lib().cd_graph_export(h, None, None, None, CD_MEM_HOST, ctypes.byref(nnz)), False)
+    rp = np.zeros(n + 1, np.int64)
+    col = np.zeros(max(nnz.value, 1), np.int32)
+    w = np.zeros(max(nnz.value, 1), np.int64)
+    _check(lib().cd_graph_export(h, rp.ctypes.data_as(ctypes.c_void_p), col.ctypes.data_as(ctypes.c_void_p),
+                                 w.ctypes.data_as(ctypes.c_void_p), CD_MEM_HOST, ctypes.byref(nnz)), False)
+    return rp, col[:nnz.value], w[:nnz.value]
+
+
+def cd_debug_fail_alloc(k: int):
+    lib().cd_debug_fail_alloc(int(k))
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Result:
+    labels: object
+    modularity: float
+    stats: dict
+    status: int
+
+
+class Graph:
+    """Owns a cd_graph handle.  Results come back as torch tensors on the
+    device of ``device`` (default cuda:0)."""
+
+    def __init__(self, row_ptr, col, w=None, stream=None):
+        self.h = cd_graph_create(row_ptr, col, w, stream)
+        self.n, self.m, self.W = cd_graph_info(self.h)
+
+    @classmethod
+    def from_synth(cls, g, device=None, stream=None):
+        if device is not None:
+            g = g.to(device)
+        return cls(g.row_ptr, g.col, g.w, stream)
+
+    def close(self):
+        if self.h is not None:
+            cd_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, out):
+        if out is not None:
+            return out
+        import torch
+        return torch.empty(max(self.n, 1), dtype=torch.int32, device="cuda")[:self.n]
+
+    def plm(self, refine=False, out=None, **kw) -> Result:
+        out = self._out(out)
+        mod, st, status = cd_plm(self.h, out, refine, default_opts(**kw))
+        return Result(out, mod, st, status)
+
+    def plp(self, out=None, theta=-1.0, **kw) -> Result:
+        out = self._out(out)
+        mod, st, status = cd_plp(self.h, out, default_opts(**kw), theta)
+        return Result(out, mod, st, status)
+
+    def epp(self, b=4, final_refine=True, out=None, **kw) -> Result:
+        out = self._out(out)
+        mod, st, status = cd_epp(self.h, out, b, final_refine, default_opts(**kw))
+        return Result(out, mod, st, status)
+
+    def modularity(self, labels) -> float:
+        return cd_modularity(self.h, labels)

@@ -1,0 +1,290 @@
+// C ABI (include/cd.h): argument checks, host/device staging of caller
+// buffers, error translation.  All computation happens in the engine.
+#include <new>
+
+#include "common.cuh"
+#include "engine.cuh"
+#include "graph.cuh"
+
+namespace cd {
+const std::string &last_error();
+}
+
+using namespace cd;
+
+namespace {
+
+template <typename F>
+cd_status guarded(F &&f) {
+    try {
+        cd_status s = f();
+        if (s == CD_OK) set_last_error("");
+        return s;
+    } catch (const Error &e) {
+        set_last_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return CD_ENOMEM;
+    } catch (...) {
+        set_last_error("unexpected internal error");
+        return CD_ECUDA;
+    }
+}
+
+RunOpts to_run(const cd_opts *o) {
+    cd_opts d;
+    cd_opts_default(&d);
+    if (!o) o = &d;
+    if (o->max_sweeps < 1 || o->max_levels < 1 || o->max_iters < 0)
+        raise(CD_EINVAL, "max_sweeps and max_levels must be >= 1, max_iters >= 0");
+    RunOpts r;
+    r.seed = o->seed;
+    r.max_sweeps = o->max_sweeps;
+    r.max_levels = o->max_levels;
+    r.max_iters = o->max_iters;
+    r.profile = o->profile != 0;
+    return r;
+}
+
+void to_stats(const RunStats &r, cd_stats *st) {
+    if (!st) return;
+    st->levels = r.levels;
+    st->colors0 = r.colors0 < 0 ? 0 : r.colors0;
+    st->converged = r.converged;
+    st->ncomm = r.ncomm;
+    st->sweeps = r.sweeps;
+    st->moves = r.moves;
+    st->iters = r.iters;
+    st->entries = r.entries;
+    st->candidates = r.candidates;
+    st->decisions = r.decisions;
+    st->ms_color = r.ms_color;
+    st->ms_move = r.ms_move;
+    st->ms_coarsen = r.ms_coarsen;
+    st->ms_total = r.ms_total;
+    st->k_launches = r.k_launches;
+    st->k_ms = r.k_ms;
+    st->k_bytes = r.k_bytes;
+}
+
+void check_mem(int mem) {
+    if (mem != CD_MEM_HOST && mem != CD_MEM_DEVICE) raise(CD_EINVAL, "unknown memory flag %d", mem);
+}
+
+// Device view of caller labels (copied in when they live on the host).
+struct LabelsIn {
+    DBuf<int32_t> tmp;
+    const int32_t *p = nullptr;
+    LabelsIn(const int32_t *labels, int mem, int64_t n, cudaStream_t s) {
+        check_mem(mem);
+        if (n > 0 && !labels) raise(CD_EINVAL, "labels is NULL");
+        if (mem == CD_MEM_DEVICE) { p = labels; return; }
+        tmp.alloc(n, s);
+        if (n) CD_CUDA(cudaMemcpyAsync(tmp.p, labels, n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        p = tmp.p;
+    }
+};
+
+// Device buffer for results, copied out to host memory when needed.
+struct LabelsOut {
+    DBuf<int32_t> tmp;
+    int32_t *dst, *p;
+    int mem;
+    int64_t n;
+    cudaStream_t s;
+    LabelsOut(int32_t *labels, int mem_, int64_t n_, cudaStream_t s_) : dst(labels), mem(mem_), n(n_), s(s_) {
+        check_mem(mem);
+        if (n > 0 && !labels) raise(CD_EINVAL, "labels is NULL");
+        if (mem == CD_MEM_DEVICE) { p = labels; return; }
+        tmp.alloc(n, s);
+        p = tmp.p;
+    }
+    void finish() {
+        if (mem == CD_MEM_HOST && n)
+            CD_CUDA(cudaMemcpyAsync(dst, p, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CD_CUDA(cudaStreamSynchronize(s));
+    }
+};
+
+cd_status finish_run(const RunStats &r, cd_stats *st) {
+    to_stats(r, st);
+    return r.converged ? CD_OK : CD_ENOTCONV;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cd_opts_default(cd_opts *o) {
+    if (!o) return;
+    o->seed = 1;
+    o->max_sweeps = 256;
+    o->max_levels = 64;
+    o->max_iters = 1000;
+    o->profile = 0;
+}
+
+const char *cd_status_str(cd_status s) {
+    switch (s) {
+        case CD_OK: return "CD_OK";
+        case CD_EINVAL: return "CD_EINVAL";
+        case CD_ENOMEM: return "CD_ENOMEM";
+        case CD_ECUDA: return "CD_ECUDA";
+        case CD_ENOTCONV: return "CD_ENOTCONV";
+        case CD_EBUSY: return "CD_EBUSY";
+        case CD_ETIMEOUT: return "CD_ETIMEOUT";
+    }
+    return "CD_UNKNOWN";
+}
+
+const char *cd_last_error(void) { return cd::last_error().c_str(); }
+
+cd_status cd_graph_create(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *w, int mem_flags,
+                          void *stream, cd_graph **out) {
+    if (!out) return CD_EINVAL;
+    *out = nullptr;
+    return guarded([&]() {
+        auto *g = new cd_graph();
+        g->stream = static_cast<cudaStream_t>(stream);
+        try {
+            build_graph(n, row_ptr, col, w, mem_flags, g->stream, g->g);
+        } catch (...) {
+            cudaStream_t st = g->stream;
+            delete g;
+            cudaStreamSynchronize(st);
+            throw;
+        }
+        g->m = g->g.view.nnz / 2;
+        *out = g;
+        return CD_OK;
+    });
+}
+
+cd_status cd_graph_destroy(cd_graph *g) {
+    if (!g) return CD_OK;
+    return guarded([&]() {
+        cudaStream_t s = g->stream;
+        delete g;
+        CD_CUDA(cudaStreamSynchronize(s));
+        return CD_OK;
+    });
+}
+
+cd_status cd_graph_info(const cd_graph *g, int64_t *n, int64_t *m, int64_t *total_weight) {
+    if (!g) return CD_EINVAL;
+    if (n) *n = g->g.view.n;
+    if (m) *m = g->m;
+    if (total_weight) *total_weight = g->g.view.W;
+    return CD_OK;
+}
+
+cd_status cd_modularity(cd_graph *g, const int32_t *labels, int labels_mem, double *mod) {
+    if (!g || !mod) return CD_EINVAL;
+    return guarded([&]() {
+        const GraphView &v = g->g.view;
+        LabelsIn in(labels, labels_mem, v.n, g->stream);
+        if (!labels_in_range(in.p, v.n, g->stream)) raise(CD_EINVAL, "label out of range [0, n)");
+        *mod = modularity(v, in.p, g->stream);
+        return CD_OK;
+    });
+}
+
+cd_status cd_plp(cd_graph *g, const cd_opts *o, double theta, int32_t *labels, int labels_mem, double *mod,
+                 cd_stats *st) {
+    if (!g) return CD_EINVAL;
+    return guarded([&]() {
+        const GraphView &v = g->g.view;
+        RunOpts ro = to_run(o);
+        if (theta < 0) theta = (double)v.n * 1e-5;
+        LabelsOut out(labels, labels_mem, v.n, g->stream);
+        RunStats r;
+        run_plp(v, ro, theta, out.p, r, g->stream);
+        if (mod) *mod = modularity(v, out.p, g->stream);
+        out.finish();
+        return finish_run(r, st);
+    });
+}
+
+cd_status cd_plm(cd_graph *g, int refine, const cd_opts *o, int32_t *labels, int labels_mem, double *mod,
+                 cd_stats *st) {
+    if (!g) return CD_EINVAL;
+    return guarded([&]() {
+        const GraphView &v = g->g.view;
+        if (refine != 0 && refine != 1) raise(CD_EINVAL, "refine must be 0 or 1");
+        RunOpts ro = to_run(o);
+        LabelsOut out(labels, labels_mem, v.n, g->stream);
+        RunStats r;
+        run_plm(v, refine == 1, ro, out.p, r, g->stream);
+        if (mod) *mod = modularity(v, out.p, g->stream);
+        out.finish();
+        return finish_run(r, st);
+    });
+}
+
+cd_status cd_epp(cd_graph *g, int ensemble_size, int final_refine, const cd_opts *o, int32_t *labels,
+                 int labels_mem, double *mod, cd_stats *st) {
+    if (!g) return CD_EINVAL;
+    return guarded([&]() {
+        const GraphView &v = g->g.view;
+        if (ensemble_size < 1) raise(CD_EINVAL, "ensemble_size must be >= 1");
+        if (final_refine != 0 && final_refine != 1) raise(CD_EINVAL, "final_refine must be 0 or 1");
+        RunOpts ro = to_run(o);
+        LabelsOut out(labels, labels_mem, v.n, g->stream);
+        RunStats r;
+        run_epp(v, ensemble_size, final_refine == 1, ro, (double)v.n * 1e-5, out.p, r, g->stream);
+        if (mod) *mod = modularity(v, out.p, g->stream);
+        out.finish();
+        return finish_run(r, st);
+    });
+}
+
+cd_status cd_color(cd_graph *g, uint64_t seed, int32_t *colors, int colors_mem, int32_t *ncolors) {
+    if (!g) return CD_EINVAL;
+    return guarded([&]() {
+        const GraphView &v = g->g.view;
+        LabelsOut out(colors, colors_mem, v.n, g->stream);
+        int32_t k = color_graph(v, seed, out.p, g->stream);
+        out.finish();
+        if (ncolors) *ncolors = k;
+        return CD_OK;
+    });
+}
+
+cd_status cd_coarsen(cd_graph *g, const int32_t *labels, int labels_mem, cd_graph **coarse) {
+    if (!g || !coarse) return CD_EINVAL;
+    *coarse = nullptr;
+    return guarded([&]() {
+        const GraphView &v = g->g.view;
+        LabelsIn in(labels, labels_mem, v.n, g->stream);
+        if (!labels_in_range(in.p, v.n, g->stream)) raise(CD_EINVAL, "label out of range [0, n)");
+        auto *c = new cd_graph();
+        c->stream = g->stream;
+        try {
+            DBuf<int64_t> rank(v.n, g->stream);
+            coarsen_graph(v, in.p, rank.p, c->g, g->stream);
+            CD_CUDA(cudaStreamSynchronize(g->stream));
+        } catch (...) {
+            delete c;
+            throw;
+        }
+        c->m = c->g.view.nnz / 2;
+        *coarse = c;
+        return CD_OK;
+    });
+}
+
+cd_status cd_graph_export(const cd_graph *g, int64_t *row_ptr, int32_t *col, int64_t *w, int mem,
+                          int64_t *nnz_out) {
+    if (!g) return CD_EINVAL;
+    return guarded([&]() {
+        check_mem(mem);
+        int64_t nnz = export_graph(g->g.view, row_ptr, col, w, mem, g->stream);
+        if (nnz_out) *nnz_out = nnz;
+        return CD_OK;
+    });
+}
+
+void cd_debug_fail_alloc(int k) { set_alloc_failure(k); }
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Runtime support: error reporting, the device memory pool, pinned staging.
+#include <atomic>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace cd {
+
+static thread_local std::string t_last_error;
+
+void set_last_error(const std::string &m) { t_last_error = m; }
+const std::string &last_error() { return t_last_error; }
+
+[[noreturn]] void raise(cd_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    throw Error{s, std::string(buf)};
+}
+
+// One pool per device, created on first use.  Its release threshold is the
+// maximum, so memory freed at the end of a run stays reserved for the next.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+static std::atomic<int> g_fail_countdown{0};
+
+void set_alloc_failure(int k) { g_fail_countdown.store(k > 0 ? k : 0); }
+
+static cudaMemPool_t pool_for_current_device() {
+    int dev = 0;
+    CD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) raise(CD_ECUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        CD_CUDA(cudaMemPoolCreate(&p, &props));
+        uint64_t thr = ~0ull;
+        CD_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr));
+        g_pools[dev] = p;
+    }
+    return g_pools[dev];
+}
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+    int k = g_fail_countdown.load();
+    if (k > 0) {
+        if (g_fail_countdown.fetch_sub(1) == 1)
+            raise(CD_ENOMEM, "injected allocation failure (%zu bytes)", bytes);
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool_for_current_device(), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        raise(e == cudaErrorMemoryAllocation ? CD_ENOMEM : CD_ECUDA,
+              "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return p;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);  // never throws (destructors)
+}
+
+Pinned::Pinned(size_t bytes) {
+    CD_CUDA(cudaHostAlloc(&p, bytes ? bytes : 8, cudaHostAllocDefault));
+}
+Pinned::~Pinned() {
+    if (p) cudaFreeHost(p);
+}
+
+}  // namespace cd
