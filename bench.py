@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""PLM throughput benchmark on one GB300 (replicas on N GPUs).
+
+Workload: R-MAT scale 22, edge factor 16, (a, b, c, d) = (0.57, 0.19, 0.19,
+0.05), seeded vertex permutation, symmetrised, de-duplicated, loops dropped,
+unit weights (seed 1).  A step is one complete cd_plm call (colouring, every
+Louvain level, coarsening, prolongation, compaction, modularity) on the
+device-resident graph; edges/s = undirected input edges / step time.
+
+Prints one JSON line.  ``--impl reference`` times the sequential CPU oracle
+instead (a bounded sample of the workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PLM edges/s (R-MAT scale 22 ef16, complete run incl. all levels)"
+UNIT = "edges/s"
+SCALE = 22
+EDGE_FACTOR = 16
+ABC = (0.57, 0.19, 0.19)
+SAMPLE_SCALE = 17          # oracle sample: same generator, 2^17 vertices
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--scale", type=int, default=SCALE)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-run", action="store_true",
+                   help="timed steps only (no e2e, PLP or CPU baseline): for ncu captures")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload_config(g, scale):
+    return {
+        "workload": f"rmat{scale}_ef{EDGE_FACTOR}_plm",
+        "graph": f"R-MAT scale {scale}, edge factor {EDGE_FACTOR}, abcd=(0.57,0.19,0.19,0.05), "
+                 "seeded vertex permutation, symmetrised, deduplicated, loops dropped, unit weights, seed 1",
+        "n": g.n if g is not None else None,
+        "m": g.m if g is not None else None,
+        "algorithm": "PLM (Algorithms 2-3), colour-class schedule, seed 1",
+        "l2": "inputs larger than L2 (adjacency alone 4*nnz bytes > 129 MB); no flush",
+        "parallelism": "replicas",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+     "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+     "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate():
+    from oracle import oracle
+    from paper_1304_4453_gb300 import synth
+    oracle.build()
+    g = synth.rmat(SAMPLE_SCALE, EDGE_FACTOR, *ABC, seed=1)
+    rp, c, w = g.numpy()
+    t = time.perf_counter()
+    r = oracle.plm(rp, c, w, seed=1)
+    dt = time.perf_counter() - t
+    return g.m / dt, dt, g, r
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if "Model name" in line:
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline_obj():
+    rate, dt, g, r = oracle_sample_rate()
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one complete sequential oracle PLM run on R-MAT scale {SAMPLE_SCALE} ef{EDGE_FACTOR} "
+                      f"(same generator and parameters; n={g.n}, m={g.m}; {dt:.1f} s, modularity {r.modularity:.4f})",
+            "cpu": cpu_model(), "nproc": os.cpu_count()}
+
+
+# ---------------------------------------------------------------------------
+# reference arm
+# ---------------------------------------------------------------------------
+
+def run_reference(a):
+    rank, local, world = dist_env()
+    if rank != 0:
+        return
+    times = []
+    rate = None
+    for i in range(a.warmup + a.steps):
+        rate, dt, g, r = oracle_sample_rate()
+        if i >= a.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = g.m * len(times) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": workload_config(None, a.scale),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one complete sequential oracle PLM run on R-MAT scale "
+                                   f"{SAMPLE_SCALE} ef{EDGE_FACTOR} (n={g.n}, m={g.m})",
+                         "cpu": cpu_model(), "nproc": os.cpu_count()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def traffic_from_profiles():
+    """Per-launch DRAM bytes of the decide kernels from the committed ncu
+    summary (a line 'traffic_bytes_per_launch: X'), else None."""
+    path = os.path.join(ROOT, "profiles", "plm_decide_rmat22.md")
+    try:
+        for line in open(path):
+            if line.strip().startswith("traffic_bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                return None if v in ("", "null", "None") else float(v)
+    except OSError:
+        pass
+    return None
+
+
+def measured_hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_ours(a):
+    import torch
+    from paper_1304_4453_gb300 import build, cd, synth
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+    cd.lib()
+
+    g = synth.rmat(a.scale, EDGE_FACTOR, *ABC, seed=1, device=dev)
+    torch.cuda.synchronize()
+    G = cd.Graph(g.row_ptr, g.col, g.w)
+    labels = torch.empty(g.n, dtype=torch.int32, device=dev)
+    opts_plain = cd.default_opts(seed=1)
+    opts_prof = cd.default_opts(seed=1, profile=True)
+
+    for _ in range(a.warmup):
+        mod, st, status = cd.cd_plm(G.h, labels, False, opts_plain)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = cd.cd_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    k_ms = k_bytes = 0.0
+    k_launches = 0
+    stats = []
+    for _ in range(a.steps):
+        mod, st, status = cd.cd_plm(G.h, labels, False, opts_prof)
+        k_ms += st["k_ms"]
+        k_bytes += st["k_bytes"]
+        k_launches += st["k_launches"]
+        stats.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = cd.cd_launch_count() - l0
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t)
+    value = g.m * world / (ms_max / 1000.0)
+
+    if a.profile_run:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": ms, "modularity": mod,
+                              "gpu_launches": launches, "k_ms": k_ms, "k_bytes": k_bytes,
+                              "k_launches": k_launches}), flush=True)
+        return
+
+    # end to end through the public API with host buffers: H2D of the CSR,
+    # graph creation, PLM, D2H of the labels, every step
+    rp_h = g.row_ptr.cpu().pin_memory()
+    col_h = g.col.cpu().pin_memory()
+    lab_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    e2e_t = []
+    for i in range(max(1, min(a.steps, 3)) + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        h = cd.cd_graph_create(rp_h, col_h, None)
+        cd.cd_plm(h, lab_h, False, opts_plain)
+        cd.cd_graph_destroy(h)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_t.append(time.perf_counter() - t)
+    e2e_ok = bool(torch.equal(lab_h, labels.cpu()))
+    e2e_value = g.m * world / statistics.median(e2e_t)
+
+    # one PLP run on the same graph (context, outside the timed region)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    plp_mod, plp_st, _ = cd.cd_plp(G.h, torch.empty_like(labels), cd.default_opts(seed=1))
+    torch.cuda.synchronize()
+    plp_s = time.perf_counter() - t
+
+    peak, peak_kind = measured_hbm_peak()
+    achieved = (k_bytes / 1e9) / (k_ms / 1e3) if k_ms > 0 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic_from_profiles(),
+            "kernel": "local-move decide kernels (k_decide_group/block, k_hub_*)",
+            "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                         if peak_kind == "measured" else "fallback 6.8 TB/s",
+            "launches_timed": k_launches, "avg_launch_us": 1000.0 * k_ms / max(k_launches, 1),
+            "alg_bytes_per_launch": k_bytes / max(k_launches, 1),
+            "share_of_step": k_ms / (ms * a.steps) if ms > 0 else None}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline_obj()
+    st = stats[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": workload_config(g, a.scale),
+        "modularity": mod,
+        "plm": {"levels": st["levels"], "colors0": st["colors0"], "sweeps": st["sweeps"],
+                "communities": st["ncomm"], "ms_color": st["ms_color"], "ms_move": st["ms_move"],
+                "ms_coarsen": st["ms_coarsen"], "converged": st["converged"]},
+        "plp": {"edges_per_s": g.m / plp_s, "modularity": plp_mod, "iters": plp_st["iters"],
+                "communities": plp_st["ncomm"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz,
+                "d2h_bytes_per_step": 4 * g.n, "labels_match_device_run": e2e_ok},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "paper_context": "paper: PLM > 21M edges/s, PLP > 53M edges/s on 2x8-core Xeon E5-2680 "
+                         "(uk-2007-05, 3.3B edges); context only",
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -164,6 +164,10 @@ cd_status cd_coarsen(cd_graph *g, const int32_t *labels, int labels_mem, cd_grap
 cd_status cd_graph_export(const cd_graph *g, int64_t *row_ptr, int32_t *col, int64_t *w,
                           int mem, int64_t *nnz_out);
 
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all threads, all devices). */
+uint64_t cd_launch_count(void);
+
 /* Testing hook: the k-th device allocation from now fails with CD_ENOMEM
  * (k <= 0 disables).  Used to check that failures leak nothing. */
 void cd_debug_fail_alloc(int k);

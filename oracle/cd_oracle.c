@@ -22,8 +22,9 @@
  *     class began, then all decisions of the class are applied.
  *   - Ties in the argmax of the move rule go to the smallest community id;
  *     a move needs a strictly positive gain (Algorithm 2).  A move phase
- *     ends when no vertex wants to move; from its 17th sweep on, a vertex
- *     that wants to move does so only on a hash coin (see move_phase).
+ *     ends when no vertex wants to move; from its 5th sweep on, the wanted
+ *     moves of a class are re-checked one by one in vertex order against
+ *     the volumes already updated (see move_phase).
  *   - PLP adopts the dominant label only if its weight strictly exceeds the
  *     weight of the current label; ties between dominant labels follow a
  *     per-iteration pseudo-random order of the labels (fmix32 of the label
@@ -157,8 +158,9 @@ static int64_t compact(int64_t n, int32_t *z)
 
 /* ---------------------------------------------------------------------- */
 /* Colouring: first-fit Jones-Plassmann with hash priorities.               */
-/* Priority of v: (fmix32(v ^ fmix32(seed_lo ^ seed_hi)), v), larger wins.  */
-/* fmix32 is the MurmurHash3 32-bit finaliser (Appleby).                    */
+/* Priority of v: (fmix32(v ^ fmix32(seed_lo ^ seed_hi)), v), compared      */
+/* lexicographically, larger wins.  fmix32 is the MurmurHash3 32-bit        */
+/* finaliser (Appleby).                                                     */
 /* ---------------------------------------------------------------------- */
 static uint32_t fmix32(uint32_t h)
 {
@@ -287,8 +289,15 @@ static i128 gain(int64_t W, int64_t w_uD, int64_t w_uC, int64_t vol_u,
 }
 
 /* Best target community for u, or z[u] if no candidate has positive gain. */
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
 static int32_t decide_move(const OG *g, const int32_t *z, const int64_t *volc,
-                           int64_t u, Scratch *s, int64_t st[ST_N], int level0)
+                           int64_t u, Scratch *s, int64_t st[ST_N], int level0,
+                           int64_t *out_wD, int64_t *out_wC)
 {
     int64_t nt = gather_weights(g, z, u, s);
     int32_t C = z[u];
@@ -309,6 +318,8 @@ static int32_t decide_move(const OG *g, const int32_t *z, const int64_t *volc,
         st[ST_ENTRIES0] += g->rp[u + 1] - g->rp[u];
         st[ST_CANDIDATES0] += nt;
     }
+    *out_wD = have ? s->acc[best] : 0;    /* omega(u, D) of the chosen target */
+    *out_wC = w_uC;                       /* omega(u, C \ u) */
     clear_weights(s, nt);
     return (have && bestg > 0) ? best : C;
 }
@@ -317,26 +328,30 @@ static int32_t decide_move(const OG *g, const int32_t *z, const int64_t *volc,
  * stable, Algorithm 2) or max_sweeps is reached.  Returns the number of
  * moves made.
  *
- * Damping: all vertices of a class decide on the same volume snapshot, so
- * vertices of one class can keep leaving and re-entering a community
- * together (a period-2 cycle).  The paper's asynchronous updates avoid such
- * cycles (Section III-A); here, from sweep DAMP_FROM on, a vertex that wants
- * to move does so only when a hash coin of (vertex, sweep, seed) is heads.
- * The phase still ends only when no vertex wants to move. */
-#define DAMP_FROM 16
-
-static uint32_t move_salt(uint64_t seed, int32_t sw)
-{
-    uint32_t s = fmix32((uint32_t)seed ^ (uint32_t)(seed >> 32));
-    return fmix32(s ^ 0x7F4A7C15u ^ (0x9E3779B9u * (uint32_t)(sw + 1)));
-}
+ * All vertices of a class decide on the volume snapshot taken when the class
+ * begins.  In the first RECHECK_FROM sweeps every wanted move of the class is
+ * applied.  Simultaneous moves into (or out of) one community can overshoot,
+ * since each assumed the others stay put, and on some graphs that churn does
+ * not die out.  From sweep RECHECK_FROM on, the wanted moves of a class are
+ * applied one at a time in ascending vertex id, each only if its gain,
+ * recomputed with the volumes as updated by the moves applied before it, is
+ * still positive (its target stays the one it chose).  Inside an independent
+ * set only the volume terms of the gain interact, so each applied move then
+ * raises modularity by its recomputed gain and the phase must terminate.
+ * The paper lets concurrent threads work on stale data and reports that
+ * termination was never a problem in practice (Section III-B). */
+#define RECHECK_FROM 4
 
 static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t seed,
                           int32_t max_sweeps, int64_t st[ST_N], int level0)
 {
+    (void)seed;
     int64_t n = g->n;
     int64_t *volc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     int32_t *prop = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int64_t *wprop = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    int64_t *wcur = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    int32_t *byid = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
     Scratch s;
     s.acc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     s.touched = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
@@ -345,22 +360,36 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
     int converged = 0;
     for (int32_t sw = 0; sw < max_sweeps; sw++) {
         int64_t wanted = 0, moved = 0;
-        uint32_t salt = move_salt(seed, sw);
         for (int32_t k = 0; k < cl->ncol; k++) {
             int64_t a = cl->off[k], b = cl->off[k + 1];
             for (int64_t i = a; i < b; i++) {            /* decide */
                 int32_t u = cl->v[i];
-                prop[u] = decide_move(g, z, volc, u, &s, st, level0);
+                prop[u] = decide_move(g, z, volc, u, &s, st, level0, &wprop[u], &wcur[u]);
             }
-            for (int64_t i = a; i < b; i++) {            /* apply */
-                int32_t u = cl->v[i];
-                if (prop[u] == z[u]) continue;
-                wanted++;
-                if (sw >= DAMP_FROM && (fmix32((uint32_t)u ^ salt) & 1u)) continue;
-                volc[z[u]] -= g->vol[u];
-                volc[prop[u]] += g->vol[u];
-                z[u] = prop[u];
-                moved++;
+            if (sw < RECHECK_FROM) {
+                for (int64_t i = a; i < b; i++) {        /* apply all */
+                    int32_t u = cl->v[i];
+                    if (prop[u] == z[u]) continue;
+                    wanted++;
+                    volc[z[u]] -= g->vol[u];
+                    volc[prop[u]] += g->vol[u];
+                    z[u] = prop[u];
+                    moved++;
+                }
+            } else {
+                int64_t nc = 0;                          /* wanted moves by id */
+                for (int64_t i = a; i < b; i++)
+                    if (prop[cl->v[i]] != z[cl->v[i]]) byid[nc++] = cl->v[i];
+                qsort(byid, (size_t)nc, sizeof(int32_t), cmp_i32);
+                wanted += nc;
+                for (int64_t j = 0; j < nc; j++) {
+                    int32_t u = byid[j], C = z[u], D = prop[u];
+                    if (gain(g->W, wprop[u], wcur[u], g->vol[u], volc[D], volc[C]) <= 0) continue;
+                    volc[C] -= g->vol[u];
+                    volc[D] += g->vol[u];
+                    z[u] = D;
+                    moved++;
+                }
             }
         }
         st[ST_SWEEPS]++;
@@ -370,6 +399,7 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
     }
     if (!converged) st[ST_CONVERGED] = 0;
     st[ST_MOVES] += total;
+    free(wprop); free(wcur); free(byid);
     free(volc); free(prop); free(s.acc); free(s.touched);
     return total;
 }

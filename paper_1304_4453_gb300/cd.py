@@ -58,7 +58,8 @@ _lib = None
 
 SYMBOLS = ["cd_opts_default", "cd_status_str", "cd_last_error", "cd_graph_create",
            "cd_graph_destroy", "cd_graph_info", "cd_modularity", "cd_plp", "cd_plm",
-           "cd_epp", "cd_color", "cd_coarsen", "cd_graph_export", "cd_debug_fail_alloc"]
+           "cd_epp", "cd_color", "cd_coarsen", "cd_graph_export", "cd_debug_fail_alloc",
+           "cd_launch_count"]
 
 
 def library_path() -> str:
@@ -90,8 +91,11 @@ def lib():
             L.cd_graph_export.argtypes = [P, P, P, P, c_int, P]
             L.cd_debug_fail_alloc.argtypes = [c_int]
             L.cd_debug_fail_alloc.restype = None
+            L.cd_launch_count.argtypes = []
+            L.cd_launch_count.restype = ctypes.c_uint64
             for name in SYMBOLS:
-                if name not in ("cd_status_str", "cd_last_error", "cd_opts_default", "cd_debug_fail_alloc"):
+                if name not in ("cd_status_str", "cd_last_error", "cd_opts_default", "cd_debug_fail_alloc",
+                                "cd_launch_count"):
                     getattr(L, name).restype = c_int
             _lib = L
     return _lib
@@ -233,6 +237,10 @@ def cd_graph_export(h):
 
 def cd_debug_fail_alloc(k: int):
     lib().cd_debug_fail_alloc(int(k))
+
+
+def cd_launch_count() -> int:
+    return int(lib().cd_launch_count())
 
 
 # ---------------------------------------------------------------------------

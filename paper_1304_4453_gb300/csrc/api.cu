@@ -287,4 +287,6 @@ cd_status cd_graph_export(const cd_graph *g, int64_t *row_ptr, int32_t *col, int
 
 void cd_debug_fail_alloc(int k) { set_alloc_failure(k); }
 
+uint64_t cd_launch_count(void) { return launch_count(); }
+
 }  // extern "C"

@@ -128,9 +128,9 @@ void coarsen_graph(const GraphView &g, const int32_t *zeta, int64_t *rank, Owned
     CD_CUDA(cudaMemsetAsync(inter.p + g.n, 0, sizeof(int64_t), s));
     const unsigned gw = grid_for(g.n * 32, kBlock, 152 * 64);
     if (g.n) {
-        if (g.wk == W_UNIT) k_coarse_count<W_UNIT><<<gw, kBlock, 0, s>>>(g, zeta, rank, inter.p, intra2.p);
-        else if (g.wk == W_I32) k_coarse_count<W_I32><<<gw, kBlock, 0, s>>>(g, zeta, rank, inter.p, intra2.p);
-        else k_coarse_count<W_I64><<<gw, kBlock, 0, s>>>(g, zeta, rank, inter.p, intra2.p);
+        if (g.wk == W_UNIT) { k_coarse_count<W_UNIT><<<gw, kBlock, 0, s>>>(g, zeta, rank, inter.p, intra2.p); ::cd::note_launch(); }
+        else if (g.wk == W_I32) { k_coarse_count<W_I32><<<gw, kBlock, 0, s>>>(g, zeta, rank, inter.p, intra2.p); ::cd::note_launch(); }
+        else { k_coarse_count<W_I64><<<gw, kBlock, 0, s>>>(g, zeta, rank, inter.p, intra2.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
     }
     DBuf<int64_t> tot(1, s);
@@ -143,9 +143,9 @@ void coarsen_graph(const GraphView &g, const int32_t *zeta, int64_t *rank, Owned
     DBuf<uint64_t> keys(T, s), keys2(T, s);
     DBuf<int64_t> wv(T, s), wv2(T, s);
     if (T) {
-        if (g.wk == W_UNIT) k_coarse_emit<W_UNIT><<<gw, kBlock, 0, s>>>(g, zeta, rank, pos.p, keys.p, wv.p);
-        else if (g.wk == W_I32) k_coarse_emit<W_I32><<<gw, kBlock, 0, s>>>(g, zeta, rank, pos.p, keys.p, wv.p);
-        else k_coarse_emit<W_I64><<<gw, kBlock, 0, s>>>(g, zeta, rank, pos.p, keys.p, wv.p);
+        if (g.wk == W_UNIT) { k_coarse_emit<W_UNIT><<<gw, kBlock, 0, s>>>(g, zeta, rank, pos.p, keys.p, wv.p); ::cd::note_launch(); }
+        else if (g.wk == W_I32) { k_coarse_emit<W_I32><<<gw, kBlock, 0, s>>>(g, zeta, rank, pos.p, keys.p, wv.p); ::cd::note_launch(); }
+        else { k_coarse_emit<W_I64><<<gw, kBlock, 0, s>>>(g, zeta, rank, pos.p, keys.p, wv.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
         std::vector<int> digits;
         const int b = bits_for(nc);
@@ -158,7 +158,7 @@ void coarsen_graph(const GraphView &g, const int32_t *zeta, int64_t *rank, Owned
     DBuf<int64_t> uidx(T, s);
     int64_t U = 0;
     if (T) {
-        k_heads<<<grid_for(T, kBlock, 152 * 32), kBlock, 0, s>>>(keys.p, T, head.p);
+        { k_heads<<<grid_for(T, kBlock, 152 * 32), kBlock, 0, s>>>(keys.p, T, head.p); ::cd::note_launch(); }
         exclusive_scan<int32_t>(head.p, uidx.p, T, tot.p, s);
         CD_CUDA(cudaMemcpyAsync(h.p, tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CD_CUDA(cudaStreamSynchronize(s));
@@ -174,8 +174,8 @@ void coarsen_graph(const GraphView &g, const int32_t *zeta, int64_t *rank, Owned
     wsum.zero();
     rowcnt.zero();
     if (T) {
-        k_reduce_runs<<<grid_for(T, kBlock, 152 * 32), kBlock, 0, s>>>(keys.p, wv.p, uidx.p, T, out.col.p, wsum.p,
-                                                                       rowcnt.p);
+        { k_reduce_runs<<<grid_for(T, kBlock, 152 * 32), kBlock, 0, s>>>(keys.p, wv.p, uidx.p, T, out.col.p, wsum.p,
+                                                                       rowcnt.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
     }
     out.rp.alloc(nc + 1, s);
@@ -187,11 +187,11 @@ void coarsen_graph(const GraphView &g, const int32_t *zeta, int64_t *rank, Owned
         v.w = out.w64.p;
     } else {
         out.w32.alloc(U, s);
-        if (U) k_to_i32<<<grid_for(U, kBlock, 152 * 32), kBlock, 0, s>>>(wsum.p, U, out.w32.p);
+        if (U) { k_to_i32<<<grid_for(U, kBlock, 152 * 32), kBlock, 0, s>>>(wsum.p, U, out.w32.p); ::cd::note_launch(); }
         v.w = out.w32.p;
     }
     out.self.alloc(nc, s);
-    if (nc) k_finish_self<<<grid_for(nc, kBlock, 152 * 32), kBlock, 0, s>>>(intra2.p, nc, out.self.p);
+    if (nc) { k_finish_self<<<grid_for(nc, kBlock, 152 * 32), kBlock, 0, s>>>(intra2.p, nc, out.self.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     finish_graph(out, s);
 }

@@ -1,47 +1,60 @@
 // Distance-1 colouring used as the deterministic schedule of the move and
 // label-propagation sweeps: first-fit Jones-Plassmann with hash priorities.
 //
-// Round r: every uncoloured vertex whose priority (fmix32(v ^ s), v) beats
-// all neighbours that were uncoloured when the round began takes the
-// smallest colour not used by its neighbours coloured in earlier rounds.
-// Such vertices are pairwise non-adjacent, so the outcome of a round does
-// not depend on the order in which they are processed.
+// Priority of v: (fmix32(v ^ s), v), larger wins.  Round r: every
+// uncoloured vertex whose priority beats all neighbours that were uncoloured
+// when the round began takes the smallest colour not used by its neighbours
+// coloured in earlier rounds.  Such vertices are pairwise non-adjacent, so a
+// round's outcome does not depend on processing order, and the result equals
+// greedy colouring in descending priority order.
 //
 // state[v] = -1 while uncoloured, else (round << 32) | colour, written with a
 // single 64-bit store so that a reader sees colour and round together.
+// Rounds run back to back on the device (the list length lives in device
+// memory); the host checks for completion every few rounds.
 #include "common.cuh"
 
 namespace cd {
 
-__device__ __forceinline__ bool prio_gt(uint32_t hx, int32_t x, uint32_t hv, int32_t v) {
-    return hx > hv || (hx == hv && x > v);
+__global__ void k_color_prio(int64_t n, uint32_t s, uint64_t *prio) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        prio[v] = fmix32((uint32_t)v ^ s);
+}
+
+__device__ __forceinline__ bool prio_gt(uint64_t px, int32_t x, uint64_t pv, int32_t v) {
+    return px > pv || (px == pv && x > v);
 }
 
 // One warp per listed vertex.
 __global__ void k_color_round(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                              const int32_t *__restrict__ list, int64_t count, uint32_t s, int32_t round,
-                              int64_t *state, int32_t *next, unsigned long long *next_count) {
+                              const uint64_t *__restrict__ prio, const int32_t *__restrict__ list,
+                              const unsigned long long *count_in, int32_t round, int64_t *state, int32_t *next,
+                              unsigned long long *next_count) {
     const int lane = threadIdx.x & 31;
+    const int64_t count = (int64_t)*count_in;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < count; i += nwarps) {
-        int32_t v = list[i];
-        uint32_t hv = fmix32((uint32_t)v ^ s);
-        int64_t beg = rp[v], end = rp[v + 1];
+        const int32_t v = list[i];
+        const uint64_t pv = prio[v];
+        const int64_t beg = rp[v], end = rp[v + 1];
         bool is_max = true;
         unsigned long long bits = 0;
-        for (int64_t e = beg + lane; e < end; e += 32) {
-            int32_t x = col[e];
-            int64_t st = ((volatile int64_t *)state)[x];
-            bool uncol = st < 0 || (int32_t)(st >> 32) == round;
-            if (uncol) {
-                if (prio_gt(fmix32((uint32_t)x ^ s), x, hv, v)) is_max = false;
-            } else {
-                uint32_t c = (uint32_t)st;
-                if (c < 64) bits |= 1ull << c;
+        for (int64_t e0 = beg; e0 < end; e0 += 32) {
+            const int64_t e = e0 + lane;
+            if (e < end) {
+                const int32_t x = col[e];
+                const int64_t st = ((volatile int64_t *)state)[x];
+                const bool uncol = st < 0 || (int32_t)(st >> 32) == round;
+                if (uncol) {
+                    if (prio_gt(prio[x], x, pv, v)) is_max = false;
+                } else {
+                    const uint32_t c = (uint32_t)st;
+                    if (c < 64) bits |= 1ull << c;
+                }
             }
+            if (__any_sync(0xffffffffu, !is_max)) { is_max = false; break; }
         }
-        is_max = __all_sync(0xffffffffu, is_max);
         if (!is_max) {
             if (lane == 0) next[atomicAdd(next_count, 1ull)] = v;
             continue;
@@ -56,8 +69,8 @@ __global__ void k_color_round(const int64_t *__restrict__ rp, const int32_t *__r
             while (true) {
                 unsigned long long b2 = 0;
                 for (int64_t e = beg + lane; e < end; e += 32) {
-                    int64_t st = state[col[e]];
-                    uint32_t cc = (uint32_t)st;
+                    const int64_t st = state[col[e]];
+                    const uint32_t cc = (uint32_t)st;
                     if (st >= 0 && cc >= base && cc < base + 64) b2 |= 1ull << (cc - base);
                 }
                 for (int o = 16; o > 0; o >>= 1) b2 |= __shfl_xor_sync(0xffffffffu, b2, o);
@@ -83,30 +96,41 @@ __global__ void k_color_extract(const int64_t *state, int64_t n, int32_t *color,
 int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStream_t s) {
     if (g.n == 0) return 0;
     const uint32_t sw = seed_word(seed);
+    constexpr int ROUNDS_PER_CHECK = 8;
     DBuf<int64_t> state(g.n, s);
+    DBuf<uint64_t> prio(g.n, s);
     CD_CUDA(cudaMemsetAsync(state.p, 0xff, g.n * sizeof(int64_t), s));
+    { k_color_prio<<<grid_for(g.n, kBlock, 152 * 32), kBlock, 0, s>>>(g.n, sw, prio.p); ::cd::note_launch(); }
     DBuf<int32_t> la(g.n, s), lb(g.n, s);
     iota32(la.p, g.n, s);
-    DBuf<unsigned long long> cnt(1, s);
+    DBuf<unsigned long long> cnt(2, s);   // list lengths: [0] current, [1] next
+    const unsigned long long n0 = (unsigned long long)g.n;
+    CD_CUDA(cudaMemcpyAsync(cnt.p, &n0, sizeof(n0), cudaMemcpyHostToDevice, s));
     Pinned h(sizeof(unsigned long long));
-    int64_t count = g.n;
+    int64_t known = g.n;   // upper bound on the current list length
     int32_t round = 0;
-    while (count > 0) {
-        cnt.zero();
-        k_color_round<<<grid_for(count * 32, kBlock, 152 * 64), kBlock, 0, s>>>(g.rp, g.col, la.p, count, sw, round,
-                                                                               state.p, lb.p, cnt.p);
-        CD_LAUNCH_CHECK();
-        CD_CUDA(cudaMemcpyAsync(h.p, cnt.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    int which = 0;         // cnt[which] holds the current length
+    while (true) {
+        for (int r = 0; r < ROUNDS_PER_CHECK; r++) {
+            int32_t *cur = (round & 1) ? lb.p : la.p;
+            int32_t *nxt = (round & 1) ? la.p : lb.p;
+            CD_CUDA(cudaMemsetAsync(cnt.p + (1 - which), 0, sizeof(unsigned long long), s));
+            { k_color_round<<<grid_for(known * 32, kBlock, 152 * 64), kBlock, 0, s>>>(
+                  g.rp, g.col, prio.p, cur, cnt.p + which, round, state.p, nxt, cnt.p + (1 - which)); ::cd::note_launch(); }
+            CD_LAUNCH_CHECK();
+            which = 1 - which;
+            round++;
+        }
+        CD_CUDA(cudaMemcpyAsync(h.p, cnt.p + which, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CD_CUDA(cudaStreamSynchronize(s));
-        int64_t left = (int64_t)*h.as<unsigned long long>();
-        if (left >= count) raise(CD_ECUDA, "colouring made no progress in round %d", round);
-        count = left;
-        std::swap(la, lb);
-        round++;
+        const int64_t left = (int64_t)*h.as<unsigned long long>();
+        if (left == 0) break;
+        if (left >= known) raise(CD_ECUDA, "colouring made no progress by round %d", round);
+        known = left;
     }
     DBuf<unsigned int> maxc(1, s);
     maxc.zero();
-    k_color_extract<<<grid_for(g.n, kBlock, 152 * 32), kBlock, 0, s>>>(state.p, g.n, color, maxc.p);
+    { k_color_extract<<<grid_for(g.n, kBlock, 152 * 32), kBlock, 0, s>>>(state.p, g.n, color, maxc.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     Pinned hm(sizeof(unsigned int));
     CD_CUDA(cudaMemcpyAsync(hm.p, maxc.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));

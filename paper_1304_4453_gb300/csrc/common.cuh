@@ -41,6 +41,10 @@ void set_last_error(const std::string &m);
 // Device memory: stream-ordered allocations from a library-owned pool that
 // keeps freed memory reserved, so repeated runs do not return to the driver.
 // ---------------------------------------------------------------------------
+// Counts kernel launches made by this library (every launch site calls it).
+void note_launch();
+uint64_t launch_count();
+
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);
 // Test hook: make the k-th next allocation fail with CD_ENOMEM (k <= 0: off).

@@ -11,16 +11,12 @@
 
 namespace cd {
 
-// From sweep DAMP_FROM of a move phase on, a vertex that wants to move does
-// so only when a hash coin of (vertex, sweep, seed) is heads.  Vertices of a
-// class decide on one volume snapshot and can otherwise keep leaving and
-// re-entering a community together; the paper's asynchronous updates avoid
-// such cycles (Section III-A).  The phase ends when no vertex wants to move.
-constexpr int DAMP_FROM = 16;
-
-static uint32_t move_salt(uint64_t seed, int32_t sw) {
-    return fmix32(seed_word(seed) ^ 0x7F4A7C15u ^ (0x9E3779B9u * (uint32_t)(sw + 1)));
-}
+// Sweeps 0 .. RECHECK_FROM-1 of a move phase apply every wanted move of a
+// class at once.  From sweep RECHECK_FROM on, a class's wanted moves are
+// re-checked one by one in ascending vertex id against the volumes updated
+// by the moves accepted before them (k_recheck), so every applied move raises
+// modularity and the phase terminates.
+constexpr int RECHECK_FROM = 4;
 
 // PLP ties between dominant labels follow fmix32(label ^ salt), a seeded
 // pseudo-random order that changes every iteration ("ties arbitrarily",
@@ -50,7 +46,7 @@ struct Schedule {
     DBuf<int32_t> hub_keys;
     DBuf<unsigned long long> hub_vals, hub_wc;
     DBuf<unsigned int> done1, done2;
-    DBuf<int64_t> part_g, part_g2;
+    DBuf<int64_t> part_g, part_g2, part_w;
     DBuf<int32_t> part_id;
     DBuf<uint32_t> part_tk;
 };
@@ -96,13 +92,13 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     if (n) {
         DBuf<uint32_t> key(n, s), key2(n, s);
         DBuf<int32_t> val2(n, s);
-        k_sched_keys<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(g.rp, n, color.p, S.ncol, key.p, S.order.p);
+        { k_sched_keys<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(g.rp, n, color.p, S.ncol, key.p, S.order.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
         std::vector<int> digits;
         for (int d = 0; d < bits_for(nbk + 1); d += 8) digits.push_back(d);
         radix_sort_pairs<uint32_t, int32_t>(key.p, S.order.p, key2.p, val2.p, n, digits, s);
         DBuf<int64_t> offd(nbk + 1, s);
-        k_bucket_bounds<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(key.p, n, nbk, offd.p);
+        { k_bucket_bounds<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(key.p, n, nbk, offd.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
         CD_CUDA(cudaMemcpyAsync(S.off.data(), offd.p, (nbk + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CD_CUDA(cudaStreamSynchronize(s));
@@ -134,7 +130,7 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
         DBuf<int32_t> dv(H, s);
         DBuf<int64_t> dd(H, s);
         CD_CUDA(cudaMemcpyAsync(dv.p, pv.p, H * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        k_degrees<<<grid_for(H, kBlock), kBlock, 0, s>>>(g.rp, dv.p, H, dd.p);
+        { k_degrees<<<grid_for(H, kBlock), kBlock, 0, s>>>(g.rp, dv.p, H, dd.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
         CD_CUDA(cudaMemcpyAsync(pd.p, dd.p, H * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CD_CUDA(cudaStreamSynchronize(s));
@@ -183,6 +179,7 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     S.done2.zero();
     S.part_g.alloc(S.max_nb2, s);
     S.part_g2.alloc(S.max_nb2, s);
+    S.part_w.alloc(S.max_nb2, s);
     S.part_id.alloc(S.max_nb2, s);
     S.part_tk.alloc(S.max_nb2, s);
     CD_CUDA(cudaStreamSynchronize(s));   // host vectors above go out of scope
@@ -206,6 +203,7 @@ static void fill_class(const Schedule &S, int32_t k, SweepCtx &c, ClassBins &cb)
     c.hub_done2 = S.done2.p + h0;
     c.part_g = S.part_g.p;
     c.part_g2 = S.part_g2.p;
+    c.part_w = S.part_w.p;
     c.part_id = S.part_id.p;
     c.part_tk = S.part_tk.p;
 }
@@ -218,21 +216,25 @@ static int wbytes(int wk) { return wk == W_UNIT ? 0 : wk == W_I32 ? 4 : 8; }
 static int64_t move_phase(const GraphView &g, const Schedule &S, int32_t *zeta, int64_t *volc, const RunOpts &o,
                           RunStats &st, LaunchTimer &timer, cudaStream_t s) {
     const bool big = needs_big(g.W);
-    DBuf<int32_t> mv_u(g.n, s), mv_c(g.n, s);
-    DBuf<unsigned long long> nmv(S.ncol, s);
+    DBuf<int32_t> mv_u(g.n, s), mv_c(g.n, s), cd_(g.n, s);
+    DBuf<int64_t> cwd(g.n, s), cwc(g.n, s);
+    DBuf<uint64_t> tmp_a(g.n, s), tmp_b(g.n, s);
+    DBuf<unsigned long long> nmv(S.ncol, s), ncand(S.ncol, s);
     DBuf<Counters> cnt(1, s);
     Pinned hc(sizeof(Counters));
+    int ubits = 1;
+    while (((int64_t)1 << ubits) < g.n) ubits++;
     int64_t total = 0;
     for (int32_t sw = 0; sw < o.max_sweeps; sw++) {
         cnt.zero();
         nmv.zero();
+        ncand.zero();
         SweepCtx c{};
         c.g = g;
         c.zeta = zeta;
         c.volc = volc;
         c.cnt = cnt.p;
-        c.coin_salt = move_salt(o.seed, sw);
-        c.damp = sw >= DAMP_FROM;
+        c.late = sw >= RECHECK_FROM;
         for (int32_t k = 0; k < S.ncol; k++) {
             const int64_t a = S.off[(int64_t)k * NBINS], e = S.off[(int64_t)k * NBINS + NBINS];
             if (e == a) continue;
@@ -241,10 +243,23 @@ static int64_t move_phase(const GraphView &g, const Schedule &S, int32_t *zeta, 
             c.mv_u = mv_u.p + a;
             c.mv_c = mv_c.p + a;
             c.nmv = nmv.p + k;
+            // candidate records reuse the move-record buffers (one or the other per sweep)
+            c.cand_u = mv_u.p + a;
+            c.cand_c = mv_c.p + a;
+            c.cand_d = cd_.p + a;
+            c.cand_wd = cwd.p + a;
+            c.cand_wc = cwc.p + a;
+            c.ncand = ncand.p + k;
             decide_class<false>(g.wk, big, c, cb, s, timer);
-            k_apply_moves<<<grid_for(e - a, kBlock, 152 * 8), kBlock, 0, s>>>(mv_u.p + a, mv_c.p + a, nmv.p + k, zeta,
-                                                                             g.vol, volc);
-            CD_LAUNCH_CHECK();
+            if (!c.late) {
+                { k_apply_moves<<<grid_for(e - a, kBlock, 152 * 8), kBlock, 0, s>>>(mv_u.p + a, mv_c.p + a, nmv.p + k, zeta,
+                                                                                 g.vol, volc); ::cd::note_launch(); }
+                CD_LAUNCH_CHECK();
+            } else {
+                RecheckArgs ra{c.cand_u, c.cand_c, c.cand_d, c.cand_wd, c.cand_wc, c.ncand, zeta, g.vol, volc,
+                               2 * g.W, tmp_a.p, tmp_b.p, ubits, cnt.p};
+                recheck_class(big, ra, s);
+            }
         }
         CD_CUDA(cudaMemcpyAsync(hc.p, cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, s));
         CD_CUDA(cudaStreamSynchronize(s));
@@ -319,12 +334,12 @@ void run_plm(const GraphView &g0, bool refine, const RunOpts &o, int32_t *labels
         Level &lv = *L[d];
         const int64_t n = lv.g.n;
         if (n)
-            k_prolong<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(lv.zeta.p, lv.rank.p, L[d + 1]->zeta.p, n);
+            { k_prolong<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(lv.zeta.p, lv.rank.p, L[d + 1]->zeta.p, n); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
         if (refine) {
             DBuf<int64_t> volc(n, s);
             volc.zero();
-            if (n) k_comm_volumes<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(lv.zeta.p, lv.g.vol, n, volc.p);
+            if (n) { k_comm_volumes<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(lv.zeta.p, lv.g.vol, n, volc.p); ::cd::note_launch(); }
             CD_LAUNCH_CHECK();
             auto t = Clock::now();
             move_phase(lv.g, lv.S, lv.zeta.p, volc.p, o, st, timer, s);
@@ -438,16 +453,16 @@ static void fold_core(int32_t *core, const int32_t *z, int64_t n, cudaStream_t s
     DBuf<int32_t> val(n, s), val2(n, s), head(n, s);
     DBuf<int64_t> uidx(n, s);
     const unsigned gb = grid_for(n, kBlock, 152 * 32);
-    k_pair_keys<<<gb, kBlock, 0, s>>>(core, z, n, key.p, val.p);
+    { k_pair_keys<<<gb, kBlock, 0, s>>>(core, z, n, key.p, val.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     std::vector<int> digits;
     const int b = bits_for(n);
     for (int d = 0; d < b; d += 8) digits.push_back(d);
     for (int d = 0; d < b; d += 8) digits.push_back(32 + d);
     radix_sort_pairs<uint64_t, int32_t>(key.p, val.p, key2.p, val2.p, n, digits, s);
-    k_heads64<<<gb, kBlock, 0, s>>>(key.p, n, head.p);
+    { k_heads64<<<gb, kBlock, 0, s>>>(key.p, n, head.p); ::cd::note_launch(); }
     exclusive_scan<int32_t>(head.p, uidx.p, n, nullptr, s);
-    k_scatter_rank<<<gb, kBlock, 0, s>>>(val.p, head.p, uidx.p, n, core);
+    { k_scatter_rank<<<gb, kBlock, 0, s>>>(val.p, head.p, uidx.p, n, core); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
 }
 
@@ -499,7 +514,7 @@ void run_epp(const GraphView &g, int b, bool final_refine, const RunOpts &o, dou
     st.ms_move += sf.ms_move;
     st.ms_coarsen += sf.ms_coarsen;
     if (!sf.converged) st.converged = 0;
-    if (n) k_gather_core<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(zc.p, core.p, n, labels);
+    if (n) { k_gather_core<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(zc.p, core.p, n, labels); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     st.ncomm = (int32_t)compact_labels(labels, n, s);
     CD_CUDA(cudaStreamSynchronize(s));

@@ -122,8 +122,8 @@ void finish_graph(OwnedGraph &g, cudaStream_t s) {
     if (v.n == 0) return;
     DBuf<unsigned long long> red(2, s);
     red.zero();
-    k_volumes<<<grid_for(v.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(v.n, v.rp, v.w, v.wk, v.self, g.vol.p,
-                                                                     red.p, red.p + 1);
+    { k_volumes<<<grid_for(v.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(v.n, v.rp, v.w, v.wk, v.self, g.vol.p,
+                                                                     red.p, red.p + 1); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     Pinned h(2 * sizeof(unsigned long long));
     CD_CUDA(cudaMemcpyAsync(h.p, red.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -164,8 +164,8 @@ void build_graph(int64_t n, const int64_t *rp_in, const int32_t *col_in, const i
     err.zero();
     DBuf<int32_t> loops(n + 1, s);
     if (n) {
-        k_validate<<<grid_for(n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(n, nnz, rp.p, col.p, w_in ? w.p : nullptr,
-                                                                        err.p, loops.p);
+        { k_validate<<<grid_for(n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(n, nnz, rp.p, col.p, w_in ? w.p : nullptr,
+                                                                        err.p, loops.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
     }
     DBuf<int64_t> loops_before(n + 1, s);
@@ -205,11 +205,11 @@ void build_graph(int64_t n, const int64_t *rp_in, const int32_t *col_in, const i
         if (w_in) out.w32.alloc(m_nnz, s);
         unsigned gb = grid_for(n * 32, kBlock, 152 * 64);
         if (w_in)
-            k_strip_loops<true><<<gb, kBlock, 0, s>>>(n, rp.p, col.p, w.p, loops_before.p, out.rp.p, out.col.p,
-                                                     out.w32.p, out.self.p);
+            { k_strip_loops<true><<<gb, kBlock, 0, s>>>(n, rp.p, col.p, w.p, loops_before.p, out.rp.p, out.col.p,
+                                                     out.w32.p, out.self.p); ::cd::note_launch(); }
         else
-            k_strip_loops<false><<<gb, kBlock, 0, s>>>(n, rp.p, col.p, nullptr, loops_before.p, out.rp.p, out.col.p,
-                                                      nullptr, out.self.p);
+            { k_strip_loops<false><<<gb, kBlock, 0, s>>>(n, rp.p, col.p, nullptr, loops_before.p, out.rp.p, out.col.p,
+                                                      nullptr, out.self.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
     }
     v.w = w_in ? (const void *)out.w32.p : nullptr;
@@ -255,7 +255,7 @@ int64_t export_graph(const GraphView &g, int64_t *rp, int32_t *col, int64_t *w, 
     DBuf<int32_t> f(g.n + 1, s);
     DBuf<int64_t> lb(g.n + 1, s);
     CD_CUDA(cudaMemsetAsync(f.p, 0, (g.n + 1) * sizeof(int32_t), s));
-    if (g.n) k_loop_flags<<<grid_for(g.n, kBlock, 152 * 32), kBlock, 0, s>>>(g.n, g.self, f.p);
+    if (g.n) { k_loop_flags<<<grid_for(g.n, kBlock, 152 * 32), kBlock, 0, s>>>(g.n, g.self, f.p); ::cd::note_launch(); }
     exclusive_scan<int32_t>(f.p, lb.p, g.n + 1, nullptr, s);
     Pinned h(sizeof(int64_t));
     CD_CUDA(cudaMemcpyAsync(h.p, lb.p + g.n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -275,8 +275,8 @@ int64_t export_graph(const GraphView &g, int64_t *rp, int32_t *col, int64_t *w, 
     if (g.n == 0) {
         if (orp) CD_CUDA(cudaMemsetAsync(orp, 0, sizeof(int64_t), s));
     } else {
-        k_export<<<grid_for(g.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(g, lb.p, orp, col ? ocol : nullptr,
-                                                                        col ? ow : nullptr);
+        { k_export<<<grid_for(g.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(g, lb.p, orp, col ? ocol : nullptr,
+                                                                        col ? ow : nullptr); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
     }
     if (!dev) {

@@ -76,14 +76,14 @@ double modularity(const GraphView &g, const int32_t *labels, cudaStream_t s) {
     volc.zero();
     in2.zero();
     const unsigned gw = grid_for(g.n * 32, kBlock, 152 * 64);
-    if (g.wk == W_UNIT) k_mod_rows<W_UNIT><<<gw, kBlock, 0, s>>>(g, labels, volc.p, in2.p);
-    else if (g.wk == W_I32) k_mod_rows<W_I32><<<gw, kBlock, 0, s>>>(g, labels, volc.p, in2.p);
-    else k_mod_rows<W_I64><<<gw, kBlock, 0, s>>>(g, labels, volc.p, in2.p);
+    if (g.wk == W_UNIT) { k_mod_rows<W_UNIT><<<gw, kBlock, 0, s>>>(g, labels, volc.p, in2.p); ::cd::note_launch(); }
+    else if (g.wk == W_I32) { k_mod_rows<W_I32><<<gw, kBlock, 0, s>>>(g, labels, volc.p, in2.p); ::cd::note_launch(); }
+    else { k_mod_rows<W_I64><<<gw, kBlock, 0, s>>>(g, labels, volc.p, in2.p); ::cd::note_launch(); }
     const int nb = (int)grid_for(g.n, kBlock, 152 * 8);
     DBuf<unsigned long long> part(2 * nb, s);
-    k_mod_sq<<<nb, kBlock, 0, s>>>(volc.p, g.n, part.p);
+    { k_mod_sq<<<nb, kBlock, 0, s>>>(volc.p, g.n, part.p); ::cd::note_launch(); }
     DBuf<double> res(1, s);
-    k_mod_final<<<1, 32, 0, s>>>(part.p, nb, in2.p, g.W, res.p);
+    { k_mod_final<<<1, 32, 0, s>>>(part.p, nb, in2.p, g.W, res.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     Pinned h(sizeof(double));
     CD_CUDA(cudaMemcpyAsync(h.p, res.p, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -57,8 +57,10 @@ struct SweepCtx {
     int32_t *mv_u, *mv_c;      // PLM: move records of this class
     unsigned long long *nmv;   // PLM: number of records of this class
     Counters *cnt;
-    uint32_t coin_salt;        // PLM damping coin
-    int damp;                  // PLM: 1 when the coin applies this sweep
+    int late;                  // PLM: 1 from the re-check sweep on
+    int32_t *cand_u, *cand_c, *cand_d;   // PLM late sweeps: wanted moves
+    int64_t *cand_wd, *cand_wc;          //   omega(u, D), omega(u, C \ u)
+    unsigned long long *ncand;           //   count for this class
     uint8_t *active;           // PLP active flags
     uint32_t tie_salt;         // PLP tie order
     // hubs of this class
@@ -71,6 +73,7 @@ struct SweepCtx {
     unsigned int *hub_done1, *hub_done2;
     int64_t *part_g;           // H2 partial bests: gain hi/lo or weight
     int64_t *part_g2;
+    int64_t *part_w;           // H2 partial bests: omega(u, D) (PLM)
     int32_t *part_id;
     uint32_t *part_tk;
 };
@@ -128,13 +131,14 @@ struct GainT<true> { using T = __int128; };
 template <bool BIG>
 struct PlmBest {
     typename GainT<BIG>::T g;
+    int64_t w;                 // omega(u, id)
     int32_t id;
-    __device__ __forceinline__ void init() { g = 0; id = -1; }
-    __device__ __forceinline__ void offer(typename GainT<BIG>::T gg, int32_t d) {
-        if (id < 0 || gg > g || (gg == g && d < id)) { g = gg; id = d; }
+    __device__ __forceinline__ void init() { g = 0; w = 0; id = -1; }
+    __device__ __forceinline__ void offer(typename GainT<BIG>::T gg, int32_t d, int64_t ww) {
+        if (id < 0 || gg > g || (gg == g && d < id)) { g = gg; id = d; w = ww; }
     }
     __device__ __forceinline__ void merge(const PlmBest &o) {
-        if (o.id >= 0) offer(o.g, o.id);
+        if (o.id >= 0) offer(o.g, o.id, o.w);
     }
     __device__ __forceinline__ PlmBest shfl_xor(unsigned mask, int off) const {
         PlmBest r;
@@ -146,6 +150,7 @@ struct PlmBest {
         } else {
             r.g = __shfl_xor_sync(mask, g, off);
         }
+        r.w = __shfl_xor_sync(mask, w, off);
         r.id = __shfl_xor_sync(mask, id, off);
         return r;
     }
@@ -199,8 +204,14 @@ __device__ __forceinline__ void add_counters(Counters *c, unsigned wanted, unsig
     }
 }
 
-__device__ __forceinline__ bool coin_skips(const SweepCtx &c, int32_t u) {
-    return c.damp && (fmix32((uint32_t)u ^ c.coin_salt) & 1u);
+// Late sweeps: record a wanted move for the class's sequential re-check.
+__device__ __forceinline__ void put_candidate(const SweepCtx &c, unsigned long long pos, int32_t u, int32_t C,
+                                              int32_t D, int64_t wD, int64_t wC) {
+    c.cand_u[pos] = u;
+    c.cand_c[pos] = C;
+    c.cand_d[pos] = D;
+    c.cand_wd[pos] = wD;
+    c.cand_wc[pos] = wC;
 }
 
 // ---------------------------------------------------------------------------
@@ -259,22 +270,27 @@ __global__ void __launch_bounds__(kBlock) k_decide_group(SweepCtx c, const int32
             const int32_t key = keys[s];
             if (valid && key >= 0) {
                 ncand++;
-                if (key != C) b.offer(plm_gain<BIG>(twoW, (int64_t)vals[s], wC, vu, c.volc[key], volC), key);
+                if (key != C)
+                    b.offer(plm_gain<BIG>(twoW, (int64_t)vals[s], wC, vu, c.volc[key], volC), key, (int64_t)vals[s]);
             }
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) b.merge(b.shfl_xor(gmask, o));
-        bool want = gl == 0 && valid && b.id >= 0 && b.g > 0;
-        bool apply = want && !coin_skips(c, u);
-        unsigned ballot = __ballot_sync(0xffffffffu, apply);
+        const bool want = gl == 0 && valid && b.id >= 0 && b.g > 0;
+        const bool apply = want && !c.late;
+        const unsigned ballot = __ballot_sync(0xffffffffu, want);
         unsigned long long base = 0;
-        if (lane == 0 && ballot) base = atomicAdd(c.nmv, (unsigned long long)__popc(ballot));
+        if (lane == 0 && ballot) base = atomicAdd(c.late ? c.ncand : c.nmv, (unsigned long long)__popc(ballot));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (apply) {
-            unsigned long long pos = base + __popc(ballot & ((1u << lane) - 1u));
-            c.zeta[u] = b.id;
-            c.mv_u[pos] = u;
-            c.mv_c[pos] = C;
+        if (want) {
+            const unsigned long long pos = base + __popc(ballot & ((1u << lane) - 1u));
+            if (apply) {
+                c.zeta[u] = b.id;
+                c.mv_u[pos] = u;
+                c.mv_c[pos] = C;
+            } else {
+                put_candidate(c, pos, u, C, b.id, b.w, wC);
+            }
         }
         add_counters(c.cnt, want, apply, gl == 0 && valid ? deg : 0, ncand, gl == 0 && valid);
     } else {
@@ -360,20 +376,24 @@ __global__ void __launch_bounds__(kBlock) k_decide_block(SweepCtx c, const int32
                 const int32_t key = keys[s];
                 if (key >= 0) {
                     ncand++;
-                    if (key != C) b.offer(plm_gain<BIG>(twoW, (int64_t)vals[s], wC, vu, c.volc[key], volC), key);
+                    if (key != C)
+                        b.offer(plm_gain<BIG>(twoW, (int64_t)vals[s], wC, vu, c.volc[key], volC), key,
+                                (int64_t)vals[s]);
                 }
             }
             ncand = __reduce_add_sync(0xffffffffu, ncand);
             if ((threadIdx.x & 31) == 0) atomicAdd(&s_cand, ncand);
             b = block_best(b, s_best);
             if (threadIdx.x == 0) {
-                bool want = b.id >= 0 && b.g > 0;
-                bool apply = want && !coin_skips(c, u);
+                const bool want = b.id >= 0 && b.g > 0;
+                const bool apply = want && !c.late;
                 if (apply) {
-                    unsigned long long pos = atomicAdd(c.nmv, 1ull);
+                    const unsigned long long pos = atomicAdd(c.nmv, 1ull);
                     c.zeta[u] = b.id;
                     c.mv_u[pos] = u;
                     c.mv_c[pos] = C;
+                } else if (want) {
+                    put_candidate(c, atomicAdd(c.ncand, 1ull), u, C, b.id, b.w, wC);
                 }
                 atomicAdd(&c.cnt->wanted, (unsigned long long)want);
                 atomicAdd(&c.cnt->moved, (unsigned long long)apply);
@@ -493,7 +513,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_decide(SweepCtx c) {
             const int32_t key = gk[s];
             if (key >= 0) {
                 ncand++;
-                if (key != C) b.offer(plm_gain<BIG>(twoW, (int64_t)gv[s], wC, vu, c.volc[key], volC), key);
+                if (key != C) b.offer(plm_gain<BIG>(twoW, (int64_t)gv[s], wC, vu, c.volc[key], volC), key, (int64_t)gv[s]);
                 gk[s] = -1;
                 gv[s] = 0;
             }
@@ -521,6 +541,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_decide(SweepCtx c) {
             } else {
                 c.part_g[pslot] = b.g;
             }
+            c.part_w[pslot] = b.w;
         } else {
             c.part_g[pslot] = b.w;
             c.part_tk[pslot] = b.tk;
@@ -550,6 +571,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_decide(SweepCtx c) {
                 } else {
                     o.g = __ldcg(c.part_g + p0 + k);
                 }
+                o.w = __ldcg(c.part_w + p0 + k);
             } else {
                 o.w = __ldcg(c.part_g + p0 + k);
                 o.tk = __ldcg(c.part_tk + p0 + k);
@@ -558,13 +580,15 @@ __global__ void __launch_bounds__(kBlock) k_hub_decide(SweepCtx c) {
         }
         const int deg = (int)(c.g.rp[u + 1] - c.g.rp[u]);
         if constexpr (!PLP) {
-            bool want = r.id >= 0 && r.g > 0;
-            bool apply = want && !coin_skips(c, u);
+            const bool want = r.id >= 0 && r.g > 0;
+            const bool apply = want && !c.late;
             if (apply) {
-                unsigned long long pos = atomicAdd(c.nmv, 1ull);
+                const unsigned long long pos = atomicAdd(c.nmv, 1ull);
                 c.zeta[u] = r.id;
                 c.mv_u[pos] = u;
                 c.mv_c[pos] = C;
+            } else if (want) {
+                put_candidate(c, atomicAdd(c.ncand, 1ull), u, C, r.id, r.w, wC);
             }
             atomicAdd(&c.cnt->wanted, (unsigned long long)want);
             atomicAdd(&c.cnt->moved, (unsigned long long)apply);

@@ -98,9 +98,9 @@ void exclusive_scan(const Tin *in, int64_t *out, int64_t count, int64_t *total_d
     int64_t chunk;
     scan_geometry(count, nb, chunk);
     DBuf<int64_t> partial(nb, s);
-    k_scan_reduce<Tin><<<nb, kBlock, 0, s>>>(in, count, chunk, partial.p);
-    k_scan_partials<<<1, kBlock, 0, s>>>(partial.p, nb, total_dev);
-    k_scan_apply<Tin><<<nb, kBlock, 0, s>>>(in, out, count, chunk, partial.p);
+    { k_scan_reduce<Tin><<<nb, kBlock, 0, s>>>(in, count, chunk, partial.p); ::cd::note_launch(); }
+    { k_scan_partials<<<1, kBlock, 0, s>>>(partial.p, nb, total_dev); ::cd::note_launch(); }
+    { k_scan_apply<Tin><<<nb, kBlock, 0, s>>>(in, out, count, chunk, partial.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
 }
 
@@ -193,9 +193,9 @@ void radix_sort_pairs(K *keys, V *vals, K *keys_alt, V *vals_alt, int64_t count,
     K *ka = keys, *kb = keys_alt;
     V *va = vals, *vb = vals_alt;
     for (int shift : digits) {
-        k_rs_hist<K><<<nb, kBlock, 0, s>>>(ka, count, chunk, shift, hist.p, nb);
+        { k_rs_hist<K><<<nb, kBlock, 0, s>>>(ka, count, chunk, shift, hist.p, nb); ::cd::note_launch(); }
         exclusive_scan<uint32_t>(hist.p, offs.p, (int64_t)256 * nb, nullptr, s);
-        k_rs_scatter<K, V><<<nb, kBlock, 0, s>>>(ka, va, kb, vb, count, chunk, shift, offs.p, nb);
+        { k_rs_scatter<K, V><<<nb, kBlock, 0, s>>>(ka, va, kb, vb, count, chunk, shift, offs.p, nb); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -223,7 +223,7 @@ __global__ void k_iota32(int32_t *out, int64_t n) {
 
 void iota32(int32_t *out, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
-    k_iota32<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(out, n);
+    { k_iota32<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(out, n); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
 }
 
@@ -235,7 +235,7 @@ __global__ void k_mark_used(const int32_t *labels, int64_t n, int64_t *flags) {
 int64_t dense_rank(const int32_t *labels, int64_t n, int64_t *rank_of_label, cudaStream_t s) {
     if (n <= 0) return 0;
     CD_CUDA(cudaMemsetAsync(rank_of_label, 0, n * sizeof(int64_t), s));
-    k_mark_used<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(labels, n, rank_of_label);
+    { k_mark_used<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(labels, n, rank_of_label); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     DBuf<int64_t> total(1, s);
     exclusive_scan<int64_t>(rank_of_label, rank_of_label, n, total.p, s);
@@ -252,7 +252,7 @@ __global__ void k_apply_rank(int32_t *labels, const int64_t *rank, int64_t n) {
 
 void apply_rank(int32_t *labels, const int64_t *rank, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
-    k_apply_rank<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(labels, rank, n);
+    { k_apply_rank<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(labels, rank, n); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
 }
 
@@ -273,7 +273,7 @@ bool labels_in_range(const int32_t *labels, int64_t n, cudaStream_t s) {
     if (n <= 0) return true;
     DBuf<int> bad(1, s);
     bad.zero();
-    k_range<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(labels, n, bad.p);
+    { k_range<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(labels, n, bad.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     Pinned h(sizeof(int));
     CD_CUDA(cudaMemcpyAsync(h.p, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));

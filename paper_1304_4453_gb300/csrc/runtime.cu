@@ -25,6 +25,10 @@ const std::string &last_error() { return t_last_error; }
 static std::mutex g_pool_mu;
 static cudaMemPool_t g_pools[64] = {};
 static std::atomic<int> g_fail_countdown{0};
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void set_alloc_failure(int k) { g_fail_countdown.store(k > 0 ? k : 0); }
 

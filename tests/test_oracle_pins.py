@@ -138,6 +138,40 @@ def test_colouring_is_proper_and_first_fit(oracle_mod, seed):
     assert np.array_equal(col, col2)
 
 
+def _greedy_in_priority_order(rp, c, seed):
+    """Sequential greedy colouring: vertices in descending priority
+    (fmix32(v ^ fmix32(seed_lo ^ seed_hi)), v), each taking the smallest
+    colour not used by its already coloured neighbours."""
+    def fmix(h):
+        h &= 0xFFFFFFFF
+        h ^= h >> 16; h = (h * 0x85EBCA6B) & 0xFFFFFFFF
+        h ^= h >> 13; h = (h * 0xC2B2AE35) & 0xFFFFFFFF
+        return h ^ (h >> 16)
+    n = len(rp) - 1
+    s = fmix((seed & 0xFFFFFFFF) ^ (seed >> 32))
+    nbrs = [[int(x) for x in c[rp[u]:rp[u + 1]] if x != u] for u in range(n)]
+    order = sorted(range(n), key=lambda v: (fmix(v ^ s), v), reverse=True)
+    col = [-1] * n
+    for v in order:
+        used = {col[x] for x in nbrs[v] if col[x] >= 0}
+        k = 0
+        while k in used:
+            k += 1
+        col[v] = k
+    return col
+
+
+@pytest.mark.parametrize("seed", [1, 5, 2**40 + 3])
+def test_colouring_equals_greedy_in_priority_order(oracle_mod, seed):
+    """Jones-Plassmann first-fit colours a vertex only after all of its
+    higher-priority neighbours, and never after a lower-priority one, so it
+    equals sequential greedy colouring in descending priority order."""
+    for g in (synth.rmat(9, seed=3), synth.random_graph(200, 900, seed=seed % 97, loops=4)):
+        rp, c, w = csr(g)
+        k, col = oracle_mod.color(rp, c, w, seed)
+        assert col.tolist() == _greedy_in_priority_order(rp, c, seed)
+
+
 def test_colouring_isolated_and_complete(oracle_mod):
     g = synth.from_edge_list(4, [], self_loops={1: 3})
     rp, c, w = csr(g)
