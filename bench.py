@@ -312,7 +312,9 @@ def run_ours(a):
         "modularity": mod,
         "plm": {"levels": st["levels"], "colors0": st["colors0"], "sweeps": st["sweeps"],
                 "communities": st["ncomm"], "ms_color": st["ms_color"], "ms_move": st["ms_move"],
-                "ms_coarsen": st["ms_coarsen"], "converged": st["converged"]},
+                "ms_coarsen": st["ms_coarsen"], "ms_total": st["ms_total"], "converged": st["converged"],
+                "move_kernel_stage_ms": {"items": st["stage_items_ms"], "hub_decide": st["stage_hub_ms"],
+                                         "recheck": st["stage_recheck_ms"]}},
         "plp": {"edges_per_s": g.m / plp_s, "modularity": plp_mod, "iters": plp_st["iters"],
                 "communities": plp_st["ncomm"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz,

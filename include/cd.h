@@ -85,10 +85,13 @@ typedef struct {
     int64_t candidates;      /* distinct neighbour communities evaluated */
     int64_t decisions;       /* vertex decisions taken */
     double ms_color, ms_move, ms_coarsen, ms_total;
-    /* local-move (decide) kernels, filled when opts.profile = 1 */
-    int64_t k_launches;      /* decide-kernel launches timed */
+    /* local-move kernels, filled when opts.profile = 1 */
+    int64_t k_launches;      /* move-phase / PLP kernel launches timed */
     double k_ms;             /* their summed device time */
-    double k_bytes;          /* their algorithmic bytes (see DESIGN) */
+    double k_bytes;          /* their algorithmic bytes (from the schedule counters) */
+    double stage_items_ms;   /* PLM move kernel: decide items of each class */
+    double stage_hub_ms;     /*   hub decisions */
+    double stage_recheck_ms; /*   sequential re-check of late sweeps */
 } cd_stats;
 
 void cd_opts_default(cd_opts *o);

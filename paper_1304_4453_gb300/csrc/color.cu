@@ -1,94 +1,210 @@
 // Distance-1 colouring used as the deterministic schedule of the move and
 // label-propagation sweeps: first-fit Jones-Plassmann with hash priorities.
 //
-// Priority of v: (fmix32(v ^ s), v), larger wins.  Round r: every
-// uncoloured vertex whose priority beats all neighbours that were uncoloured
-// when the round began takes the smallest colour not used by its neighbours
-// coloured in earlier rounds.  Such vertices are pairwise non-adjacent, so a
-// round's outcome does not depend on processing order, and the result equals
-// greedy colouring in descending priority order.
+// Priority of v: (fmix32(v ^ s), v), larger wins.  Jones-Plassmann colours a
+// vertex once all of its higher-priority neighbours are coloured, giving it
+// the smallest colour none of them uses; the result equals greedy colouring
+// in descending priority order.
 //
-// state[v] = -1 while uncoloured, else (round << 32) | colour, written with a
-// single 64-bit store so that a reader sees colour and round together.
-// Rounds run back to back on the device (the list length lives in device
-// memory); the host checks for completion every few rounds.
+// Dependency-count form: wait[v] = number of higher-priority neighbours.
+// Vertices with wait 0 form the first frontier.  A frontier vertex reads the
+// colours of its higher-priority neighbours (all set), takes the smallest
+// free colour, and decrements wait of its lower-priority neighbours; those
+// that reach 0 form the next frontier.  Every adjacency entry is read once to
+// count and once when its row's vertex is coloured (plus a rescan per extra
+// window of 64 colours).  Frontier vertices of degree <= 1024 are handled by
+// one warp each; the adjacency of larger ones is cut into chunks spread over
+// all blocks (k_color_round_hubs).  Rounds run back to back on
+// the device (frontier lengths live in device memory); the host checks for
+// completion every few rounds.
 #include "common.cuh"
 
 namespace cd {
 
-__global__ void k_color_prio(int64_t n, uint32_t s, uint64_t *prio) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        prio[v] = fmix32((uint32_t)v ^ s);
+constexpr int COLOR_BIG_DEG = 1024;
+
+__device__ __forceinline__ bool prio_gt(uint32_t hx, int32_t x, uint32_t hv, int32_t v) {
+    return hx > hv || (hx == hv && x > v);
 }
 
-__device__ __forceinline__ bool prio_gt(uint64_t px, int32_t x, uint64_t pv, int32_t v) {
-    return px > pv || (px == pv && x > v);
+__device__ __forceinline__ void push_ready(int32_t x, const int64_t *rp, int32_t *nl, unsigned long long *nlc,
+                                           int32_t *nh, unsigned long long *nhc) {
+    if (rp[x + 1] - rp[x] > COLOR_BIG_DEG) nh[atomicAdd(nhc, 1ull)] = x;
+    else nl[atomicAdd(nlc, 1ull)] = x;
 }
 
-// One warp per listed vertex.
-__global__ void k_color_round(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                              const uint64_t *__restrict__ prio, const int32_t *__restrict__ list,
-                              const unsigned long long *count_in, int32_t round, int64_t *state, int32_t *next,
-                              unsigned long long *next_count) {
+// wait[v] and the first frontier; one warp per vertex.
+__global__ void k_color_init(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, int64_t n, uint32_t s,
+                             uint32_t *hash, int32_t *wait, int32_t *color, int32_t *nl, unsigned long long *nlc,
+                             int32_t *nh, unsigned long long *nhc, int32_t *hub_slot, unsigned int *nhubs) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        const uint32_t hv = fmix32((uint32_t)v ^ s);
+        const int64_t beg = rp[v], end = rp[v + 1];
+        int cnt = 0;
+        for (int64_t e = beg + lane; e < end; e += 32) {
+            const int32_t x = col[e];
+            cnt += prio_gt(fmix32((uint32_t)x ^ s), x, hv, (int32_t)v) ? 1 : 0;
+        }
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0) {
+            hash[v] = hv;
+            wait[v] = cnt;
+            color[v] = -1;
+            if (end - beg > COLOR_BIG_DEG) hub_slot[v] = (int32_t)atomicAdd(nhubs, 1u);
+            if (cnt == 0) push_ready((int32_t)v, rp, nl, nlc, nh, nhc);
+        }
+    }
+}
+
+// Colours of higher-priority neighbours falling in [base, base + 64).
+__device__ __forceinline__ unsigned long long window_bits(const int64_t *rp, const int32_t *col, const uint32_t *hash,
+                                                          const int32_t *color, int32_t v, uint32_t hv, int64_t e0,
+                                                          int64_t step, uint32_t base) {
+    unsigned long long b = 0;
+    for (int64_t e = rp[v] + e0; e < rp[v + 1]; e += step) {
+        const int32_t x = col[e];
+        if (prio_gt(hash[x], x, hv, v)) {
+            const uint32_t c = (uint32_t)color[x];
+            if (c >= base && c < base + 64) b |= 1ull << (c - base);
+        }
+    }
+    return b;
+}
+
+// One warp per frontier vertex (degree <= COLOR_BIG_DEG).
+__global__ void k_color_round_warp(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                   const uint32_t *__restrict__ hash, const int32_t *list,
+                                   const unsigned long long *count_in, int32_t *wait, int32_t *color, int32_t *nl,
+                                   unsigned long long *nlc, int32_t *nh, unsigned long long *nhc,
+                                   unsigned long long *done) {
     const int lane = threadIdx.x & 31;
     const int64_t count = (int64_t)*count_in;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < count; i += nwarps) {
         const int32_t v = list[i];
-        const uint64_t pv = prio[v];
+        const uint32_t hv = hash[v];
         const int64_t beg = rp[v], end = rp[v + 1];
-        bool is_max = true;
         unsigned long long bits = 0;
-        for (int64_t e0 = beg; e0 < end; e0 += 32) {
-            const int64_t e = e0 + lane;
-            if (e < end) {
-                const int32_t x = col[e];
-                const int64_t st = ((volatile int64_t *)state)[x];
-                const bool uncol = st < 0 || (int32_t)(st >> 32) == round;
-                if (uncol) {
-                    if (prio_gt(prio[x], x, pv, v)) is_max = false;
-                } else {
-                    const uint32_t c = (uint32_t)st;
-                    if (c < 64) bits |= 1ull << c;
-                }
+        for (int64_t e = beg + lane; e < end; e += 32) {
+            const int32_t x = col[e];
+            if (prio_gt(hash[x], x, hv, v)) {
+                const uint32_t c = (uint32_t)color[x];
+                if (c < 64) bits |= 1ull << c;
+            } else if (atomicSub(&wait[x], 1) == 1) {
+                push_ready(x, rp, nl, nlc, nh, nhc);
             }
-            if (__any_sync(0xffffffffu, !is_max)) { is_max = false; break; }
-        }
-        if (!is_max) {
-            if (lane == 0) next[atomicAdd(next_count, 1ull)] = v;
-            continue;
         }
         for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
-        uint32_t c;
-        if (bits != ~0ull) {
-            c = __ffsll((long long)~bits) - 1;
-        } else {
-            // all of 0..63 taken: scan further windows of 64 colours
-            uint32_t base = 64;
-            while (true) {
-                unsigned long long b2 = 0;
-                for (int64_t e = beg + lane; e < end; e += 32) {
-                    const int64_t st = state[col[e]];
-                    const uint32_t cc = (uint32_t)st;
-                    if (st >= 0 && cc >= base && cc < base + 64) b2 |= 1ull << (cc - base);
-                }
-                for (int o = 16; o > 0; o >>= 1) b2 |= __shfl_xor_sync(0xffffffffu, b2, o);
-                if (b2 != ~0ull) { c = base + __ffsll((long long)~b2) - 1; break; }
-                base += 64;
-            }
+        uint32_t base = 0;
+        while (bits == ~0ull) {
+            base += 64;
+            bits = window_bits(rp, col, hash, color, v, hv, lane, 32, base);
+            for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
         }
-        if (lane == 0) state[v] = ((int64_t)round << 32) | (int64_t)c;
+        if (lane == 0) {
+            color[v] = (int32_t)(base + __ffsll((long long)~bits) - 1);
+            atomicAdd(done, 1ull);
+        }
     }
 }
 
-__global__ void k_color_extract(const int64_t *state, int64_t n, int32_t *color, unsigned int *maxc) {
-    unsigned int m = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t c = (uint32_t)state[i];
-        color[i] = (int32_t)c;
-        m = max(m, c + 1);
+// Frontier hubs (degree > COLOR_BIG_DEG): each hub's adjacency is cut into
+// chunks of COLOR_CHUNK entries, and the (hub, chunk) items of the round are
+// spread over all blocks.  A chunk ORs the colours (< COLOR_BITS) of its
+// higher-priority neighbours into the hub's bitmap and releases its
+// lower-priority neighbours; the last chunk of a hub takes the first free
+// colour (scanning the adjacency for windows beyond COLOR_BITS if needed).
+constexpr int COLOR_CHUNK = 2048;
+constexpr int COLOR_BITS = 4096;
+constexpr int COLOR_WORDS = COLOR_BITS / 32;
+
+__global__ void k_color_round_hubs(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                   const uint32_t *__restrict__ hash, const int32_t *list,
+                                   const unsigned long long *count_in, const int32_t *hub_slot, uint32_t *bitmaps,
+                                   unsigned int *chunks_done, int32_t *wait, int32_t *color, int32_t *nl,
+                                   unsigned long long *nlc, int32_t *nh, unsigned long long *nhc,
+                                   unsigned long long *done) {
+    __shared__ uint32_t sbm[COLOR_WORDS];
+    __shared__ int s_last;
+    __shared__ unsigned long long sbits;
+    const int64_t count = (int64_t)*count_in;
+    int64_t item0 = 0;
+    for (int64_t i = 0; i < count; i++) {
+        const int32_t v = list[i];
+        const int64_t beg = rp[v], end = rp[v + 1];
+        const int64_t nch = (end - beg + COLOR_CHUNK - 1) / COLOR_CHUNK;
+        const uint32_t hv = hash[v];
+        const int32_t slot = hub_slot[v];
+        uint32_t *bm = bitmaps + (size_t)slot * COLOR_WORDS;
+        // items item0 .. item0 + nch - 1 belong to this hub
+        int64_t first = item0 + ((blockIdx.x - item0 % gridDim.x) + gridDim.x) % gridDim.x;
+        for (int64_t it = first; it < item0 + nch; it += gridDim.x) {
+            const int64_t j = it - item0;
+            for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock) sbm[w] = 0;
+            __syncthreads();
+            const int64_t cb = beg + j * COLOR_CHUNK, ce = min(end, cb + COLOR_CHUNK);
+            for (int64_t e = cb + threadIdx.x; e < ce; e += kBlock) {
+                const int32_t x = col[e];
+                if (prio_gt(hash[x], x, hv, v)) {
+                    const uint32_t c = (uint32_t)color[x];
+                    if (c < COLOR_BITS) atomicOr(&sbm[c >> 5], 1u << (c & 31));
+                } else if (atomicSub(&wait[x], 1) == 1) {
+                    push_ready(x, rp, nl, nlc, nh, nhc);
+                }
+            }
+            __syncthreads();
+            for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock)
+                if (sbm[w]) atomicOr(&bm[w], sbm[w]);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_last = atomicAdd(&chunks_done[slot], 1u) == (unsigned)(nch - 1);
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                // first zero bit of the bitmap
+                if (threadIdx.x == 0) sbits = ~0ull;
+                __syncthreads();
+                for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock) {
+                    const uint32_t word = __ldcg(bm + w);
+                    if (word != 0xffffffffu) atomicMin(&sbits, (unsigned long long)(w * 32 + __ffs(~word) - 1));
+                }
+                __syncthreads();
+                uint32_t c = (uint32_t)sbits;
+                if (sbits == ~0ull) {
+                    // every colour below COLOR_BITS is taken: scan windows of 64 above it
+                    uint32_t base = COLOR_BITS;
+                    while (true) {
+                        __syncthreads();
+                        if (threadIdx.x == 0) sbits = 0;
+                        __syncthreads();
+                        unsigned long long b = window_bits(rp, col, hash, color, v, hv, threadIdx.x, kBlock, base);
+                        for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
+                        if ((threadIdx.x & 31) == 0) atomicOr(&sbits, b);
+                        __syncthreads();
+                        const unsigned long long bits = sbits;
+                        if (bits != ~0ull) { c = base + __ffsll((long long)~bits) - 1; break; }
+                        base += 64;
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    color[v] = (int32_t)c;
+                    atomicAdd(done, 1ull);
+                }
+            }
+            __syncthreads();
+        }
+        item0 += nch;
     }
+}
+
+__global__ void k_color_max(const int32_t *color, int64_t n, unsigned int *maxc) {
+    unsigned int m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned int)color[i] + 1);
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(maxc, m);
 }
@@ -97,40 +213,52 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     if (g.n == 0) return 0;
     const uint32_t sw = seed_word(seed);
     constexpr int ROUNDS_PER_CHECK = 8;
-    DBuf<int64_t> state(g.n, s);
-    DBuf<uint64_t> prio(g.n, s);
-    CD_CUDA(cudaMemsetAsync(state.p, 0xff, g.n * sizeof(int64_t), s));
-    { k_color_prio<<<grid_for(g.n, kBlock, 152 * 32), kBlock, 0, s>>>(g.n, sw, prio.p); ::cd::note_launch(); }
-    DBuf<int32_t> la(g.n, s), lb(g.n, s);
-    iota32(la.p, g.n, s);
-    DBuf<unsigned long long> cnt(2, s);   // list lengths: [0] current, [1] next
-    const unsigned long long n0 = (unsigned long long)g.n;
-    CD_CUDA(cudaMemcpyAsync(cnt.p, &n0, sizeof(n0), cudaMemcpyHostToDevice, s));
+    DBuf<uint32_t> hash(g.n, s);
+    DBuf<int32_t> wait(g.n, s);
+    DBuf<int32_t> lists(4 * g.n, s);          // low / high frontier, current and next
+    DBuf<unsigned long long> cnt(5, s);       // [0,1] low, [2,3] high, [4] coloured
+    cnt.zero();
+    int32_t *L[2] = {lists.p, lists.p + g.n};
+    int32_t *H[2] = {lists.p + 2 * g.n, lists.p + 3 * g.n};
+    // every hub has more than COLOR_BIG_DEG entries
+    const int64_t max_hubs = g.nnz / (COLOR_BIG_DEG + 1) + 1;
+    DBuf<int32_t> hub_slot(g.n, s);
+    DBuf<uint32_t> bitmaps((size_t)max_hubs * COLOR_WORDS, s);
+    DBuf<unsigned int> chunks_done(max_hubs, s), nhubs(1, s);
+    bitmaps.zero();
+    chunks_done.zero();
+    nhubs.zero();
+    { k_color_init<<<grid_for(g.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(g.rp, g.col, g.n, sw, hash.p, wait.p, color,
+                                                                          L[0], cnt.p + 0, H[0], cnt.p + 2, hub_slot.p,
+                                                                          nhubs.p); ::cd::note_launch(); }
+    CD_LAUNCH_CHECK();
     Pinned h(sizeof(unsigned long long));
-    int64_t known = g.n;   // upper bound on the current list length
-    int32_t round = 0;
-    int which = 0;         // cnt[which] holds the current length
+    int cur = 0;
+    int64_t rounds = 0;
     while (true) {
         for (int r = 0; r < ROUNDS_PER_CHECK; r++) {
-            int32_t *cur = (round & 1) ? lb.p : la.p;
-            int32_t *nxt = (round & 1) ? la.p : lb.p;
-            CD_CUDA(cudaMemsetAsync(cnt.p + (1 - which), 0, sizeof(unsigned long long), s));
-            { k_color_round<<<grid_for(known * 32, kBlock, 152 * 64), kBlock, 0, s>>>(
-                  g.rp, g.col, prio.p, cur, cnt.p + which, round, state.p, nxt, cnt.p + (1 - which)); ::cd::note_launch(); }
+            const int nx = 1 - cur;
+            CD_CUDA(cudaMemsetAsync(cnt.p + nx, 0, sizeof(unsigned long long), s));
+            CD_CUDA(cudaMemsetAsync(cnt.p + 2 + nx, 0, sizeof(unsigned long long), s));
+            { k_color_round_warp<<<152 * 16, kBlock, 0, s>>>(g.rp, g.col, hash.p, L[cur], cnt.p + cur, wait.p, color,
+                                                           L[nx], cnt.p + nx, H[nx], cnt.p + 2 + nx, cnt.p + 4); ::cd::note_launch(); }
+            { k_color_round_hubs<<<152 * 4, kBlock, 0, s>>>(g.rp, g.col, hash.p, H[cur], cnt.p + 2 + cur, hub_slot.p,
+                                                          bitmaps.p, chunks_done.p, wait.p, color, L[nx], cnt.p + nx,
+                                                          H[nx], cnt.p + 2 + nx, cnt.p + 4); ::cd::note_launch(); }
             CD_LAUNCH_CHECK();
-            which = 1 - which;
-            round++;
+            cur = nx;
+            rounds++;
         }
-        CD_CUDA(cudaMemcpyAsync(h.p, cnt.p + which, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CD_CUDA(cudaMemcpyAsync(h.p, cnt.p + 4, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CD_CUDA(cudaStreamSynchronize(s));
-        const int64_t left = (int64_t)*h.as<unsigned long long>();
-        if (left == 0) break;
-        if (left >= known) raise(CD_ECUDA, "colouring made no progress by round %d", round);
-        known = left;
+        const int64_t coloured = (int64_t)*h.as<unsigned long long>();
+        if (coloured >= g.n) break;
+        // every round colours at least one vertex
+        if (rounds > g.n + 64) raise(CD_ECUDA, "colouring did not finish after %lld rounds", (long long)rounds);
     }
     DBuf<unsigned int> maxc(1, s);
     maxc.zero();
-    { k_color_extract<<<grid_for(g.n, kBlock, 152 * 32), kBlock, 0, s>>>(state.p, g.n, color, maxc.p); ::cd::note_launch(); }
+    { k_color_max<<<grid_for(g.n, kBlock, 152 * 32), kBlock, 0, s>>>(color, g.n, maxc.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     Pinned hm(sizeof(unsigned int));
     CD_CUDA(cudaMemcpyAsync(hm.p, maxc.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));

@@ -18,13 +18,6 @@ namespace cd {
 // modularity and the phase terminates.
 constexpr int RECHECK_FROM = 4;
 
-// PLP ties between dominant labels follow fmix32(label ^ salt), a seeded
-// pseudo-random order that changes every iteration ("ties arbitrarily",
-// Section III-A).
-static uint32_t plp_salt(uint64_t seed, int32_t it) {
-    return fmix32(seed_word(seed) ^ (0x9E3779B9u * (uint32_t)(it + 1)));
-}
-
 using Clock = std::chrono::steady_clock;
 static double ms_since(Clock::time_point t) {
     return std::chrono::duration<double, std::milli>(Clock::now() - t).count();
@@ -49,6 +42,9 @@ struct Schedule {
     DBuf<int64_t> part_g, part_g2, part_w;
     DBuf<int32_t> part_id;
     DBuf<uint32_t> part_tk;
+    // class metadata on the device (persistent kernels)
+    DBuf<int64_t> d_off;
+    DBuf<int32_t> d_hub0, d_nb1, d_nb2;
 };
 
 __global__ void k_sched_keys(const int64_t *rp, int64_t n, const int32_t *color, int32_t ncol, uint32_t *key,
@@ -80,6 +76,21 @@ static int bits_for(int64_t x) {
     int b = 1;
     while (((int64_t)1 << b) < x) b++;
     return b;
+}
+
+static void upload_class_meta(Schedule &S, cudaStream_t s) {
+    S.d_off.alloc(S.off.size(), s);
+    S.d_hub0.alloc(S.hub_start.size(), s);
+    S.d_nb1.alloc(S.ncol + 1, s);
+    S.d_nb2.alloc(S.ncol + 1, s);
+    CD_CUDA(cudaMemcpyAsync(S.d_off.p, S.off.data(), S.off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CD_CUDA(cudaMemcpyAsync(S.d_hub0.p, S.hub_start.data(), S.hub_start.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+    if (S.ncol) {
+        CD_CUDA(cudaMemcpyAsync(S.d_nb1.p, S.nb1.data(), S.ncol * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CD_CUDA(cudaMemcpyAsync(S.d_nb2.p, S.nb2.data(), S.ncol * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    CD_CUDA(cudaStreamSynchronize(s));   // the host vectors may change after return
 }
 
 static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaStream_t s) {
@@ -115,7 +126,10 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     S.hub_start[S.ncol] = (int32_t)H;
     S.nhubs = H;
     S.max_tab = S.max_nb2 = 0;
-    if (H == 0) return;
+    if (H == 0) {
+        upload_class_meta(S, s);
+        return;
+    }
     std::vector<int32_t> hv(H);
     std::vector<int64_t> hd(H);
     {
@@ -182,30 +196,8 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     S.part_w.alloc(S.max_nb2, s);
     S.part_id.alloc(S.max_nb2, s);
     S.part_tk.alloc(S.max_nb2, s);
+    upload_class_meta(S, s);
     CD_CUDA(cudaStreamSynchronize(s));   // host vectors above go out of scope
-}
-
-static void fill_class(const Schedule &S, int32_t k, SweepCtx &c, ClassBins &cb) {
-    const int64_t a = S.off[(int64_t)k * NBINS];
-    cb.order = S.order.p + a;
-    for (int b = 0; b <= NBINS; b++) cb.off[b] = S.off[(int64_t)k * NBINS + b] - a;
-    cb.nb1 = S.nb1[k];
-    cb.nb2 = S.nb2[k];
-    const int32_t h0 = S.hub_start[k];
-    c.nhubs = S.hub_start[k + 1] - h0;
-    c.hubs = S.hubs.p + h0;
-    c.hub_b1 = S.hb1.p + h0;
-    c.hub_b2 = S.hb2.p + h0;
-    c.hub_keys = S.hub_keys.p;
-    c.hub_vals = S.hub_vals.p;
-    c.hub_wc = S.hub_wc.p + h0;
-    c.hub_done1 = S.done1.p + h0;
-    c.hub_done2 = S.done2.p + h0;
-    c.part_g = S.part_g.p;
-    c.part_g2 = S.part_g2.p;
-    c.part_w = S.part_w.p;
-    c.part_id = S.part_id.p;
-    c.part_tk = S.part_tk.p;
 }
 
 static int wbytes(int wk) { return wk == W_UNIT ? 0 : wk == W_I32 ? 4 : 8; }
@@ -213,70 +205,120 @@ static int wbytes(int wk) { return wk == W_UNIT ? 0 : wk == W_I32 ? 4 : 8; }
 // ---------------------------------------------------------------------------
 // Move phase (Algorithm 2) under the colour-class schedule.
 // ---------------------------------------------------------------------------
+// Arguments shared by the persistent kernels: graph, schedule, hub tables.
+static PhaseArgs phase_args(const GraphView &g, const Schedule &S, int32_t *zeta) {
+    PhaseArgs a{};
+    a.g = g;
+    a.zeta = zeta;
+    a.order = S.order.p;
+    a.ncol = S.ncol;
+    a.class_off = S.d_off.p;
+    a.class_hub0 = S.d_hub0.p;
+    a.class_nb1 = S.d_nb1.p;
+    a.class_nb2 = S.d_nb2.p;
+    a.hubs = S.hubs.p;
+    a.hb1 = S.hb1.p;
+    a.hb2 = S.hb2.p;
+    a.hub_keys = S.hub_keys.p;
+    a.hub_vals = S.hub_vals.p;
+    a.hub_wc = S.hub_wc.p;
+    a.done1 = S.done1.p;
+    a.done2 = S.done2.p;
+    a.part_g = S.part_g.p;
+    a.part_g2 = S.part_g2.p;
+    a.part_w = S.part_w.p;
+    a.part_id = S.part_id.p;
+    a.part_tk = S.part_tk.p;
+    return a;
+}
+
+// Reads a persistent run's result words and per-sweep counters.
+static int32_t finish_phase(const DBuf<int32_t> &result, const DBuf<Counters> &cnt, const DBuf<GridBarrier> &bar,
+                            int32_t *conv, std::vector<Counters> &per, cudaStream_t s) {
+    Pinned hr(4 * sizeof(int32_t) + sizeof(GridBarrier));
+    CD_CUDA(cudaMemcpyAsync(hr.p, result.p, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaMemcpyAsync(hr.as<char>() + 4 * sizeof(int32_t), bar.p, sizeof(GridBarrier), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaStreamSynchronize(s));
+    const GridBarrier *hb = reinterpret_cast<const GridBarrier *>(hr.as<char>() + 4 * sizeof(int32_t));
+    if (hb->err) raise(CD_ETIMEOUT, "a grid barrier of the persistent kernel timed out");
+    const int32_t runs = hr.as<int32_t>()[0];
+    *conv = hr.as<int32_t>()[1];
+    per.resize(runs);
+    if (runs) CD_CUDA(cudaMemcpyAsync(per.data(), cnt.p, runs * sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaStreamSynchronize(s));
+    for (const Counters &c : per)
+        if (c.overflow) raise(CD_ECUDA, "internal hash table overflow (%llu failed inserts)", c.overflow);
+    return runs;
+}
+
+// ---------------------------------------------------------------------------
+// Move phase (Algorithm 2) under the colour-class schedule: one persistent
+// launch.  volc holds the community volumes of zeta on entry.
+// ---------------------------------------------------------------------------
 static int64_t move_phase(const GraphView &g, const Schedule &S, int32_t *zeta, int64_t *volc, const RunOpts &o,
                           RunStats &st, LaunchTimer &timer, cudaStream_t s) {
     const bool big = needs_big(g.W);
+    const int64_t ncol = S.ncol;
     DBuf<int32_t> mv_u(g.n, s), mv_c(g.n, s), cd_(g.n, s);
-    DBuf<int64_t> cwd(g.n, s), cwc(g.n, s);
+    DBuf<int64_t> cwd(g.n, s), cwc(g.n, s), volb(g.n, s);
     DBuf<uint64_t> tmp_a(g.n, s), tmp_b(g.n, s);
-    DBuf<unsigned long long> nmv(S.ncol, s), ncand(S.ncol, s);
-    DBuf<Counters> cnt(1, s);
-    Pinned hc(sizeof(Counters));
+    DBuf<unsigned long long> nmv(2 * ncol + 1, s), ncand(ncol + 1, s);
+    DBuf<Counters> cnt(o.max_sweeps, s);
+    DBuf<GridBarrier> bar(1, s);
+    DBuf<int32_t> result(4, s);
+    cnt.zero();
+    bar.zero();
+    result.zero();
+    nmv.zero();
+    if (g.n) CD_CUDA(cudaMemcpyAsync(volb.p, volc, g.n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    PhaseArgs a = phase_args(g, S, zeta);
+    a.cnt = cnt.p;
+    a.bar = bar.p;
+    a.result = result.p;
+    a.vol_a = volc;
+    a.vol_b = volb.p;
+    a.mv_u = mv_u.p;
+    a.mv_c = mv_c.p;
+    a.cd = cd_.p;
+    a.cwd = cwd.p;
+    a.cwc = cwc.p;
+    a.nmv = nmv.p;
+    a.ncand = ncand.p;
+    a.tmp_a = tmp_a.p;
+    a.tmp_b = tmp_b.p;
     int ubits = 1;
     while (((int64_t)1 << ubits) < g.n) ubits++;
+    a.ubits = ubits;
+    a.max_sweeps = o.max_sweeps;
+    a.recheck_from = RECHECK_FROM;
+    DBuf<unsigned long long> stage(3, s);
+    stage.zero();
+    if (timer.on) a.stage_ns = stage.p;
+    timer.before(s);
+    launch_move_phase(g.wk, big, a, s);
+    timer.after(s);
+    int32_t conv = 0;
+    std::vector<Counters> per;
+    const int32_t sweeps = finish_phase(result, cnt, bar, &conv, per, s);
     int64_t total = 0;
-    for (int32_t sw = 0; sw < o.max_sweeps; sw++) {
-        cnt.zero();
-        nmv.zero();
-        ncand.zero();
-        SweepCtx c{};
-        c.g = g;
-        c.zeta = zeta;
-        c.volc = volc;
-        c.cnt = cnt.p;
-        c.late = sw >= RECHECK_FROM;
-        for (int32_t k = 0; k < S.ncol; k++) {
-            const int64_t a = S.off[(int64_t)k * NBINS], e = S.off[(int64_t)k * NBINS + NBINS];
-            if (e == a) continue;
-            ClassBins cb;
-            fill_class(S, k, c, cb);
-            c.mv_u = mv_u.p + a;
-            c.mv_c = mv_c.p + a;
-            c.nmv = nmv.p + k;
-            // candidate records reuse the move-record buffers (one or the other per sweep)
-            c.cand_u = mv_u.p + a;
-            c.cand_c = mv_c.p + a;
-            c.cand_d = cd_.p + a;
-            c.cand_wd = cwd.p + a;
-            c.cand_wc = cwc.p + a;
-            c.ncand = ncand.p + k;
-            decide_class<false>(g.wk, big, c, cb, s, timer);
-            if (!c.late) {
-                { k_apply_moves<<<grid_for(e - a, kBlock, 152 * 8), kBlock, 0, s>>>(mv_u.p + a, mv_c.p + a, nmv.p + k, zeta,
-                                                                                 g.vol, volc); ::cd::note_launch(); }
-                CD_LAUNCH_CHECK();
-            } else {
-                RecheckArgs ra{c.cand_u, c.cand_c, c.cand_d, c.cand_wd, c.cand_wc, c.ncand, zeta, g.vol, volc,
-                               2 * g.W, tmp_a.p, tmp_b.p, ubits, cnt.p};
-                recheck_class(big, ra, s);
-            }
-        }
-        CD_CUDA(cudaMemcpyAsync(hc.p, cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-        CD_CUDA(cudaStreamSynchronize(s));
-        const Counters h = *hc.as<Counters>();
+    for (const Counters &h : per) {
         st.sweeps++;
         st.moves += h.moved;
         st.entries += h.entries;
         st.candidates += h.candidates;
         st.decisions += h.decisions;
-        if (timer.on) {
-            st.k_ms += timer.collect_ms();
-            st.k_bytes += 40.0 * h.decisions + (8.0 + wbytes(g.wk)) * h.entries + 8.0 * h.candidates + 12.0 * h.moved;
-        }
         total += h.moved;
-        if (h.wanted == 0) return total;
+        if (timer.on)
+            st.k_bytes += 40.0 * h.decisions + (8.0 + wbytes(g.wk)) * h.entries + 8.0 * h.candidates + 12.0 * h.moved;
     }
-    st.converged = 0;
+    if (timer.on) {
+        st.k_ms += timer.collect_ms();
+        unsigned long long ns[3];
+        CD_CUDA(cudaMemcpy(ns, stage.p, sizeof(ns), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < 3; i++) st.stage_ms[i] += ns[i] * 1e-6;
+    }
+    if (!conv) st.converged = 0;
+    (void)sweeps;
     return total;
 }
 
@@ -365,42 +407,38 @@ static void plp_iterate(const GraphView &g, const Schedule &S, const RunOpts &o,
     DBuf<uint8_t> active(g.n, s);
     if (g.n) CD_CUDA(cudaMemsetAsync(active.p, 1, g.n, s));
     iota32(zeta, g.n, s);
-    DBuf<Counters> cnt(1, s);
-    Pinned hc(sizeof(Counters));
-    int64_t updated = g.n;
-    int32_t it = 0;
+    DBuf<Counters> cnt(o.max_iters + 1, s);
+    DBuf<GridBarrier> bar(1, s);
+    DBuf<int32_t> result(4, s);
+    cnt.zero();
+    bar.zero();
+    result.zero();
+    PhaseArgs a = phase_args(g, S, zeta);
+    a.cnt = cnt.p;
+    a.bar = bar.p;
+    a.result = result.p;
+    a.active = active.p;
+    a.seed = o.seed;
+    a.theta = theta;
+    a.max_iters = o.max_iters;
+    timer.before(s);
+    launch_plp_run(g.wk, big, a, s);
+    timer.after(s);
+    int32_t conv = 0;
+    std::vector<Counters> per;
+    const int32_t iters = finish_phase(result, cnt, bar, &conv, per, s);
     const int64_t listed = S.off[(int64_t)S.ncol * NBINS];
-    while ((double)updated > theta && it < o.max_iters) {
-        cnt.zero();
-        SweepCtx c{};
-        c.g = g;
-        c.zeta = zeta;
-        c.cnt = cnt.p;
-        c.active = active.p;
-        c.tie_salt = plp_salt(o.seed, it);
-        for (int32_t k = 0; k < S.ncol; k++) {
-            const int64_t a = S.off[(int64_t)k * NBINS], e = S.off[(int64_t)k * NBINS + NBINS];
-            if (e == a) continue;
-            ClassBins cb;
-            fill_class(S, k, c, cb);
-            decide_class<true>(g.wk, big, c, cb, s, timer);
-        }
-        CD_CUDA(cudaMemcpyAsync(hc.p, cnt.p, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-        CD_CUDA(cudaStreamSynchronize(s));
-        const Counters h = *hc.as<Counters>();
-        updated = (int64_t)h.moved;
+    for (const Counters &h : per) {
         st.moves += h.moved;
         st.entries += h.entries;
         st.candidates += h.candidates;
         st.decisions += h.decisions;
-        if (timer.on) {
-            st.k_ms += timer.collect_ms();
+        if (timer.on)
             st.k_bytes += 5.0 * listed + 20.0 * h.decisions + (8.0 + wbytes(g.wk)) * h.entries + 4.0 * h.moved;
-        }
-        it++;
     }
-    st.iters += it;
-    if ((double)updated > theta) st.converged = 0;
+    if (timer.on) st.k_ms += timer.collect_ms();
+    st.iters += iters;
+    if (!conv) st.converged = 0;
 }
 
 void run_plp(const GraphView &g, const RunOpts &o, double theta, int32_t *labels, RunStats &st, cudaStream_t s) {
@@ -510,6 +548,7 @@ void run_epp(const GraphView &g, int b, bool final_refine, const RunOpts &o, dou
     st.k_ms += sf.k_ms;
     st.k_bytes += sf.k_bytes;
     st.k_launches += sf.k_launches;
+    for (int i = 0; i < 3; i++) st.stage_ms[i] += sf.stage_ms[i];
     st.ms_color += sf.ms_color;
     st.ms_move += sf.ms_move;
     st.ms_coarsen += sf.ms_coarsen;

@@ -1,18 +1,17 @@
-// PLP decide kernels (Algorithm 1).
+// PLP (Algorithm 1): persistent kernel instantiations.
 #include "move_dispatch.cuh"
 
 namespace cd {
 
-template <>
-void decide_class<true>(int wk, bool big, const SweepCtx &c, const ClassBins &cb, cudaStream_t s, LaunchTimer &t) {
+void launch_plp_run(int wk, bool big, const PhaseArgs &a, cudaStream_t s) {
     if (!big) {
-        if (wk == W_UNIT) decide_class_t<W_UNIT, false, true>(c, cb, s, t);
-        else if (wk == W_I32) decide_class_t<W_I32, false, true>(c, cb, s, t);
+        if (wk == W_UNIT) launch_persistent((const void *)k_plp_run<W_UNIT, false>, a, s);
+        else if (wk == W_I32) launch_persistent((const void *)k_plp_run<W_I32, false>, a, s);
         else raise(CD_ECUDA, "int64 weights need the 128-bit path");
     } else {
-        if (wk == W_UNIT) decide_class_t<W_UNIT, true, true>(c, cb, s, t);
-        else if (wk == W_I32) decide_class_t<W_I32, true, true>(c, cb, s, t);
-        else decide_class_t<W_I64, true, true>(c, cb, s, t);
+        if (wk == W_UNIT) launch_persistent((const void *)k_plp_run<W_UNIT, true>, a, s);
+        else if (wk == W_I32) launch_persistent((const void *)k_plp_run<W_I32, true>, a, s);
+        else launch_persistent((const void *)k_plp_run<W_I64, true>, a, s);
     }
 }
 

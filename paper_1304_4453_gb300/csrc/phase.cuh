@@ -1,0 +1,597 @@
+// Persistent kernels: one cooperative launch runs a whole PLM move phase
+// (every sweep, every colour class) or a whole PLP run (every iteration).
+// Colour classes follow each other in order, separated by grid barriers;
+// inside a class, blocks take work items (group / block / hub roles, then
+// hub-decide slices) in a grid-stride loop.  Late PLM sweeps end each class
+// with the sequential re-check, done by block 0 between two barriers.
+//
+// The grid barrier is a generation counter; a block that waits longer than
+// BARRIER_TIMEOUT_NS sets an error flag and every block leaves the kernel,
+// which the host reports as CD_ETIMEOUT.
+#pragma once
+#include "move_kernels.cuh"
+
+namespace cd {
+
+constexpr int PHASE_SMEM = 32768;          // dynamic shared memory per block
+constexpr int RC_SMALL = 4096;             // candidates sorted in shared memory
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 20ull * 1000 * 1000 * 1000;
+
+// Two-level arrival tree: block b arrives at sub-counter b / 32; the last
+// arrival of a sub-counter arrives at the root; the last root arrival opens
+// the next generation.  Every counter is reset by its last arrival before
+// the generation changes, so the next barrier starts from zero.
+constexpr int BARRIER_FAN = 32;
+constexpr int BARRIER_SUBS = 64;           // up to 2048 blocks
+struct GridBarrier {
+    unsigned int gen;
+    int err;
+    unsigned int root;
+    unsigned int pad;
+    unsigned int sub[BARRIER_SUBS];
+};
+
+struct PhaseArgs {
+    GraphView g;
+    int32_t *zeta;
+    const int32_t *order;
+    int32_t ncol;
+    const int64_t *class_off;              // [ncol * NBINS + 1]
+    const int32_t *class_hub0;             // [ncol + 1]
+    const int32_t *class_nb1, *class_nb2;  // [ncol]
+    const HubInfo *hubs;
+    const int32_t *hb1, *hb2;
+    int32_t *hub_keys;
+    void *hub_vals, *hub_wc;
+    unsigned int *done1, *done2;
+    int64_t *part_g, *part_g2, *part_w;
+    int32_t *part_id;
+    uint32_t *part_tk;
+    Counters *cnt;                         // one per sweep / iteration
+    GridBarrier *bar;
+    int32_t *result;                       // [0] sweeps / iterations run, [1] converged
+    // PLM
+    int64_t *vol_a, *vol_b;                // launch t reads vol[t & 1], writes vol[(t+1) & 1]
+    int32_t *mv_u, *mv_c, *cd;
+    int64_t *cwd, *cwc;
+    unsigned long long *nmv;               // [2][ncol]
+    unsigned long long *ncand;             // [ncol]
+    uint64_t *tmp_a, *tmp_b;
+    int32_t ubits;
+    int32_t max_sweeps, recheck_from;
+    // PLP
+    uint8_t *active;
+    uint64_t seed;
+    double theta;
+    int32_t max_iters;
+    // profile mode: block 0 adds the wall time of each class stage (ns):
+    // [0] items (+ barrier), [1] hub decide (+ barrier), [2] re-check (+ barrier)
+    unsigned long long *stage_ns;
+};
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Returns false when the barrier failed (timeout here or in another block).
+__device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned *s_gen, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g = *s_gen;
+        int ok = 1;
+        __threadfence();
+        const unsigned sb = blockIdx.x / BARRIER_FAN;
+        const unsigned nsub = (gridDim.x + BARRIER_FAN - 1) / BARRIER_FAN;
+        const unsigned sub_size = min((unsigned)BARRIER_FAN, gridDim.x - sb * BARRIER_FAN);
+        bool opener = false;
+        if (atomicAdd(&b->sub[sb], 1u) == sub_size - 1) {
+            atomicExch(&b->sub[sb], 0u);
+            __threadfence();
+            if (atomicAdd(&b->root, 1u) == nsub - 1) {
+                atomicExch(&b->root, 0u);
+                __threadfence();
+                atomicExch(&b->gen, g + 1);
+                opener = true;
+            }
+        }
+        if (!opener) {
+            const uint64_t t0 = global_ns();
+            while (*(volatile unsigned *)&b->gen == g) {
+                if (*(volatile int *)&b->err != 0) { ok = 0; break; }
+                if (global_ns() - t0 > BARRIER_TIMEOUT_NS) { atomicExch(&b->err, 1); ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        *s_gen = g + 1;
+        *s_ok = ok && *(volatile int *)&b->err == 0;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// SweepCtx of class k (layout, roles, hubs).
+__device__ __forceinline__ int32_t class_ctx(const PhaseArgs &a, int32_t k, SweepCtx &c) {
+    const int64_t base = a.class_off[(int64_t)k * NBINS];
+    c.order = a.order + base;
+    for (int b = 0; b <= NBINS; b++) c.off[b] = a.class_off[(int64_t)k * NBINS + b] - base;
+    const int32_t h0 = a.class_hub0[k];
+    c.nhubs = a.class_hub0[k + 1] - h0;
+    c.hubs = a.hubs + h0;
+    c.hub_b1 = a.hb1 + h0;
+    c.hub_b2 = a.hb2 + h0;
+    c.hub_keys = a.hub_keys;
+    c.hub_vals = a.hub_vals;
+    c.hub_wc = static_cast<char *>(a.hub_wc) + (size_t)h0 * 8;
+    c.hub_done1 = a.done1 + h0;
+    c.hub_done2 = a.done2 + h0;
+    c.part_g = a.part_g;
+    c.part_g2 = a.part_g2;
+    c.part_w = a.part_w;
+    c.part_id = a.part_id;
+    c.part_tk = a.part_tk;
+    const int64_t n0 = c.off[1] - c.off[0], n1 = c.off[2] - c.off[1], n2 = c.off[3] - c.off[2];
+    const int64_t n3 = c.off[4] - c.off[3];
+    c.bend[0] = (int32_t)((n0 + kBlock / 4 - 1) / (kBlock / 4));
+    c.bend[1] = c.bend[0] + (int32_t)((n1 + kBlock / 8 - 1) / (kBlock / 8));
+    c.bend[2] = c.bend[1] + (int32_t)((n2 + kBlock / 32 - 1) / (kBlock / 32));
+    c.bend[3] = c.bend[2] + (int32_t)n3;
+    c.bend[4] = c.bend[3] + a.class_nb1[k];
+    return a.class_nb2[k];
+}
+
+template <int WK, bool BIG, bool PLP>
+__device__ __forceinline__ void run_item(const SweepCtx &c, int32_t b, unsigned char *smem,
+                                         typename BestOf<PLP, BIG>::T *s_best, unsigned *s_cand, int *s_last) {
+    if (b < c.bend[0]) role_group<4, 4, WK, BIG, PLP>(c, b, c.order + c.off[0], c.off[1] - c.off[0], smem);
+    else if (b < c.bend[1]) role_group<8, 16, WK, BIG, PLP>(c, b - c.bend[0], c.order + c.off[1], c.off[2] - c.off[1], smem);
+    else if (b < c.bend[2]) role_group<32, 128, WK, BIG, PLP>(c, b - c.bend[1], c.order + c.off[2], c.off[3] - c.off[2], smem);
+    else if (b < c.bend[3]) role_block<WK, BIG, PLP>(c, b - c.bend[2], c.order + c.off[3], smem, s_best, s_cand);
+    else role_hub_aggregate<WK, BIG, PLP>(c, b - c.bend[3], smem, s_last);
+}
+
+// Hub decide: slice `item` of a hub table; the last slice of a hub decides.
+template <int WK, bool BIG, bool PLP>
+__device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item, typename BestOf<PLP, BIG>::T *s_best,
+                                                unsigned *s_cand, int *s_last) {
+    using VT = ValT<BIG>;
+    using BT = typename BestOf<PLP, BIG>::T;
+    const int h = find_hub(c.hub_b2, c.nhubs, item);
+    const HubInfo hi = c.hubs[h];
+    const int32_t u = hi.v;
+    if constexpr (PLP) {
+        if (!c.active[u]) return;
+    }
+    const int j = item - c.hub_b2[h];
+    int32_t *gk = c.hub_keys + hi.tab;
+    VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
+    const int64_t s0 = (int64_t)j * HUB_SCAN, s1 = min(hi.slots, s0 + HUB_SCAN);
+    const int32_t C = c.zeta[u];
+    const int64_t wC = (int64_t)static_cast<const VT *>(c.hub_wc)[h];
+    if (threadIdx.x == 0) *s_cand = 0;
+    __syncthreads();
+    unsigned ncand = 0;
+    BT b;
+    b.init();
+    if constexpr (!PLP) {
+        const int64_t vu = c.g.vol[u], volC = c.volc[C], twoW = 2 * c.g.W;
+        for (int64_t s = s0 + threadIdx.x; s < s1; s += kBlock) {
+            const int32_t key = gk[s];
+            if (key >= 0) {
+                ncand++;
+                if (key != C) b.offer(plm_gain<BIG>(twoW, (int64_t)gv[s], wC, vu, c.volc[key], volC), key, (int64_t)gv[s]);
+                gk[s] = -1;
+                gv[s] = 0;
+            }
+        }
+    } else {
+        for (int64_t s = s0 + threadIdx.x; s < s1; s += kBlock) {
+            const int32_t key = gk[s];
+            if (key >= 0) {
+                ncand++;
+                b.offer((int64_t)gv[s], fmix32((uint32_t)key ^ c.tie_salt), key);
+                gk[s] = -1;
+                gv[s] = 0;
+            }
+        }
+    }
+    ncand = __reduce_add_sync(0xffffffffu, ncand);
+    if ((threadIdx.x & 31) == 0) atomicAdd(s_cand, ncand);
+    b = block_best(b, s_best);
+    if (threadIdx.x == 0) {
+        if constexpr (!PLP) {
+            if constexpr (BIG) {
+                c.part_g[item] = (int64_t)(uint64_t)b.g;
+                c.part_g2[item] = (int64_t)(b.g >> 64);
+            } else {
+                c.part_g[item] = b.g;
+            }
+            c.part_w[item] = b.w;
+        } else {
+            c.part_g[item] = b.w;
+            c.part_tk[item] = b.tk;
+        }
+        c.part_id[item] = b.id;
+        atomicAdd(&c.cnt->candidates, (unsigned long long)*s_cand);
+        __threadfence();
+        const unsigned done = atomicAdd(&c.hub_done2[h], 1u);
+        *s_last = (done == (unsigned)hi.nb2 - 1);
+    }
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();
+    {   // merge the partial bests of every slice of this hub
+        BT r;
+        r.init();
+        const int64_t p0 = c.hub_b2[h];
+        for (int k = threadIdx.x; k < hi.nb2; k += kBlock) {
+            BT o;
+            o.id = __ldcg(c.part_id + p0 + k);
+            if constexpr (!PLP) {
+                if constexpr (BIG) {
+                    const uint64_t lo = (uint64_t)__ldcg(c.part_g + p0 + k);
+                    const uint64_t hi2 = (uint64_t)__ldcg(c.part_g2 + p0 + k);
+                    o.g = (__int128)(((unsigned __int128)hi2 << 64) | lo);
+                } else {
+                    o.g = __ldcg(c.part_g + p0 + k);
+                }
+                o.w = __ldcg(c.part_w + p0 + k);
+            } else {
+                o.w = __ldcg(c.part_g + p0 + k);
+                o.tk = __ldcg(c.part_tk + p0 + k);
+            }
+            r.merge(o);
+        }
+        b = block_best(r, s_best);
+    }
+    if (threadIdx.x == 0) {
+        c.hub_done2[h] = 0;
+        const BT r = b;
+        if constexpr (!PLP) {
+            const bool want = r.id >= 0 && r.g > 0;
+            if (want) take_move(c, atomicAdd(c.late ? c.ncand : c.nmv, 1ull), u, C, r.id, r.w, wC);
+            atomicAdd(&c.cnt->wanted, (unsigned long long)want);
+            atomicAdd(&c.cnt->moved, (unsigned long long)(want && !c.late));
+            *s_last = 1;
+        } else {
+            const bool adopt = r.id >= 0 && r.w > wC;
+            if (adopt) c.zeta[u] = r.id;
+            else c.active[u] = 0;
+            atomicAdd(&c.cnt->moved, (unsigned long long)adopt);
+            *s_last = adopt ? 2 : 1;
+        }
+        atomicAdd(&c.cnt->decisions, 1ull);
+    }
+    __syncthreads();
+    if constexpr (PLP) {
+        if (*s_last == 2) {
+            const int64_t rb = c.g.rp[u], re = c.g.rp[u + 1];
+            for (int64_t e = rb + threadIdx.x; e < re; e += kBlock) c.active[c.g.col[e]] = 1;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Sequential re-check of one class's wanted moves, by one block.  The
+// candidates are sorted by vertex id (bitonic sort in shared memory, or a
+// block-wide LSD radix sort in global scratch for long lists); then warp 0
+// walks them in windows of 32: lane k recomputes its gain with the volumes
+// of its source and target as updated by every move accepted before it, and
+// every later lane of the window adjusts its copies of the volumes it shares
+// with an accepted move.  Accepted moves update zeta and the volumes before
+// the next window loads its volumes.
+// ---------------------------------------------------------------------------
+struct RecheckArgs {
+    const int32_t *cu, *cc, *cd;
+    const int64_t *cwd, *cwc;
+    const unsigned long long *ncand;
+    int32_t *zeta;
+    const int64_t *vol;
+    int64_t *volc;
+    int64_t twoW;
+    uint64_t *tmp_a, *tmp_b;   // class-sized scratch for long candidate lists
+    int ubits;                 // bits of the largest vertex id
+    Counters *cnt;
+};
+
+__device__ __forceinline__ void rc_radix_pass(const uint64_t *in, uint64_t *out, int64_t m, int shift,
+                                              unsigned char *smem) {
+    constexpr int NW = kBlock / 32;
+    uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem);                          // [NW][256]
+    int64_t *base = reinterpret_cast<int64_t *>(smem + NW * 256 * 4);            // [256]
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + NW * 256 * 4 + 256 * 8);  // [256]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 256) hist[tid] = 0;
+    for (int j = tid; j < NW * 256; j += kBlock) wcnt[j] = 0;
+    __syncthreads();
+    for (int64_t i = tid; i < m; i += kBlock) atomicAdd(&hist[(uint32_t)(in[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    if (tid == 0) {
+        int64_t run = 0;
+        for (int d = 0; d < 256; d++) { base[d] = run; run += hist[d]; }
+    }
+    __syncthreads();
+    for (int64_t r = 0; r < m; r += kBlock) {
+        const int64_t i = r + tid;
+        const bool valid = i < m;
+        const uint64_t k = valid ? in[i] : 0;
+        const uint32_t d = valid ? ((uint32_t)(k >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[warp * 256 + d] = __popc(peers);
+        __syncthreads();
+        uint32_t run = 0;
+        for (int j = 0; j < NW; j++) {
+            const uint32_t cc = wcnt[j * 256 + tid];
+            wcnt[j * 256 + tid] = run;
+            run += cc;
+        }
+        __syncthreads();
+        if (valid) out[base[d] + wcnt[warp * 256 + d] + rank] = k;
+        __syncthreads();
+        base[tid] += run;
+        for (int j = 0; j < NW; j++) wcnt[j * 256 + tid] = 0;
+        __syncthreads();
+    }
+}
+
+template <bool BIG>
+__device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *smem) {
+    const int64_t m = (int64_t)__ldcg(a.ncand);
+    if (m == 0) return;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint64_t *keys;
+    if (m <= RC_SMALL) {
+        uint64_t *sk = reinterpret_cast<uint64_t *>(smem);
+        int P = 1;
+        while (P < m) P <<= 1;
+        for (int i = tid; i < P; i += kBlock)
+            sk[i] = i < m ? (((uint64_t)(uint32_t)__ldcg(a.cu + i) << 32) | (uint32_t)i) : ~0ull;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < P; i += kBlock) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const bool up = (i & k) == 0;
+                        const uint64_t x = sk[i], y = sk[ixj];
+                        if ((x > y) == up) { sk[i] = y; sk[ixj] = x; }
+                    }
+                }
+                __syncthreads();
+            }
+        keys = sk;
+    } else {
+        for (int64_t i = tid; i < m; i += kBlock)
+            a.tmp_a[i] = ((uint64_t)(uint32_t)__ldcg(a.cu + i) << 32) | (uint32_t)i;
+        __syncthreads();
+        uint64_t *src = a.tmp_a, *dst = a.tmp_b;
+        for (int shift = 32; shift < 32 + a.ubits; shift += 8) {
+            rc_radix_pass(src, dst, m, shift, smem);
+            uint64_t *t = src;
+            src = dst;
+            dst = t;
+        }
+        __syncthreads();
+        keys = src;
+    }
+    if (tid < 32) {
+        unsigned long long moved = 0;
+        for (int64_t w0 = 0; w0 < m; w0 += 32) {
+            const int64_t i = w0 + lane;
+            const bool valid = i < m;
+            const uint32_t ci = valid ? (uint32_t)(keys[i] & 0xffffffffull) : 0u;
+            const int32_t u = valid ? __ldcg(a.cu + ci) : 0;
+            const int32_t C = valid ? __ldcg(a.cc + ci) : -1;
+            const int32_t D = valid ? __ldcg(a.cd + ci) : -2;
+            const int64_t vu = valid ? a.vol[u] : 0;
+            const int64_t wD = valid ? __ldcg(a.cwd + ci) : 0, wC = valid ? __ldcg(a.cwc + ci) : 0;
+            int64_t volC = valid ? __ldcg(a.volc + C) : 0;
+            int64_t volD = valid ? __ldcg(a.volc + D) : 0;
+            bool mine = false;
+            const int cnt = (m - w0) < 32 ? (int)(m - w0) : 32;
+            for (int k = 0; k < cnt; k++) {
+                int acc = 0;
+                if (lane == k) acc = plm_gain<BIG>(a.twoW, wD, wC, vu, volD, volC) > 0;
+                acc = __shfl_sync(0xffffffffu, acc, k);
+                if (acc) {
+                    const int32_t Ck = __shfl_sync(0xffffffffu, C, k), Dk = __shfl_sync(0xffffffffu, D, k);
+                    const int64_t vk = __shfl_sync(0xffffffffu, vu, k);
+                    if (lane == k) {
+                        mine = true;
+                    } else if (lane > k) {
+                        if (C == Ck) volC -= vk; else if (C == Dk) volC += vk;
+                        if (D == Ck) volD -= vk; else if (D == Dk) volD += vk;
+                    }
+                }
+            }
+            if (valid && mine) {
+                a.zeta[u] = D;
+                vol_add(a.volc, C, -vu);
+                vol_add(a.volc, D, vu);
+            }
+            moved += __popc(__ballot_sync(0xffffffffu, valid && mine));
+            __syncwarp();
+        }
+        if (lane == 0 && moved) atomicAdd(&a.cnt->moved, moved);
+    }
+    __syncthreads();
+}
+
+// PLP ties between dominant labels follow fmix32(label ^ salt), a seeded
+// pseudo-random order that changes every iteration ("ties arbitrarily",
+// Section III-A).
+__device__ __forceinline__ uint32_t plp_salt_dev(uint64_t seed, int32_t it) {
+    return fmix32(seed_word(seed) ^ (0x9E3779B9u * (uint32_t)(it + 1)));
+}
+
+// ---------------------------------------------------------------------------
+// PLM move phase (Algorithm 2): sweeps until no vertex wants to move.
+// ---------------------------------------------------------------------------
+template <int WK, bool BIG>
+__global__ void __launch_bounds__(kBlock, 4) k_move_phase(PhaseArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PlmBest<BIG> s_best[kBlock / 32];
+    __shared__ unsigned s_cand, s_gen;
+    __shared__ int s_last, s_ok, s_nb2;
+    __shared__ SweepCtx c;
+    if (threadIdx.x == 0) s_gen = 0;
+    __syncthreads();
+    int64_t *vb[2] = {a.vol_a, a.vol_b};
+    int64_t t = 0;
+    int32_t prev_k = -1, prev_par = 0;
+    int32_t sw = 0;
+    int conv = 0;
+    const int64_t gtid = blockIdx.x * (int64_t)kBlock + threadIdx.x, gthreads = (int64_t)gridDim.x * kBlock;
+    for (; sw < a.max_sweeps; sw++) {
+        const int par = sw & 1;
+        const int late = sw >= a.recheck_from;
+        if (!late)
+            for (int64_t i = gtid; i < a.ncol; i += gthreads) a.nmv[par * a.ncol + i] = 0;
+        else
+            for (int64_t i = gtid; i < a.ncol; i += gthreads) a.ncand[i] = 0;
+        if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+        for (int32_t k = 0; k < a.ncol; k++) {
+            const int64_t cb = a.class_off[(int64_t)k * NBINS], ce = a.class_off[(int64_t)k * NBINS + NBINS];
+            if (ce == cb) continue;
+            __syncthreads();   // every thread is done with the previous class's context
+            if (threadIdx.x == 0) {
+                s_nb2 = class_ctx(a, k, c);
+                c.g = a.g;
+                c.zeta = a.zeta;
+                c.cnt = a.cnt + sw;
+                c.late = late;
+                c.rp_n = nullptr;
+                if (!late) {
+                    c.volc = vb[t & 1];
+                    c.volw = vb[(t + 1) & 1];
+                    c.mv_u = a.mv_u + cb;
+                    c.mv_c = a.mv_c + cb;
+                    c.nmv = a.nmv + par * a.ncol + k;
+                } else {
+                    c.volc = vb[t & 1];
+                    c.volw = vb[t & 1];
+                    c.cand_u = a.mv_u + cb;
+                    c.cand_c = a.mv_c + cb;
+                    c.cand_d = a.cd + cb;
+                    c.cand_wd = a.cwd + cb;
+                    c.cand_wc = a.cwc + cb;
+                    c.ncand = a.ncand + k;
+                }
+            }
+            __syncthreads();
+            const int32_t nb2 = s_nb2;
+            if (!late) {
+                if (prev_k >= 0) {
+                    const int64_t pa = a.class_off[(int64_t)prev_k * NBINS];
+                    const int64_t nr = (int64_t)__ldcg(a.nmv + prev_par * a.ncol + prev_k);
+                    for (int64_t i = gtid; i < nr; i += gthreads) {
+                        const int32_t u = a.mv_u[pa + i];
+                        const int64_t vu = a.g.vol[u];
+                        vol_add(c.volw, a.mv_c[pa + i], -vu);
+                        vol_add(c.volw, a.zeta[u], vu);
+                    }
+                }
+            }
+            // a block walks several items; the barrier keeps one item's warps
+            // out of the shared tables of the next
+            const bool timed = a.stage_ns && blockIdx.x == 0 && threadIdx.x == 0;
+            uint64_t t0 = timed ? global_ns() : 0;
+            for (int32_t b = blockIdx.x; b < c.bend[4]; b += gridDim.x) {
+                run_item<WK, BIG, false>(c, b, smem, s_best, &s_cand, &s_last);
+                __syncthreads();
+            }
+            if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+            if (timed) { const uint64_t t1 = global_ns(); a.stage_ns[0] += t1 - t0; t0 = t1; }
+            if (nb2 > 0) {
+                for (int32_t b = blockIdx.x; b < nb2; b += gridDim.x)
+                    role_hub_decide<WK, BIG, false>(c, b, s_best, &s_cand, &s_last);
+                if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+                if (timed) { const uint64_t t1 = global_ns(); a.stage_ns[1] += t1 - t0; t0 = t1; }
+            }
+            if (late) {
+                if (__ldcg(c.ncand) != 0) {   // same value in every block after the barrier
+                    if (blockIdx.x == 0) {
+                        RecheckArgs ra{c.cand_u, c.cand_c, c.cand_d, c.cand_wd, c.cand_wc, c.ncand, a.zeta,
+                                       a.g.vol, c.volw, 2 * a.g.W, a.tmp_a, a.tmp_b, a.ubits, c.cnt};
+                        recheck_block<BIG>(ra, smem);
+                    }
+                    if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+                    if (timed) a.stage_ns[2] += global_ns() - t0;
+                }
+            } else {
+                prev_k = k;
+                prev_par = par;
+                t++;
+            }
+        }
+        if (__ldcg(&a.cnt[sw].wanted) == 0) {
+            conv = 1;
+            sw++;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.result[0] = sw;
+        a.result[1] = conv;
+        a.result[2] = (int32_t)(t & 1);   // buffer holding the final volumes
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PLP (Algorithm 1): iterations while more than theta labels changed.
+// ---------------------------------------------------------------------------
+template <int WK, bool BIG>
+__global__ void __launch_bounds__(kBlock, 4) k_plp_run(PhaseArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ PlpBest s_best[kBlock / 32];
+    __shared__ unsigned s_cand, s_gen;
+    __shared__ int s_last, s_ok, s_nb2;
+    __shared__ SweepCtx c;
+    if (threadIdx.x == 0) s_gen = 0;
+    __syncthreads();
+    int32_t it = 0;
+    int conv = 0;
+    unsigned long long updated = (unsigned long long)a.g.n;
+    while ((double)updated > a.theta && it < a.max_iters) {
+        const uint32_t salt = plp_salt_dev(a.seed, it);
+        for (int32_t k = 0; k < a.ncol; k++) {
+            const int64_t cb = a.class_off[(int64_t)k * NBINS], ce = a.class_off[(int64_t)k * NBINS + NBINS];
+            if (ce == cb) continue;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_nb2 = class_ctx(a, k, c);
+                c.g = a.g;
+                c.zeta = a.zeta;
+                c.cnt = a.cnt + it;
+                c.active = a.active;
+                c.tie_salt = salt;
+            }
+            __syncthreads();
+            const int32_t nb2 = s_nb2;
+            for (int32_t b = blockIdx.x; b < c.bend[4]; b += gridDim.x) {
+                run_item<WK, BIG, true>(c, b, smem, s_best, &s_cand, &s_last);
+                __syncthreads();
+            }
+            if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+            if (nb2 > 0) {
+                for (int32_t b = blockIdx.x; b < nb2; b += gridDim.x)
+                    role_hub_decide<WK, BIG, true>(c, b, s_best, &s_cand, &s_last);
+                if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+            }
+        }
+        if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+        updated = __ldcg(&a.cnt[it].moved);
+        it++;
+    }
+    conv = !((double)updated > a.theta);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.result[0] = it;
+        a.result[1] = conv;
+    }
+}
+
+}  // namespace cd

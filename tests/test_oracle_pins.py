@@ -264,6 +264,29 @@ def test_move_phase_converged_has_no_positive_move(oracle_mod):
     assert _no_positive_move(rp, c, w, z)
 
 
+@pytest.mark.parametrize("gname", ["rmat10", "rand_loops", "pp"])
+def test_late_sweeps_never_lower_modularity(oracle_mod, gname):
+    """From the re-check sweep (the 5th) on, every applied move has a
+    positive gain against the volumes already updated, so modularity (exact
+    fractions) never decreases from one sweep to the next, and the phase
+    converges."""
+    g = {"rmat10": lambda: synth.rmat(10, seed=8),
+         "rand_loops": lambda: synth.random_graph(120, 500, seed=9, loops=10),
+         "pp": lambda: synth.planted_partition(400, 8, 0.08, 0.01, seed=4)}[gname]()
+    rp, c, w = csr(g)
+    ed = exact.edges_of(rp, c, w)
+    full, st = oracle_mod.move_phase(rp, c, w, 1)
+    assert st["converged"] == 1
+    prev = None
+    for sweeps in range(4, st["sweeps"] + 1):
+        z, _ = oracle_mod.move_phase(rp, c, w, 1, max_sweeps=sweeps)
+        q = exact.modularity_fraction(g.n, ed, z)
+        if prev is not None:
+            assert q >= prev, sweeps
+        prev = q
+    assert np.array_equal(z, full)
+
+
 def _sequential_louvain_complete(n, wmat, order):
     """Textbook sequential local moving on a complete graph (every colour class
     is one vertex), with every gain taken as an exact modularity difference,
