@@ -167,6 +167,29 @@ cd_status cd_coarsen(cd_graph *g, const int32_t *labels, int labels_mem, cd_grap
 cd_status cd_graph_export(const cd_graph *g, int64_t *row_ptr, int32_t *col, int64_t *w,
                           int mem, int64_t *nnz_out);
 
+/* Modularity (as cd_modularity) of `labels` on a CSR that the caller keeps
+ * in device memory, computed without allocating any device memory.  The
+ * paper has no counterpart: this serves callers that must not allocate when
+ * they ask, such as code running inside a device-memory budget another
+ * framework owns, latency-critical loops that may not reach the allocator
+ * (an allocation can synchronise the device), or hooks run where allocation
+ * is not permitted.
+ *   n, row_ptr, col, w   the graph in the input conventions above (device
+ *                        pointers; w may be NULL for unit weights); n must
+ *                        not exceed 1,048,576
+ *   labels               device int32[n], each in [0, n)
+ *   stream               cudaStream_t to run on (NULL: legacy default)
+ *   mod                  host double receiving the result
+ * Scratch is one fixed device array in the library (8.4 MB, held on every GPU
+ * that loads the library until the process exits).  The first call on a device
+ * looks up that array's address with the device current, so make it before
+ * any stream capture.  Calls share the array: each call clears what must
+ * start at zero, and calls that overlap on the GPU race, so serialise them.
+ * Synchronous.  Errors: CD_EINVAL (n too large, NULL pointer, column or label
+ * out of range, non-positive weight, bad row_ptr), CD_ECUDA. */
+cd_status cd_modularity_static(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *w,
+                               const int32_t *labels, void *stream, double *mod);
+
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all threads, all devices). */
 uint64_t cd_launch_count(void);

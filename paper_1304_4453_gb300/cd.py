@@ -60,7 +60,7 @@ _lib = None
 SYMBOLS = ["cd_opts_default", "cd_status_str", "cd_last_error", "cd_graph_create",
            "cd_graph_destroy", "cd_graph_info", "cd_modularity", "cd_plp", "cd_plm",
            "cd_epp", "cd_color", "cd_coarsen", "cd_graph_export", "cd_debug_fail_alloc",
-           "cd_launch_count"]
+           "cd_launch_count", "cd_modularity_static"]
 
 
 def library_path() -> str:
@@ -92,6 +92,7 @@ def lib():
             L.cd_graph_export.argtypes = [P, P, P, P, c_int, P]
             L.cd_debug_fail_alloc.argtypes = [c_int]
             L.cd_debug_fail_alloc.restype = None
+            L.cd_modularity_static.argtypes = [i64, P, P, P, P, P, P]
             L.cd_launch_count.argtypes = []
             L.cd_launch_count.restype = ctypes.c_uint64
             for name in SYMBOLS:
@@ -238,6 +239,21 @@ def cd_graph_export(h):
 
 def cd_debug_fail_alloc(k: int):
     lib().cd_debug_fail_alloc(int(k))
+
+
+def cd_modularity_static(row_ptr, col, w, labels, stream=None) -> float:
+    """Modularity through the allocation-free entry point: every array must be
+    a CUDA tensor (the caller's device CSR and labels)."""
+    rp, m1, k1 = _arr(row_ptr, np.int64)
+    cp, m2, k2 = _arr(col, np.int32)
+    wp, m3, k3 = _arr(w, np.int32)
+    lp, m4, k4 = _arr(labels, np.int32)
+    if CD_MEM_HOST in (m1, m2, m4) or (w is not None and m3 == CD_MEM_HOST):
+        raise CDError(CD_EINVAL, "cd_modularity_static takes device arrays only")
+    n = k1.numel() - 1
+    out = ctypes.c_double()
+    _check(lib().cd_modularity_static(n, rp, cp, wp, lp, _stream(stream), ctypes.byref(out)), False)
+    return out.value
 
 
 def cd_launch_count() -> int:
