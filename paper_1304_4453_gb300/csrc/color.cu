@@ -12,31 +12,39 @@
 // free colour, and decrements wait of its lower-priority neighbours; those
 // that reach 0 form the next frontier.  Every adjacency entry is read once to
 // count and once when its row's vertex is coloured (plus a rescan per extra
-// window of 64 colours).  Frontier vertices of degree <= 1024 are handled by
-// one warp each; the adjacency of larger ones is cut into chunks spread over
-// all blocks (k_color_round_hubs).  Rounds run back to back on
+// window of 64 colours).  Frontier vertices of degree <= 64 are handled by one
+// warp each, up to 4096 by one block each, and the adjacency of larger ones
+// is cut into chunks spread over all blocks (k_color_round_hubs): a round
+// lasts as long as its slowest vertex.  Rounds run back to back on
 // the device (frontier lengths live in device memory); the host checks for
 // completion every few rounds.
 #include "common.cuh"
 
 namespace cd {
 
-constexpr int COLOR_BIG_DEG = 1024;
+constexpr int COLOR_WARP_DEG = 64;     // frontier vertices up to this degree: one warp each
+constexpr int COLOR_BIG_DEG = 4096;    // up to this degree: one block each; above: chunked
 
 __device__ __forceinline__ bool prio_gt(uint32_t hx, int32_t x, uint32_t hv, int32_t v) {
     return hx > hv || (hx == hv && x > v);
 }
 
-__device__ __forceinline__ void push_ready(int32_t x, const int64_t *rp, int32_t *nl, unsigned long long *nlc,
-                                           int32_t *nh, unsigned long long *nhc) {
-    if (rp[x + 1] - rp[x] > COLOR_BIG_DEG) nh[atomicAdd(nhc, 1ull)] = x;
-    else nl[atomicAdd(nlc, 1ull)] = x;
+// Next-round frontier: three lists by degree (warp / block / chunked).
+struct Frontier {
+    int32_t *list[3];
+    unsigned long long *count[3];
+};
+
+__device__ __forceinline__ void push_ready(int32_t x, const int64_t *rp, const Frontier &f) {
+    const int64_t d = rp[x + 1] - rp[x];
+    const int t = d <= COLOR_WARP_DEG ? 0 : d <= COLOR_BIG_DEG ? 1 : 2;
+    f.list[t][atomicAdd(f.count[t], 1ull)] = x;
 }
 
 // wait[v] and the first frontier; one warp per vertex.
 __global__ void k_color_init(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, int64_t n, uint32_t s,
-                             uint32_t *hash, int32_t *wait, int32_t *color, int32_t *nl, unsigned long long *nlc,
-                             int32_t *nh, unsigned long long *nhc, int32_t *hub_slot, unsigned int *nhubs) {
+                             uint32_t *hash, int32_t *wait, int32_t *color, Frontier nf, int32_t *hub_slot,
+                             unsigned int *nhubs) {
     const int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -54,7 +62,7 @@ __global__ void k_color_init(const int64_t *__restrict__ rp, const int32_t *__re
             wait[v] = cnt;
             color[v] = -1;
             if (end - beg > COLOR_BIG_DEG) hub_slot[v] = (int32_t)atomicAdd(nhubs, 1u);
-            if (cnt == 0) push_ready((int32_t)v, rp, nl, nlc, nh, nhc);
+            if (cnt == 0) push_ready((int32_t)v, rp, nf);
         }
     }
 }
@@ -77,11 +85,15 @@ __device__ __forceinline__ unsigned long long window_bits(const int64_t *rp, con
 // One warp per frontier vertex (degree <= COLOR_BIG_DEG).
 __global__ void k_color_round_warp(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                    const uint32_t *__restrict__ hash, const int32_t *list,
-                                   const unsigned long long *count_in, int32_t *wait, int32_t *color, int32_t *nl,
-                                   unsigned long long *nlc, int32_t *nh, unsigned long long *nhc,
+                                   const unsigned long long *count_in, int32_t *wait, int32_t *color, Frontier nf,
                                    unsigned long long *done) {
+    __shared__ int64_t s_count;
     const int lane = threadIdx.x & 31;
-    const int64_t count = (int64_t)*count_in;
+    // one read of the frontier length per block: every warp reading it would
+    // queue thousands of requests on one L2 line
+    if (threadIdx.x == 0) s_count = (int64_t)*count_in;
+    __syncthreads();
+    const int64_t count = s_count;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < count; i += nwarps) {
@@ -95,7 +107,7 @@ __global__ void k_color_round_warp(const int64_t *__restrict__ rp, const int32_t
                 const uint32_t c = (uint32_t)color[x];
                 if (c < 64) bits |= 1ull << c;
             } else if (atomicSub(&wait[x], 1) == 1) {
-                push_ready(x, rp, nl, nlc, nh, nhc);
+                push_ready(x, rp, nf);
             }
         }
         for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
@@ -112,6 +124,56 @@ __global__ void k_color_round_warp(const int64_t *__restrict__ rp, const int32_t
     }
 }
 
+// One block per frontier vertex (COLOR_WARP_DEG < degree <= COLOR_BIG_DEG).
+__global__ void k_color_round_block(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                    const uint32_t *__restrict__ hash, const int32_t *list,
+                                    const unsigned long long *count_in, int32_t *wait, int32_t *color, Frontier nf,
+                                    unsigned long long *done) {
+    __shared__ unsigned long long sbits;
+    __shared__ int64_t s_count;
+    if (threadIdx.x == 0) s_count = (int64_t)*count_in;
+    __syncthreads();
+    const int64_t count = s_count;
+    for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const int32_t v = list[i];
+        const uint32_t hv = hash[v];
+        const int64_t beg = rp[v], end = rp[v + 1];
+        if (threadIdx.x == 0) sbits = 0;
+        __syncthreads();
+        unsigned long long bits = 0;
+        for (int64_t e = beg + threadIdx.x; e < end; e += kBlock) {
+            const int32_t x = col[e];
+            if (prio_gt(hash[x], x, hv, v)) {
+                const uint32_t c = (uint32_t)color[x];
+                if (c < 64) bits |= 1ull << c;
+            } else if (atomicSub(&wait[x], 1) == 1) {
+                push_ready(x, rp, nf);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+        if ((threadIdx.x & 31) == 0) atomicOr(&sbits, bits);
+        __syncthreads();
+        bits = sbits;
+        uint32_t base = 0;
+        while (bits == ~0ull) {
+            base += 64;
+            __syncthreads();
+            if (threadIdx.x == 0) sbits = 0;
+            __syncthreads();
+            unsigned long long b = window_bits(rp, col, hash, color, v, hv, threadIdx.x, kBlock, base);
+            for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
+            if ((threadIdx.x & 31) == 0) atomicOr(&sbits, b);
+            __syncthreads();
+            bits = sbits;
+        }
+        if (threadIdx.x == 0) {
+            color[v] = (int32_t)(base + __ffsll((long long)~bits) - 1);
+            atomicAdd(done, 1ull);
+        }
+        __syncthreads();
+    }
+}
+
 // Frontier hubs (degree > COLOR_BIG_DEG): each hub's adjacency is cut into
 // chunks of COLOR_CHUNK entries, and the (hub, chunk) items of the round are
 // spread over all blocks.  A chunk ORs the colours (< COLOR_BITS) of its
@@ -125,13 +187,15 @@ constexpr int COLOR_WORDS = COLOR_BITS / 32;
 __global__ void k_color_round_hubs(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                    const uint32_t *__restrict__ hash, const int32_t *list,
                                    const unsigned long long *count_in, const int32_t *hub_slot, uint32_t *bitmaps,
-                                   unsigned int *chunks_done, int32_t *wait, int32_t *color, int32_t *nl,
-                                   unsigned long long *nlc, int32_t *nh, unsigned long long *nhc,
+                                   unsigned int *chunks_done, int32_t *wait, int32_t *color, Frontier nf,
                                    unsigned long long *done) {
     __shared__ uint32_t sbm[COLOR_WORDS];
     __shared__ int s_last;
     __shared__ unsigned long long sbits;
-    const int64_t count = (int64_t)*count_in;
+    __shared__ int64_t s_count;
+    if (threadIdx.x == 0) s_count = (int64_t)*count_in;
+    __syncthreads();
+    const int64_t count = s_count;
     int64_t item0 = 0;
     for (int64_t i = 0; i < count; i++) {
         const int32_t v = list[i];
@@ -153,7 +217,7 @@ __global__ void k_color_round_hubs(const int64_t *__restrict__ rp, const int32_t
                     const uint32_t c = (uint32_t)color[x];
                     if (c < COLOR_BITS) atomicOr(&sbm[c >> 5], 1u << (c & 31));
                 } else if (atomicSub(&wait[x], 1) == 1) {
-                    push_ready(x, rp, nl, nlc, nh, nhc);
+                    push_ready(x, rp, nf);
                 }
             }
             __syncthreads();
@@ -215,12 +279,16 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     constexpr int ROUNDS_PER_CHECK = 8;
     DBuf<uint32_t> hash(g.n, s);
     DBuf<int32_t> wait(g.n, s);
-    DBuf<int32_t> lists(4 * g.n, s);          // low / high frontier, current and next
-    DBuf<unsigned long long> cnt(5, s);       // [0,1] low, [2,3] high, [4] coloured
+    DBuf<int32_t> lists(6 * g.n, s);          // three tiers, current and next
+    DBuf<unsigned long long> cnt(7, s);       // [tier * 2 + side], [6] coloured
     cnt.zero();
-    int32_t *L[2] = {lists.p, lists.p + g.n};
-    int32_t *H[2] = {lists.p + 2 * g.n, lists.p + 3 * g.n};
-    // every hub has more than COLOR_BIG_DEG entries
+    Frontier F[2];
+    for (int side = 0; side < 2; side++)
+        for (int t = 0; t < 3; t++) {
+            F[side].list[t] = lists.p + (size_t)(2 * t + side) * g.n;
+            F[side].count[t] = cnt.p + 2 * t + side;
+        }
+    // every chunked hub has more than COLOR_BIG_DEG entries
     const int64_t max_hubs = g.nnz / (COLOR_BIG_DEG + 1) + 1;
     DBuf<int32_t> hub_slot(g.n, s);
     DBuf<uint32_t> bitmaps((size_t)max_hubs * COLOR_WORDS, s);
@@ -229,8 +297,7 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     chunks_done.zero();
     nhubs.zero();
     { k_color_init<<<grid_for(g.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(g.rp, g.col, g.n, sw, hash.p, wait.p, color,
-                                                                          L[0], cnt.p + 0, H[0], cnt.p + 2, hub_slot.p,
-                                                                          nhubs.p); ::cd::note_launch(); }
+                                                                          F[0], hub_slot.p, nhubs.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     Pinned h(sizeof(unsigned long long));
     int cur = 0;
@@ -238,18 +305,19 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     while (true) {
         for (int r = 0; r < ROUNDS_PER_CHECK; r++) {
             const int nx = 1 - cur;
-            CD_CUDA(cudaMemsetAsync(cnt.p + nx, 0, sizeof(unsigned long long), s));
-            CD_CUDA(cudaMemsetAsync(cnt.p + 2 + nx, 0, sizeof(unsigned long long), s));
-            { k_color_round_warp<<<152 * 16, kBlock, 0, s>>>(g.rp, g.col, hash.p, L[cur], cnt.p + cur, wait.p, color,
-                                                           L[nx], cnt.p + nx, H[nx], cnt.p + 2 + nx, cnt.p + 4); ::cd::note_launch(); }
-            { k_color_round_hubs<<<152 * 4, kBlock, 0, s>>>(g.rp, g.col, hash.p, H[cur], cnt.p + 2 + cur, hub_slot.p,
-                                                          bitmaps.p, chunks_done.p, wait.p, color, L[nx], cnt.p + nx,
-                                                          H[nx], cnt.p + 2 + nx, cnt.p + 4); ::cd::note_launch(); }
+            for (int t = 0; t < 3; t++) CD_CUDA(cudaMemsetAsync(F[nx].count[t], 0, sizeof(unsigned long long), s));
+            { k_color_round_warp<<<152 * 4, kBlock, 0, s>>>(g.rp, g.col, hash.p, F[cur].list[0], F[cur].count[0],
+                                                          wait.p, color, F[nx], cnt.p + 6); ::cd::note_launch(); }
+            { k_color_round_block<<<152 * 4, kBlock, 0, s>>>(g.rp, g.col, hash.p, F[cur].list[1], F[cur].count[1],
+                                                           wait.p, color, F[nx], cnt.p + 6); ::cd::note_launch(); }
+            { k_color_round_hubs<<<152 * 2, kBlock, 0, s>>>(g.rp, g.col, hash.p, F[cur].list[2], F[cur].count[2],
+                                                          hub_slot.p, bitmaps.p, chunks_done.p, wait.p, color, F[nx],
+                                                          cnt.p + 6); ::cd::note_launch(); }
             CD_LAUNCH_CHECK();
             cur = nx;
             rounds++;
         }
-        CD_CUDA(cudaMemcpyAsync(h.p, cnt.p + 4, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CD_CUDA(cudaMemcpyAsync(h.p, cnt.p + 6, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CD_CUDA(cudaStreamSynchronize(s));
         const int64_t coloured = (int64_t)*h.as<unsigned long long>();
         if (coloured >= g.n) break;

@@ -35,8 +35,9 @@ namespace cd {
 constexpr int NBINS = 5;
 constexpr int BLK_MAXDEG = 1024;
 constexpr int BLK_SLOTS = 2048;     // block role table (deg <= 1024)
-constexpr int HUB_CHUNK = 1024;     // adjacency entries per hub-aggregation block
-constexpr int HUB_SCAN = 4096;      // table slots per hub-decide block
+constexpr int HUB_CHUNK = 256;      // adjacency entries per hub-aggregation item
+constexpr int HUB_CHUNK_SLOTS = 512;  // shared table of one hub-aggregation item
+constexpr int HUB_SCAN = 1024;      // hub table slots per hub-decide item
 constexpr int SMEM_BYTES = 24576;   // shared table union of every role
 
 __host__ __device__ inline int degree_bin(int64_t d) {
@@ -461,7 +462,7 @@ template <int WK, bool BIG, bool PLP>
 __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb, unsigned char *smem, int *s_last) {
     using VT = ValT<BIG>;
     int32_t *keys = reinterpret_cast<int32_t *>(smem);
-    VT *vals = reinterpret_cast<VT *>(smem + BLK_SLOTS * 4);
+    VT *vals = reinterpret_cast<VT *>(smem + HUB_CHUNK_SLOTS * 4);
     const int h = find_hub(c.hub_b1, c.nhubs, rb);
     const HubInfo hi = c.hubs[h];
     const int32_t u = hi.v;
@@ -472,15 +473,16 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
     const int64_t rbeg = c.g.rp[u], rend = c.g.rp[u + 1];
     const int64_t beg = rbeg + (int64_t)j * HUB_CHUNK;
     const int64_t end = min(rend, beg + HUB_CHUNK);
-    for (int s = threadIdx.x; s < BLK_SLOTS; s += kBlock) { keys[s] = -1; vals[s] = 0; }
+    for (int s = threadIdx.x; s < HUB_CHUNK_SLOTS; s += kBlock) { keys[s] = -1; vals[s] = 0; }
     __syncthreads();
     for (int64_t e = beg + threadIdx.x; e < end; e += kBlock)
-        tab_insert<VT>(keys, vals, BLK_SLOTS - 1, c.zeta[c.g.col[e]], (VT)edge_weight<WK>(c.g.w, e), &c.cnt->overflow);
+        tab_insert<VT>(keys, vals, HUB_CHUNK_SLOTS - 1, c.zeta[c.g.col[e]], (VT)edge_weight<WK>(c.g.w, e),
+                       &c.cnt->overflow);
     __syncthreads();
     int32_t *gk = c.hub_keys + hi.tab;
     VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
     const uint32_t gmask = (uint32_t)(hi.slots - 1);
-    for (int s = threadIdx.x; s < BLK_SLOTS; s += kBlock)
+    for (int s = threadIdx.x; s < HUB_CHUNK_SLOTS; s += kBlock)
         if (keys[s] >= 0) tab_insert<VT>(gk, gv, gmask, keys[s], vals[s], &c.cnt->overflow);
     __threadfence();
     __syncthreads();
