@@ -75,16 +75,25 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+// A team: `size` consecutive blocks of the grid that work on one graph and
+// synchronise through their own barrier.  The single-graph kernels use the
+// whole grid as one team.
+struct Team {
+    int32_t rank, size;
+    GridBarrier *bar;
+};
+
 // Returns false when the barrier failed (timeout here or in another block).
-__device__ __forceinline__ bool grid_sync(GridBarrier *b, unsigned *s_gen, int *s_ok) {
+__device__ __forceinline__ bool team_sync(const Team &t, unsigned *s_gen, int *s_ok) {
+    GridBarrier *b = t.bar;
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned g = *s_gen;
         int ok = 1;
         __threadfence();
-        const unsigned sb = blockIdx.x / BARRIER_FAN;
-        const unsigned nsub = (gridDim.x + BARRIER_FAN - 1) / BARRIER_FAN;
-        const unsigned sub_size = min((unsigned)BARRIER_FAN, gridDim.x - sb * BARRIER_FAN);
+        const unsigned sb = (unsigned)t.rank / BARRIER_FAN;
+        const unsigned nsub = ((unsigned)t.size + BARRIER_FAN - 1) / BARRIER_FAN;
+        const unsigned sub_size = min((unsigned)BARRIER_FAN, (unsigned)t.size - sb * BARRIER_FAN);
         bool opener = false;
         if (atomicAdd(&b->sub[sb], 1u) == sub_size - 1) {
             atomicExch(&b->sub[sb], 0u);
@@ -428,24 +437,29 @@ __device__ __forceinline__ uint32_t plp_salt_dev(uint64_t seed, int32_t it) {
     return fmix32(seed_word(seed) ^ (0x9E3779B9u * (uint32_t)(it + 1)));
 }
 
+// Per-block shared state of the phase bodies.
+template <typename BT>
+struct BlockShared {
+    unsigned char *smem;       // dynamic PHASE_SMEM bytes
+    BT *best;                  // [kBlock / 32]
+    unsigned *cand, *gen;
+    int *last, *ok, *nb2;
+    SweepCtx *c;
+};
+
 // ---------------------------------------------------------------------------
-// PLM move phase (Algorithm 2): sweeps until no vertex wants to move.
+// PLM move phase (Algorithm 2) of one graph, run by one team: sweeps until
+// no vertex wants to move.  Returns false when a barrier failed.
 // ---------------------------------------------------------------------------
 template <int WK, bool BIG>
-__global__ void __launch_bounds__(kBlock, 4) k_move_phase(PhaseArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ PlmBest<BIG> s_best[kBlock / 32];
-    __shared__ unsigned s_cand, s_gen;
-    __shared__ int s_last, s_ok, s_nb2;
-    __shared__ SweepCtx c;
-    if (threadIdx.x == 0) s_gen = 0;
-    __syncthreads();
+__device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockShared<PlmBest<BIG>> &sh) {
+    SweepCtx &c = *sh.c;
     int64_t *vb[2] = {a.vol_a, a.vol_b};
     int64_t t = 0;
     int32_t prev_k = -1, prev_par = 0;
     int32_t sw = 0;
     int conv = 0;
-    const int64_t gtid = blockIdx.x * (int64_t)kBlock + threadIdx.x, gthreads = (int64_t)gridDim.x * kBlock;
+    const int64_t gtid = (int64_t)tm.rank * kBlock + threadIdx.x, gthreads = (int64_t)tm.size * kBlock;
     for (; sw < a.max_sweeps; sw++) {
         const int par = sw & 1;
         const int late = sw >= a.recheck_from;
@@ -453,13 +467,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_move_phase(PhaseArgs a) {
             for (int64_t i = gtid; i < a.ncol; i += gthreads) a.nmv[par * a.ncol + i] = 0;
         else
             for (int64_t i = gtid; i < a.ncol; i += gthreads) a.ncand[i] = 0;
-        if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+        if (!team_sync(tm, sh.gen, sh.ok)) return false;
         for (int32_t k = 0; k < a.ncol; k++) {
             const int64_t cb = a.class_off[(int64_t)k * NBINS], ce = a.class_off[(int64_t)k * NBINS + NBINS];
             if (ce == cb) continue;
             __syncthreads();   // every thread is done with the previous class's context
             if (threadIdx.x == 0) {
-                s_nb2 = class_ctx(a, k, c);
+                *sh.nb2 = class_ctx(a, k, c);
                 c.g = a.g;
                 c.zeta = a.zeta;
                 c.cnt = a.cnt + sw;
@@ -483,43 +497,42 @@ __global__ void __launch_bounds__(kBlock, 4) k_move_phase(PhaseArgs a) {
                 }
             }
             __syncthreads();
-            const int32_t nb2 = s_nb2;
-            if (!late) {
-                if (prev_k >= 0) {
-                    const int64_t pa = a.class_off[(int64_t)prev_k * NBINS];
-                    const int64_t nr = (int64_t)__ldcg(a.nmv + prev_par * a.ncol + prev_k);
-                    for (int64_t i = gtid; i < nr; i += gthreads) {
-                        const int32_t u = a.mv_u[pa + i];
-                        const int64_t vu = a.g.vol[u];
-                        vol_add(c.volw, a.mv_c[pa + i], -vu);
-                        vol_add(c.volw, a.zeta[u], vu);
-                    }
+            const int32_t nb2 = *sh.nb2;
+            if (!late && prev_k >= 0) {
+                // replay the previous class's moves into this class's write buffer
+                const int64_t pa = a.class_off[(int64_t)prev_k * NBINS];
+                const int64_t nr = (int64_t)__ldcg(a.nmv + prev_par * a.ncol + prev_k);
+                for (int64_t i = gtid; i < nr; i += gthreads) {
+                    const int32_t u = a.mv_u[pa + i];
+                    const int64_t vu = a.g.vol[u];
+                    vol_add(c.volw, a.mv_c[pa + i], -vu);
+                    vol_add(c.volw, a.zeta[u], vu);
                 }
             }
+            const bool timed = a.stage_ns && tm.rank == 0 && threadIdx.x == 0;
+            uint64_t t0 = timed ? global_ns() : 0;
             // a block walks several items; the barrier keeps one item's warps
             // out of the shared tables of the next
-            const bool timed = a.stage_ns && blockIdx.x == 0 && threadIdx.x == 0;
-            uint64_t t0 = timed ? global_ns() : 0;
-            for (int32_t b = blockIdx.x; b < c.bend[4]; b += gridDim.x) {
-                run_item<WK, BIG, false>(c, b, smem, s_best, &s_cand, &s_last);
+            for (int32_t b = tm.rank; b < c.bend[4]; b += tm.size) {
+                run_item<WK, BIG, false>(c, b, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
             }
-            if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+            if (!team_sync(tm, sh.gen, sh.ok)) return false;
             if (timed) { const uint64_t t1 = global_ns(); a.stage_ns[0] += t1 - t0; t0 = t1; }
             if (nb2 > 0) {
-                for (int32_t b = blockIdx.x; b < nb2; b += gridDim.x)
-                    role_hub_decide<WK, BIG, false>(c, b, s_best, &s_cand, &s_last);
-                if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+                for (int32_t b = tm.rank; b < nb2; b += tm.size)
+                    role_hub_decide<WK, BIG, false>(c, b, sh.best, sh.cand, sh.last);
+                if (!team_sync(tm, sh.gen, sh.ok)) return false;
                 if (timed) { const uint64_t t1 = global_ns(); a.stage_ns[1] += t1 - t0; t0 = t1; }
             }
             if (late) {
                 if (__ldcg(c.ncand) != 0) {   // same value in every block after the barrier
-                    if (blockIdx.x == 0) {
+                    if (tm.rank == 0) {
                         RecheckArgs ra{c.cand_u, c.cand_c, c.cand_d, c.cand_wd, c.cand_wc, c.ncand, a.zeta,
                                        a.g.vol, c.volw, 2 * a.g.W, a.tmp_a, a.tmp_b, a.ubits, c.cnt};
-                        recheck_block<BIG>(ra, smem);
+                        recheck_block<BIG>(ra, sh.smem);
                     }
-                    if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+                    if (!team_sync(tm, sh.gen, sh.ok)) return false;
                     if (timed) a.stage_ns[2] += global_ns() - t0;
                 }
             } else {
@@ -534,27 +547,22 @@ __global__ void __launch_bounds__(kBlock, 4) k_move_phase(PhaseArgs a) {
             break;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (tm.rank == 0 && threadIdx.x == 0) {
         a.result[0] = sw;
         a.result[1] = conv;
         a.result[2] = (int32_t)(t & 1);   // buffer holding the final volumes
     }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
-// PLP (Algorithm 1): iterations while more than theta labels changed.
+// PLP (Algorithm 1) of one graph, run by one team: iterations while more than
+// theta labels changed.  Returns false when a barrier failed.
 // ---------------------------------------------------------------------------
 template <int WK, bool BIG>
-__global__ void __launch_bounds__(kBlock, 4) k_plp_run(PhaseArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ PlpBest s_best[kBlock / 32];
-    __shared__ unsigned s_cand, s_gen;
-    __shared__ int s_last, s_ok, s_nb2;
-    __shared__ SweepCtx c;
-    if (threadIdx.x == 0) s_gen = 0;
-    __syncthreads();
+__device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<PlpBest> &sh) {
+    SweepCtx &c = *sh.c;
     int32_t it = 0;
-    int conv = 0;
     unsigned long long updated = (unsigned long long)a.g.n;
     while ((double)updated > a.theta && it < a.max_iters) {
         const uint32_t salt = plp_salt_dev(a.seed, it);
@@ -563,7 +571,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_plp_run(PhaseArgs a) {
             if (ce == cb) continue;
             __syncthreads();
             if (threadIdx.x == 0) {
-                s_nb2 = class_ctx(a, k, c);
+                *sh.nb2 = class_ctx(a, k, c);
                 c.g = a.g;
                 c.zeta = a.zeta;
                 c.cnt = a.cnt + it;
@@ -571,26 +579,113 @@ __global__ void __launch_bounds__(kBlock, 4) k_plp_run(PhaseArgs a) {
                 c.tie_salt = salt;
             }
             __syncthreads();
-            const int32_t nb2 = s_nb2;
-            for (int32_t b = blockIdx.x; b < c.bend[4]; b += gridDim.x) {
-                run_item<WK, BIG, true>(c, b, smem, s_best, &s_cand, &s_last);
+            const int32_t nb2 = *sh.nb2;
+            for (int32_t b = tm.rank; b < c.bend[4]; b += tm.size) {
+                run_item<WK, BIG, true>(c, b, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
             }
-            if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+            if (!team_sync(tm, sh.gen, sh.ok)) return false;
             if (nb2 > 0) {
-                for (int32_t b = blockIdx.x; b < nb2; b += gridDim.x)
-                    role_hub_decide<WK, BIG, true>(c, b, s_best, &s_cand, &s_last);
-                if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+                for (int32_t b = tm.rank; b < nb2; b += tm.size)
+                    role_hub_decide<WK, BIG, true>(c, b, sh.best, sh.cand, sh.last);
+                if (!team_sync(tm, sh.gen, sh.ok)) return false;
             }
         }
-        if (!grid_sync(a.bar, &s_gen, &s_ok)) return;
+        if (!team_sync(tm, sh.gen, sh.ok)) return false;
         updated = __ldcg(&a.cnt[it].moved);
         it++;
     }
-    conv = !((double)updated > a.theta);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (tm.rank == 0 && threadIdx.x == 0) {
         a.result[0] = it;
-        a.result[1] = conv;
+        a.result[1] = !((double)updated > a.theta);
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels.  Single graph: the whole grid is one team.  Batch: teams of
+// team_size consecutive blocks pull graph indices from a device queue and
+// run each graph's phase on their own barrier, so graphs of uneven size
+// share one launch.
+// ---------------------------------------------------------------------------
+struct BatchArgs {
+    const PhaseArgs *graphs;   // device array
+    int32_t ngraphs;
+    int32_t team_size;
+    GridBarrier *bars;         // one per team
+    unsigned int *queue;       // next graph index
+    int32_t *team_graph;       // current graph of each team
+};
+
+#define CD_BLOCK_SHARED(BT)                                                     \
+    extern __shared__ __align__(16) unsigned char smem[];                       \
+    __shared__ BT s_best[kBlock / 32];                                          \
+    __shared__ unsigned s_cand, s_gen;                                          \
+    __shared__ int s_last, s_ok, s_nb2;                                         \
+    __shared__ SweepCtx s_ctx;                                                  \
+    if (threadIdx.x == 0) s_gen = 0;                                            \
+    __syncthreads();                                                            \
+    const BlockShared<BT> sh{smem, s_best, &s_cand, &s_gen, &s_last, &s_ok, &s_nb2, &s_ctx};
+
+template <int WK, bool BIG>
+__global__ void __launch_bounds__(kBlock, 4) k_move_phase(PhaseArgs a) {
+    CD_BLOCK_SHARED(PlmBest<BIG>)
+    const Team tm{(int32_t)blockIdx.x, (int32_t)gridDim.x, a.bar};
+    move_phase_body<WK, BIG>(a, tm, sh);
+}
+
+template <int WK, bool BIG>
+__global__ void __launch_bounds__(kBlock, 4) k_plp_run(PhaseArgs a) {
+    CD_BLOCK_SHARED(PlpBest)
+    const Team tm{(int32_t)blockIdx.x, (int32_t)gridDim.x, a.bar};
+    plp_body<WK, BIG>(a, tm, sh);
+}
+
+// Assigns the team's next graph; all blocks of the team read it after the barrier.
+__device__ __forceinline__ int32_t next_graph(const BatchArgs &b, const Team &tm, int32_t team, unsigned *s_gen,
+                                              int *s_ok) {
+    if (tm.rank == 0 && threadIdx.x == 0) b.team_graph[team] = (int32_t)atomicAdd(b.queue, 1u);
+    if (!team_sync(tm, s_gen, s_ok)) return -1;
+    const int32_t g = __ldcg(b.team_graph + team);
+    // everyone has read the assignment before it can change
+    if (!team_sync(tm, s_gen, s_ok)) return -1;
+    return g < b.ngraphs ? g : -1;
+}
+
+static_assert(sizeof(PhaseArgs) % 8 == 0, "PhaseArgs is copied in 64-bit words");
+
+// Copies a graph's arguments into shared memory (read many times per class).
+__device__ __forceinline__ void load_args(const PhaseArgs *src, unsigned long long *dst) {
+    const unsigned long long *w = reinterpret_cast<const unsigned long long *>(src);
+    for (int i = threadIdx.x; i < (int)(sizeof(PhaseArgs) / 8); i += blockDim.x) dst[i] = w[i];
+    __syncthreads();
+}
+
+template <int WK, bool BIG>
+__global__ void __launch_bounds__(kBlock, 4) k_move_phase_batch(BatchArgs b) {
+    CD_BLOCK_SHARED(PlmBest<BIG>)
+    const int32_t team = blockIdx.x / b.team_size;
+    const Team tm{(int32_t)(blockIdx.x % b.team_size), b.team_size, b.bars + team};
+    __shared__ __align__(16) unsigned long long s_args[sizeof(PhaseArgs) / 8];
+    while (true) {
+        const int32_t g = next_graph(b, tm, team, &s_gen, &s_ok);
+        if (g < 0) return;
+        load_args(b.graphs + g, s_args);
+        if (!move_phase_body<WK, BIG>(*reinterpret_cast<const PhaseArgs *>(s_args), tm, sh)) return;
+    }
+}
+
+template <int WK, bool BIG>
+__global__ void __launch_bounds__(kBlock, 4) k_plp_batch(BatchArgs b) {
+    CD_BLOCK_SHARED(PlpBest)
+    const int32_t team = blockIdx.x / b.team_size;
+    const Team tm{(int32_t)(blockIdx.x % b.team_size), b.team_size, b.bars + team};
+    __shared__ __align__(16) unsigned long long s_args[sizeof(PhaseArgs) / 8];
+    while (true) {
+        const int32_t g = next_graph(b, tm, team, &s_gen, &s_ok);
+        if (g < 0) return;
+        load_args(b.graphs + g, s_args);
+        if (!plp_body<WK, BIG>(*reinterpret_cast<const PhaseArgs *>(s_args), tm, sh)) return;
     }
 }
 
