@@ -56,20 +56,29 @@ typedef enum {
 enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1 };
 
 /* Options.  cd_opts_default() fills: seed 1, max_sweeps 256, max_levels 64,
- * max_iters 1000, profile 0.
- *   seed        colouring priorities (Jones-Plassmann), PLP tie order and the
- *               move-damping coin all derive from it; EPP base i uses seed+i.
+ * max_iters 1000, profile 0, team_quantum 262144, team_min 8.
+ *   seed        colouring priorities (Jones-Plassmann) and the PLP tie order
+ *               derive from it; EPP base i uses seed+i.
  *   max_sweeps  cap on sweeps of one move phase (Algorithm 2 "repeat").
  *   max_levels  cap on the coarsening hierarchy depth (Algorithm 3).
  *   max_iters   cap on PLP iterations (Algorithm 1 "while").
- *   profile     1: time every local-move kernel launch with CUDA events and
- *               report it in cd_stats (adds host synchronisation). */
+ *   profile     1: time every persistent launch with CUDA events and report
+ *               it in cd_stats (adds host synchronisation).
+ *   team_quantum, team_min  launch shape of shared launches (EPP bases,
+ *               batches, the server): a graph whose work (adjacency entries
+ *               + vertices) is w gets teams of at least
+ *               ceil(w / team_quantum) blocks rounded up to a power of two,
+ *               and up to team_min graphs of a tier run side by side.  They
+ *               change speed only, never results. */
 typedef struct {
     uint64_t seed;
     int32_t max_sweeps;
     int32_t max_levels;
     int32_t max_iters;
     int32_t profile;
+    int64_t team_quantum;
+    int32_t team_min;
+    int32_t reserved;   /* 0 */
 } cd_opts;
 
 /* Run statistics (all optional: pass NULL to skip). */
@@ -147,6 +156,75 @@ cd_status cd_plm(cd_graph *g, int refine, const cd_opts *o, int32_t *labels,
  * core graph, prolongation.  b >= 1. */
 cd_status cd_epp(cd_graph *g, int ensemble_size, int final_refine, const cd_opts *o,
                  int32_t *labels, int labels_mem, double *mod, cd_stats *st);
+
+/* Batched and served runs.  The paper runs one graph at a time; its only
+ * multi-instance notion is the nested parallelism of EPP's base runs
+ * (Section III-C).  Here many runs share the GPU: each run advances through
+ * the same stages as the single-graph call (on host worker threads), and the
+ * persistent phases (PLM move phases, PLP runs) pending at the same moment
+ * share one cooperative launch, in which teams of blocks pull graphs from a
+ * device queue.  Batching changes nothing observable: every run's labels,
+ * modularity and statistics equal those of the single-graph call with the
+ * same task and options. */
+
+enum { CD_ALGO_PLP = 0, CD_ALGO_PLM = 1, CD_ALGO_EPP = 2 };
+
+/* What to run on a graph. */
+typedef struct {
+    int32_t algo;       /* CD_ALGO_PLP, CD_ALGO_PLM or CD_ALGO_EPP */
+    int32_t refine;     /* PLM: 1 = PLMR; EPP: 1 = PLMR as the final algorithm */
+    int32_t ensemble;   /* EPP: number of PLP base runs b >= 1 */
+    int32_t reserved;   /* 0 */
+    double theta;       /* PLP: iteration threshold (< 0: n * 1e-5); EPP bases always use n * 1e-5 */
+} cd_task;
+
+/* Runs `task` on `count` graphs together.
+ *   gs          count graph handles (a handle may repeat); their streams are
+ *               synchronised on entry
+ *   labels      count pointers; labels[i] holds n_i entries in labels_mem memory
+ *   mods        NULL or double[count]
+ *   st          NULL or cd_stats[count]
+ *   stream      cudaStream_t of the batched launches (NULL: legacy default)
+ * Synchronous.  Up to 16 host threads advance the runs between launches.
+ * Errors: after every run has stopped, the status of the first failing run
+ * in order (CD_EINVAL for bad arguments before anything runs); CD_ENOTCONV
+ * when some run hit its cap (results still valid). */
+cd_status cd_run_batch(cd_graph *const *gs, int count, const cd_task *task, const cd_opts *o,
+                       int32_t *const *labels, int labels_mem, double *mods, cd_stats *st, void *stream);
+
+/* cd_run_batch of PLM (refine 0) or PLMR (refine 1) on the stream of gs[0]. */
+cd_status cd_plm_batch(cd_graph *const *gs, int count, int refine, const cd_opts *o,
+                       int32_t *const *labels, int labels_mem, double *mods, cd_stats *st);
+
+/* Server: continuous batching of submitted runs.  A host thread admits
+ * queued runs in submission order while at most max_slots run at once and
+ * the estimated device memory of the admitted runs stays within
+ * device_mem_budget bytes (0: 80% of the device memory free at creation).
+ * An admitted run joins the next batched launch, so runs submitted while
+ * others are on the GPU overlap with them; a finished run frees its slot and
+ * memory at once.  Graphs, labels and volumes of every level stay on the
+ * device for the whole run.
+ *   max_queue   submitted runs not yet admitted, at most (CD_EBUSY beyond)
+ *   stream      cudaStream_t of the batched launches (NULL: the server
+ *               creates its own) */
+cd_status cd_server_create(size_t device_mem_budget, int max_slots, int max_queue, void *stream, cd_server **out);
+/* Queues `task` on g; g must stay alive until the run's result is taken.
+ * ticket receives the run's id.  Errors: CD_EBUSY (queue full), CD_EINVAL
+ * (bad task, or a run that could never fit the budget). */
+cd_status cd_server_submit(cd_server *s, cd_graph *g, const cd_task *task, const cd_opts *o, uint64_t *ticket);
+/* Takes a finished run's result: labels (n entries, labels_mem memory; NULL
+ * to skip), modularity, latency from submission to completion in ms, stats
+ * (each may be NULL); the ticket is then released.  Waits at most timeout_ms
+ * (0: do not wait; < 0: no limit).  Returns CD_EBUSY while the run is queued
+ * or running when the wait ends, CD_EINVAL for an unknown ticket, otherwise
+ * the run's own status. */
+cd_status cd_server_poll(cd_server *s, uint64_t ticket, double timeout_ms, int32_t *labels, int labels_mem,
+                         double *mod, double *latency_ms, cd_stats *st);
+/* Counters: runs queued, running and finished but not yet taken. */
+cd_status cd_server_info(cd_server *s, int64_t *queued, int64_t *running, int64_t *finished);
+/* Stops admitting, lets the runs on the GPU finish their current launch,
+ * drops every unfinished run and frees everything. */
+cd_status cd_server_destroy(cd_server *s);
 
 /* Building blocks exposed for verification. */
 

@@ -1,7 +1,7 @@
 """Python binding of the C ABI in include/cd.h (argument marshalling only).
 
 Functions keep the C names (``cd_graph_create``, ``cd_plp``, ``cd_plm``,
-``cd_epp``, ``cd_modularity``, ...).  Arrays may be torch tensors (CPU or CUDA)
+``cd_epp``, ``cd_modularity``, ``cd_run_batch``, ``cd_server_submit``, ...).  Arrays may be torch tensors (CPU or CUDA)
 or numpy arrays; CUDA tensors are passed as device pointers, everything else
 as host pointers.  PyTorch supplies device memory and the CUDA stream; all
 computation happens in libcdgpu.so.  If the library is not built, every call
@@ -20,6 +20,7 @@ from . import build as _build
 
 CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_ENOTCONV, CD_EBUSY, CD_ETIMEOUT = range(7)
 CD_MEM_HOST, CD_MEM_DEVICE = 0, 1
+CD_ALGO_PLP, CD_ALGO_PLM, CD_ALGO_EPP = 0, 1, 2
 
 
 class CDError(RuntimeError):
@@ -35,7 +36,8 @@ _STATUS = {0: "CD_OK", 1: "CD_EINVAL", 2: "CD_ENOMEM", 3: "CD_ECUDA", 4: "CD_ENO
 class cd_opts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("max_sweeps", ctypes.c_int32),
                 ("max_levels", ctypes.c_int32), ("max_iters", ctypes.c_int32),
-                ("profile", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("team_quantum", ctypes.c_int64),
+                ("team_min", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class cd_stats(ctypes.Structure):
@@ -54,13 +56,24 @@ class cd_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class cd_task(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("refine", ctypes.c_int32), ("ensemble", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("theta", ctypes.c_double)]
+
+
+def make_task(algo: int, refine: bool = False, ensemble: int = 1, theta: float = -1.0) -> cd_task:
+    return cd_task(int(algo), int(refine), int(ensemble), 0, float(theta))
+
+
 _lock = threading.Lock()
 _lib = None
 
 SYMBOLS = ["cd_opts_default", "cd_status_str", "cd_last_error", "cd_graph_create",
            "cd_graph_destroy", "cd_graph_info", "cd_modularity", "cd_plp", "cd_plm",
            "cd_epp", "cd_color", "cd_coarsen", "cd_graph_export", "cd_debug_fail_alloc",
-           "cd_launch_count", "cd_modularity_static"]
+           "cd_launch_count", "cd_modularity_static", "cd_run_batch", "cd_plm_batch",
+           "cd_server_create", "cd_server_submit", "cd_server_poll", "cd_server_info",
+           "cd_server_destroy"]
 
 
 def library_path() -> str:
@@ -93,6 +106,13 @@ def lib():
             L.cd_debug_fail_alloc.argtypes = [c_int]
             L.cd_debug_fail_alloc.restype = None
             L.cd_modularity_static.argtypes = [i64, P, P, P, P, P, P]
+            L.cd_run_batch.argtypes = [P, c_int, P, P, P, c_int, P, P, P]
+            L.cd_plm_batch.argtypes = [P, c_int, c_int, P, P, c_int, P, P]
+            L.cd_server_create.argtypes = [ctypes.c_size_t, c_int, c_int, P, P]
+            L.cd_server_submit.argtypes = [P, P, P, P, P]
+            L.cd_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.c_double, P, c_int, P, P, P]
+            L.cd_server_info.argtypes = [P, P, P, P]
+            L.cd_server_destroy.argtypes = [P]
             L.cd_launch_count.argtypes = []
             L.cd_launch_count.restype = ctypes.c_uint64
             for name in SYMBOLS:
@@ -141,10 +161,15 @@ def _stream(stream):
 
 
 def default_opts(seed: int = 1, max_sweeps: int = 256, max_levels: int = 64,
-                 max_iters: int = 1000, profile: bool = False) -> cd_opts:
+                 max_iters: int = 1000, profile: bool = False, team_quantum: int = 0,
+                 team_min: int = 0) -> cd_opts:
     o = cd_opts()
     lib().cd_opts_default(ctypes.byref(o))
     o.seed, o.max_sweeps, o.max_levels, o.max_iters, o.profile = seed, max_sweeps, max_levels, max_iters, int(profile)
+    if team_quantum:
+        o.team_quantum = team_quantum
+    if team_min:
+        o.team_min = team_min
     return o
 
 
@@ -256,6 +281,82 @@ def cd_modularity_static(row_ptr, col, w, labels, stream=None) -> float:
     return out.value
 
 
+def _batch_args(handles, labels_list):
+    if len(handles) != len(labels_list):
+        raise CDError(CD_EINVAL, "one labels buffer per graph")
+    count = len(handles)
+    hs = (ctypes.c_void_p * max(count, 1))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    ptrs, mems, keep = [], set(), []
+    for lab in labels_list:
+        lp, mem, k = _arr(lab, np.int32)
+        ptrs.append(lp.value if lp is not None else None)
+        mems.add(mem)
+        keep.append(k)
+    if len(mems) > 1:
+        raise CDError(CD_EINVAL, "labels must all live in the same memory")
+    lps = (ctypes.c_void_p * max(count, 1))(*ptrs)
+    return count, hs, lps, (mems.pop() if mems else CD_MEM_DEVICE), keep
+
+
+def cd_run_batch(handles, task: cd_task, labels_list, opts=None, stream=None):
+    """Runs ``task`` on every graph together.  Returns (mods, stats, status)."""
+    o = opts or default_opts()
+    count, hs, lps, mem, keep = _batch_args(handles, labels_list)
+    mods = (ctypes.c_double * max(count, 1))()
+    sts = (cd_stats * max(count, 1))()
+    status = lib().cd_run_batch(hs, count, ctypes.byref(task), ctypes.byref(o), lps, mem, mods, sts,
+                                _stream(stream))
+    _check(status)
+    return [mods[i] for i in range(count)], [sts[i].as_dict() for i in range(count)], status
+
+
+def cd_plm_batch(handles, labels_list, refine: bool = False, opts=None):
+    o = opts or default_opts()
+    count, hs, lps, mem, keep = _batch_args(handles, labels_list)
+    mods = (ctypes.c_double * max(count, 1))()
+    sts = (cd_stats * max(count, 1))()
+    status = lib().cd_plm_batch(hs, count, int(refine), ctypes.byref(o), lps, mem, mods, sts)
+    _check(status)
+    return [mods[i] for i in range(count)], [sts[i].as_dict() for i in range(count)], status
+
+
+def cd_server_create(device_mem_budget: int = 0, max_slots: int = 64, max_queue: int = 4096, stream=None):
+    h = ctypes.c_void_p()
+    st = _stream(stream) if stream is not None else ctypes.c_void_p(0)
+    _check(lib().cd_server_create(int(device_mem_budget), int(max_slots), int(max_queue), st, ctypes.byref(h)),
+           False)
+    return h
+
+
+def cd_server_submit(server, h, task: cd_task, opts=None) -> int:
+    o = opts or default_opts()
+    t = ctypes.c_uint64()
+    _check(lib().cd_server_submit(server, h, ctypes.byref(task), ctypes.byref(o), ctypes.byref(t)), False)
+    return t.value
+
+
+def cd_server_poll(server, ticket: int, labels_out=None, timeout_ms: float = 0.0):
+    """None while the run is queued or running, else (status, mod, latency_ms, stats)."""
+    lp, mem, keep = _arr(labels_out, np.int32)
+    mod, lat, st = ctypes.c_double(), ctypes.c_double(), cd_stats()
+    status = lib().cd_server_poll(server, ctypes.c_uint64(ticket), float(timeout_ms), lp, mem, ctypes.byref(mod),
+                                  ctypes.byref(lat), ctypes.byref(st))
+    if status == CD_EBUSY:
+        return None
+    _check(status)
+    return status, mod.value, lat.value, st.as_dict()
+
+
+def cd_server_info(server):
+    q, r, f = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().cd_server_info(server, ctypes.byref(q), ctypes.byref(r), ctypes.byref(f)), False)
+    return q.value, r.value, f.value
+
+
+def cd_server_destroy(server):
+    _check(lib().cd_server_destroy(server), False)
+
+
 def cd_launch_count() -> int:
     return int(lib().cd_launch_count())
 
@@ -320,3 +421,42 @@ class Graph:
 
     def modularity(self, labels) -> float:
         return cd_modularity(self.h, labels)
+
+
+def run_batch(graphs, algo: int = CD_ALGO_PLM, refine: bool = False, ensemble: int = 1, theta: float = -1.0,
+              outs=None, stream=None, **kw):
+    """Runs one task on many ``Graph`` objects in one batched call; returns a
+    list of ``Result`` (labels as CUDA tensors unless ``outs`` is given)."""
+    outs = outs if outs is not None else [g._out(None) for g in graphs]
+    mods, sts, status = cd_run_batch([g.h for g in graphs], make_task(algo, refine, ensemble, theta), outs,
+                                     default_opts(**kw), stream)
+    return [Result(o, m, s, status) for o, m, s in zip(outs, mods, sts)]
+
+
+class Server:
+    """Continuous-batching server (cd_server_*).  Submitted graphs must stay
+    alive until their result is taken."""
+
+    def __init__(self, device_mem_budget: int = 0, max_slots: int = 64, max_queue: int = 4096, stream=None):
+        self.h = cd_server_create(device_mem_budget, max_slots, max_queue, stream)
+
+    def submit(self, graph: "Graph", algo: int = CD_ALGO_PLM, refine: bool = False, ensemble: int = 1,
+               theta: float = -1.0, **kw) -> int:
+        return cd_server_submit(self.h, graph.h, make_task(algo, refine, ensemble, theta), default_opts(**kw))
+
+    def poll(self, ticket: int, out=None, timeout_ms: float = 0.0):
+        return cd_server_poll(self.h, ticket, out, timeout_ms)
+
+    def info(self):
+        return cd_server_info(self.h)
+
+    def close(self):
+        if self.h is not None:
+            cd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

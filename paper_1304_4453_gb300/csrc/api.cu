@@ -1,79 +1,19 @@
 // C ABI (include/cd.h): argument checks, host/device staging of caller
 // buffers, error translation.  All computation happens in the engine.
+#include <algorithm>
+#include <memory>
 #include <new>
+#include <thread>
 
 #include "common.cuh"
 #include "engine.cuh"
 #include "graph.cuh"
 
-namespace cd {
-const std::string &last_error();
-}
+#include "api_common.cuh"
 
 using namespace cd;
 
 namespace {
-
-template <typename F>
-cd_status guarded(F &&f) {
-    try {
-        cd_status s = f();
-        if (s == CD_OK) set_last_error("");
-        return s;
-    } catch (const Error &e) {
-        set_last_error(e.msg);
-        return e.status;
-    } catch (const std::bad_alloc &) {
-        set_last_error("host allocation failed");
-        return CD_ENOMEM;
-    } catch (...) {
-        set_last_error("unexpected internal error");
-        return CD_ECUDA;
-    }
-}
-
-RunOpts to_run(const cd_opts *o) {
-    cd_opts d;
-    cd_opts_default(&d);
-    if (!o) o = &d;
-    if (o->max_sweeps < 1 || o->max_levels < 1 || o->max_iters < 0)
-        raise(CD_EINVAL, "max_sweeps and max_levels must be >= 1, max_iters >= 0");
-    RunOpts r;
-    r.seed = o->seed;
-    r.max_sweeps = o->max_sweeps;
-    r.max_levels = o->max_levels;
-    r.max_iters = o->max_iters;
-    r.profile = o->profile != 0;
-    return r;
-}
-
-void to_stats(const RunStats &r, cd_stats *st) {
-    if (!st) return;
-    st->levels = r.levels;
-    st->colors0 = r.colors0 < 0 ? 0 : r.colors0;
-    st->converged = r.converged;
-    st->ncomm = r.ncomm;
-    st->sweeps = r.sweeps;
-    st->moves = r.moves;
-    st->iters = r.iters;
-    st->entries = r.entries;
-    st->candidates = r.candidates;
-    st->decisions = r.decisions;
-    st->ms_color = r.ms_color;
-    st->ms_move = r.ms_move;
-    st->ms_coarsen = r.ms_coarsen;
-    st->ms_total = r.ms_total;
-    st->k_launches = r.k_launches;
-    st->k_ms = r.k_ms;
-    st->k_bytes = r.k_bytes;
-    st->stage_items_ms = r.stage_ms[0];
-    st->stage_hub_ms = r.stage_ms[1];
-    st->stage_recheck_ms = r.stage_ms[2];
-}
-
-void check_mem(int mem) {
-    if (mem != CD_MEM_HOST && mem != CD_MEM_DEVICE) raise(CD_EINVAL, "unknown memory flag %d", mem);
-}
 
 // Device view of caller labels (copied in when they live on the host).
 struct LabelsIn {
@@ -126,6 +66,9 @@ void cd_opts_default(cd_opts *o) {
     o->max_levels = 64;
     o->max_iters = 1000;
     o->profile = 0;
+    o->team_quantum = int64_t(1) << 18;
+    o->team_min = 8;
+    o->reserved = 0;
 }
 
 const char *cd_status_str(cd_status s) {
@@ -240,6 +183,50 @@ cd_status cd_epp(cd_graph *g, int ensemble_size, int final_refine, const cd_opts
         out.finish();
         return finish_run(r, st);
     });
+}
+
+cd_status cd_run_batch(cd_graph *const *gs, int count, const cd_task *task, const cd_opts *o,
+                       int32_t *const *labels, int labels_mem, double *mods, cd_stats *st, void *stream) {
+    return guarded([&]() {
+        if (count < 0) raise(CD_EINVAL, "count must be >= 0");
+        if (count > 0 && (!gs || !labels)) raise(CD_EINVAL, "gs and labels are required");
+        check_mem(labels_mem);
+        RunOpts ro = to_run(o);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        std::vector<std::unique_ptr<Job>> jobs;
+        std::vector<Job *> jp;
+        for (int i = 0; i < count; i++) {
+            if (!gs[i]) raise(CD_EINVAL, "graph %d is NULL", i);
+            const GraphView &v = gs[i]->g.view;
+            if (v.n > 0 && !labels[i]) raise(CD_EINVAL, "labels[%d] is NULL", i);
+            CD_CUDA(cudaStreamSynchronize(gs[i]->stream));
+            jobs.push_back(std::make_unique<Job>(
+                task_spec(v, task, ro, labels_mem == CD_MEM_DEVICE ? labels[i] : nullptr)));
+            jp.push_back(jobs.back().get());
+        }
+        if (count == 0) return CD_OK;
+        const int hw = (int)std::thread::hardware_concurrency();
+        const int workers = std::max(1, std::min({16, count, hw > 0 ? hw : 4}));
+        run_jobs(jp, s, workers);
+        bool notconv = false;
+        for (int i = 0; i < count; i++) {
+            const Job &j = *jobs[i];
+            if (labels_mem == CD_MEM_HOST && j.spec.g.n)
+                CD_CUDA(cudaMemcpyAsync(labels[i], j.labels(), j.spec.g.n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            if (mods) mods[i] = j.mod;
+            if (st) to_stats(j.st, st + i);
+            notconv = notconv || !j.st.converged;
+        }
+        CD_CUDA(cudaStreamSynchronize(s));
+        return notconv ? CD_ENOTCONV : CD_OK;
+    });
+}
+
+cd_status cd_plm_batch(cd_graph *const *gs, int count, int refine, const cd_opts *o, int32_t *const *labels,
+                       int labels_mem, double *mods, cd_stats *st) {
+    cd_task t = {CD_ALGO_PLM, refine, 1, 0, -1.0};
+    void *stream = (count > 0 && gs && gs[0]) ? static_cast<void *>(gs[0]->stream) : nullptr;
+    return cd_run_batch(gs, count, &t, o, labels, labels_mem, mods, st, stream);
 }
 
 cd_status cd_color(cd_graph *g, uint64_t seed, int32_t *colors, int colors_mem, int32_t *ncolors) {

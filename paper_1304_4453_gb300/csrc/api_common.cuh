@@ -1,0 +1,107 @@
+// Helpers shared by the C ABI translation units (api.cu, server.cu):
+// exception-to-status translation, option and statistics conversion.
+#pragma once
+#include <new>
+
+#include "common.cuh"
+#include "engine.cuh"
+
+namespace cd {
+
+const std::string &last_error();
+
+template <typename F>
+cd_status guarded(F &&f) {
+    try {
+        cd_status s = f();
+        if (s == CD_OK) set_last_error("");
+        return s;
+    } catch (const Error &e) {
+        set_last_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return CD_ENOMEM;
+    } catch (...) {
+        set_last_error("unexpected internal error");
+        return CD_ECUDA;
+    }
+}
+
+inline RunOpts to_run(const cd_opts *o) {
+    cd_opts d;
+    cd_opts_default(&d);
+    if (!o) o = &d;
+    if (o->max_sweeps < 1 || o->max_levels < 1 || o->max_iters < 0)
+        raise(CD_EINVAL, "max_sweeps and max_levels must be >= 1, max_iters >= 0");
+    if (o->team_quantum < 1 || o->team_min < 1) raise(CD_EINVAL, "team_quantum and team_min must be >= 1");
+    RunOpts r;
+    r.seed = o->seed;
+    r.max_sweeps = o->max_sweeps;
+    r.max_levels = o->max_levels;
+    r.max_iters = o->max_iters;
+    r.profile = o->profile != 0;
+    r.team_quantum = o->team_quantum;
+    r.team_min = o->team_min;
+    return r;
+}
+
+inline void to_stats(const RunStats &r, cd_stats *st) {
+    if (!st) return;
+    st->levels = r.levels;
+    st->colors0 = r.colors0 < 0 ? 0 : r.colors0;
+    st->converged = r.converged;
+    st->ncomm = r.ncomm;
+    st->sweeps = r.sweeps;
+    st->moves = r.moves;
+    st->iters = r.iters;
+    st->entries = r.entries;
+    st->candidates = r.candidates;
+    st->decisions = r.decisions;
+    st->ms_color = r.ms_color;
+    st->ms_move = r.ms_move;
+    st->ms_coarsen = r.ms_coarsen;
+    st->ms_total = r.ms_total;
+    st->k_launches = r.k_launches;
+    st->k_ms = r.k_ms;
+    st->k_bytes = r.k_bytes;
+    st->stage_items_ms = r.stage_ms[0];
+    st->stage_hub_ms = r.stage_ms[1];
+    st->stage_recheck_ms = r.stage_ms[2];
+}
+
+inline void check_mem(int mem) {
+    if (mem != CD_MEM_HOST && mem != CD_MEM_DEVICE) raise(CD_EINVAL, "unknown memory flag %d", mem);
+}
+
+// Job of a cd_task on a graph (validated); labels nullptr: job-owned.
+inline JobSpec task_spec(const GraphView &g, const cd_task *t, const RunOpts &o, int32_t *labels) {
+    if (!t) raise(CD_EINVAL, "task is NULL");
+    JobSpec sp;
+    sp.g = g;
+    sp.o = o;
+    sp.labels = labels;
+    sp.want_mod = true;
+    if (t->refine != 0 && t->refine != 1) raise(CD_EINVAL, "refine must be 0 or 1");
+    sp.refine = t->refine == 1;
+    switch (t->algo) {
+    case CD_ALGO_PLP:
+        sp.algo = ALGO_PLP;
+        sp.theta = t->theta < 0 ? (double)g.n * 1e-5 : t->theta;
+        break;
+    case CD_ALGO_PLM:
+        sp.algo = ALGO_PLM;
+        break;
+    case CD_ALGO_EPP:
+        if (t->ensemble < 1) raise(CD_EINVAL, "ensemble must be >= 1");
+        sp.algo = ALGO_EPP;
+        sp.ensemble = t->ensemble;
+        sp.theta = (double)g.n * 1e-5;
+        break;
+    default:
+        raise(CD_EINVAL, "unknown algorithm %d", t->algo);
+    }
+    return sp;
+}
+
+}  // namespace cd

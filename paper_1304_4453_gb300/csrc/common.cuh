@@ -80,11 +80,15 @@ struct DBuf {
     void zero() { CD_CUDA(cudaMemsetAsync(p, 0, (n ? n : 1) * sizeof(T), s)); }
 };
 
-// Pinned host staging for small readbacks.
+// Pinned host staging for small readbacks, recycled per host thread (a
+// fresh cudaHostAlloc per readback would cost more than the readback).
 struct Pinned {
     void *p = nullptr;
+    size_t cap = 0;
     explicit Pinned(size_t bytes);
     ~Pinned();
+    Pinned(const Pinned &) = delete;
+    Pinned &operator=(const Pinned &) = delete;
     template <typename T> T *as() const { return static_cast<T *>(p); }
 };
 

@@ -1,9 +1,16 @@
-// Host drivers: schedule construction, the move phase (Algorithm 2), PLP
+// Host engine: schedule construction, the move phase (Algorithm 2), PLP
 // (Algorithm 1), the PLM / PLMR level loop (Algorithms 3, 4) and EPP
-// (Algorithm 5).  Every step of the computation is a kernel; the host only
-// sequences launches and reads back per-sweep counters.
+// (Algorithm 5) as jobs that advance on host worker threads and meet in
+// batched persistent launches.  Every step of the computation is a kernel;
+// the host only sequences launches and reads back per-sweep counters.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <functional>
 #include <memory>
+#include <mutex>
+#include <thread>
 
 #include "engine.cuh"
 #include "graph.cuh"
@@ -14,7 +21,7 @@ namespace cd {
 // Sweeps 0 .. RECHECK_FROM-1 of a move phase apply every wanted move of a
 // class at once.  From sweep RECHECK_FROM on, a class's wanted moves are
 // re-checked one by one in ascending vertex id against the volumes updated
-// by the moves accepted before them (k_recheck), so every applied move raises
+// by the moves accepted before them (the re-check), so every applied move raises
 // modularity and the phase terminates.
 constexpr int RECHECK_FROM = 4;
 
@@ -203,8 +210,33 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
 static int wbytes(int wk) { return wk == W_UNIT ? 0 : wk == W_I32 ? 4 : 8; }
 
 // ---------------------------------------------------------------------------
-// Move phase (Algorithm 2) under the colour-class schedule.
+// Persistent phases.  A PhaseRun owns the buffers and arguments of one PLM
+// move phase (Algorithm 2) or one PLP run (Algorithm 1) of one graph.
 // ---------------------------------------------------------------------------
+struct PhaseRun {
+    bool plp = false;
+    int wk = W_UNIT;
+    bool big = false;
+    bool profile = false;
+    int64_t work = 0;             // adjacency entries + vertices (team sizing)
+    int64_t quantum = 1;          // launch shape (RunOpts::team_quantum, team_min)
+    int32_t team_min = 1;
+    int64_t listed = 0;           // vertices the schedule visits
+    int32_t cap = 0;              // counter slots
+    PhaseArgs a{};
+    DBuf<Counters> cnt;           // cap counters, then one slot holding the result words
+    DBuf<unsigned long long> stage;
+    DBuf<int32_t> mv_u, mv_c, cd_;
+    DBuf<int64_t> vol_a, vol_b, cwd, cwc;
+    DBuf<uint64_t> tmp_a, tmp_b;
+    DBuf<unsigned long long> nmv, ncand;
+    DBuf<uint8_t> active;
+    // set by the engine after the launch
+    double launch_ms = 0, wall_ms = 0;
+    cd_status fail = CD_OK;
+    std::string fail_msg;
+};
+
 // Arguments shared by the persistent kernels: graph, schedule, hub tables.
 static PhaseArgs phase_args(const GraphView &g, const Schedule &S, int32_t *zeta) {
     PhaseArgs a{};
@@ -232,74 +264,108 @@ static PhaseArgs phase_args(const GraphView &g, const Schedule &S, int32_t *zeta
     return a;
 }
 
-// Reads a persistent run's result words and per-sweep counters.
-static int32_t finish_phase(const DBuf<int32_t> &result, const DBuf<Counters> &cnt, const DBuf<GridBarrier> &bar,
-                            int32_t *conv, std::vector<Counters> &per, cudaStream_t s) {
-    Pinned hr(4 * sizeof(int32_t) + sizeof(GridBarrier));
-    CD_CUDA(cudaMemcpyAsync(hr.p, result.p, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    CD_CUDA(cudaMemcpyAsync(hr.as<char>() + 4 * sizeof(int32_t), bar.p, sizeof(GridBarrier), cudaMemcpyDeviceToHost, s));
+static void alloc_counters(PhaseRun &r, int32_t cap, cudaStream_t s) {
+    r.cap = cap;
+    r.cnt.alloc((size_t)cap + 1, s);
+    r.cnt.zero();
+    r.a.cnt = r.cnt.p;
+    r.a.result = reinterpret_cast<int32_t *>(r.cnt.p + cap);
+    if (r.profile) {
+        r.stage.alloc(3, s);
+        r.stage.zero();
+        r.a.stage_ns = r.stage.p;
+    }
+}
+
+// Reads a finished run's result words and per-sweep counters.
+static int32_t read_counters(PhaseRun &r, int32_t *conv, std::vector<Counters> &per, RunStats &st, cudaStream_t s) {
+    if (r.fail != CD_OK) raise(r.fail, "%s", r.fail_msg.c_str());
+    per.resize((size_t)r.cap + 1);
+    CD_CUDA(cudaMemcpyAsync(per.data(), r.cnt.p, per.size() * sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    unsigned long long ns[3] = {0, 0, 0};
+    if (r.profile) CD_CUDA(cudaMemcpyAsync(ns, r.stage.p, sizeof(ns), cudaMemcpyDeviceToHost, s));
     CD_CUDA(cudaStreamSynchronize(s));
-    const GridBarrier *hb = reinterpret_cast<const GridBarrier *>(hr.as<char>() + 4 * sizeof(int32_t));
-    if (hb->err) raise(CD_ETIMEOUT, "a grid barrier of the persistent kernel timed out");
-    const int32_t runs = hr.as<int32_t>()[0];
-    *conv = hr.as<int32_t>()[1];
+    const int32_t *res = reinterpret_cast<const int32_t *>(&per[r.cap]);
+    const int32_t runs = res[0];
+    *conv = res[1];
+    if (runs < 0 || runs > r.cap) raise(CD_ECUDA, "persistent phase reported %d sweeps (cap %d)", runs, r.cap);
     per.resize(runs);
-    if (runs) CD_CUDA(cudaMemcpyAsync(per.data(), cnt.p, runs * sizeof(Counters), cudaMemcpyDeviceToHost, s));
-    CD_CUDA(cudaStreamSynchronize(s));
     for (const Counters &c : per)
         if (c.overflow) raise(CD_ECUDA, "internal hash table overflow (%llu failed inserts)", c.overflow);
+    for (int i = 0; i < 3; i++) st.stage_ms[i] += ns[i] * 1e-6;
+    st.ms_move += r.wall_ms;
+    if (r.profile) {
+        st.k_ms += r.launch_ms;
+        st.k_launches += 1;
+    }
     return runs;
 }
 
-// ---------------------------------------------------------------------------
-// Move phase (Algorithm 2) under the colour-class schedule: one persistent
-// launch.  volc holds the community volumes of zeta on entry.
-// ---------------------------------------------------------------------------
-static int64_t move_phase(const GraphView &g, const Schedule &S, int32_t *zeta, int64_t *volc, const RunOpts &o,
-                          RunStats &st, LaunchTimer &timer, cudaStream_t s) {
-    const bool big = needs_big(g.W);
-    const int64_t ncol = S.ncol;
-    DBuf<int32_t> mv_u(g.n, s), mv_c(g.n, s), cd_(g.n, s);
-    DBuf<int64_t> cwd(g.n, s), cwc(g.n, s), volb(g.n, s);
-    DBuf<uint64_t> tmp_a(g.n, s), tmp_b(g.n, s);
-    DBuf<unsigned long long> nmv(2 * ncol + 1, s), ncand(ncol + 1, s);
-    DBuf<Counters> cnt(o.max_sweeps, s);
-    DBuf<GridBarrier> bar(1, s);
-    DBuf<int32_t> result(4, s);
-    cnt.zero();
-    bar.zero();
-    result.zero();
-    nmv.zero();
-    if (g.n) CD_CUDA(cudaMemcpyAsync(volb.p, volc, g.n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    PhaseArgs a = phase_args(g, S, zeta);
-    a.cnt = cnt.p;
-    a.bar = bar.p;
-    a.result = result.p;
-    a.vol_a = volc;
-    a.vol_b = volb.p;
-    a.mv_u = mv_u.p;
-    a.mv_c = mv_c.p;
-    a.cd = cd_.p;
-    a.cwd = cwd.p;
-    a.cwc = cwc.p;
-    a.nmv = nmv.p;
-    a.ncand = ncand.p;
-    a.tmp_a = tmp_a.p;
-    a.tmp_b = tmp_b.p;
+__global__ void k_comm_volumes(const int32_t *zeta, const int64_t *vol, int64_t n, int64_t *volc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(reinterpret_cast<unsigned long long *>(volc + zeta[i]), (unsigned long long)vol[i]);
+}
+
+// Move phase of zeta on g.  init_vol: community volumes of zeta (the vertex
+// volumes when zeta is the singleton partition); nullptr computes them.
+static std::unique_ptr<PhaseRun> prepare_move(const GraphView &g, const Schedule &S, int32_t *zeta,
+                                              const int64_t *init_vol, const RunOpts &o, cudaStream_t s) {
+    auto r = std::make_unique<PhaseRun>();
+    const int64_t n = g.n, ncol = S.ncol;
+    r->plp = false;
+    r->wk = g.wk;
+    r->big = needs_big(g.W);
+    r->profile = o.profile;
+    r->work = g.nnz + n;
+    r->quantum = o.team_quantum;
+    r->team_min = o.team_min;
+    r->a = phase_args(g, S, zeta);
+    r->mv_u.alloc(n, s);
+    r->mv_c.alloc(n, s);
+    r->cd_.alloc(n, s);
+    r->cwd.alloc(n, s);
+    r->cwc.alloc(n, s);
+    r->vol_a.alloc(n, s);
+    r->vol_b.alloc(n, s);
+    r->tmp_a.alloc(n, s);
+    r->tmp_b.alloc(n, s);
+    r->nmv.alloc(2 * ncol + 1, s);
+    r->nmv.zero();
+    r->ncand.alloc(ncol + 1, s);
+    if (init_vol) {
+        if (n) CD_CUDA(cudaMemcpyAsync(r->vol_a.p, init_vol, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    } else {
+        r->vol_a.zero();
+        if (n) { k_comm_volumes<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(zeta, g.vol, n, r->vol_a.p); ::cd::note_launch(); }
+        CD_LAUNCH_CHECK();
+    }
+    if (n) CD_CUDA(cudaMemcpyAsync(r->vol_b.p, r->vol_a.p, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    alloc_counters(*r, o.max_sweeps, s);
+    PhaseArgs &a = r->a;
+    a.vol_a = r->vol_a.p;
+    a.vol_b = r->vol_b.p;
+    a.mv_u = r->mv_u.p;
+    a.mv_c = r->mv_c.p;
+    a.cd = r->cd_.p;
+    a.cwd = r->cwd.p;
+    a.cwc = r->cwc.p;
+    a.nmv = r->nmv.p;
+    a.ncand = r->ncand.p;
+    a.tmp_a = r->tmp_a.p;
+    a.tmp_b = r->tmp_b.p;
     int ubits = 1;
-    while (((int64_t)1 << ubits) < g.n) ubits++;
+    while (((int64_t)1 << ubits) < n) ubits++;
     a.ubits = ubits;
     a.max_sweeps = o.max_sweeps;
     a.recheck_from = RECHECK_FROM;
-    DBuf<unsigned long long> stage(3, s);
-    stage.zero();
-    if (timer.on) a.stage_ns = stage.p;
-    timer.before(s);
-    launch_move_phase(g.wk, big, a, s);
-    timer.after(s);
+    return r;
+}
+
+// Returns the number of moves of the phase.
+static int64_t finish_move(PhaseRun &r, RunStats &st, cudaStream_t s) {
     int32_t conv = 0;
     std::vector<Counters> per;
-    const int32_t sweeps = finish_phase(result, cnt, bar, &conv, per, s);
+    read_counters(r, &conv, per, st, s);
     int64_t total = 0;
     for (const Counters &h : per) {
         st.sweeps++;
@@ -308,160 +374,61 @@ static int64_t move_phase(const GraphView &g, const Schedule &S, int32_t *zeta, 
         st.candidates += h.candidates;
         st.decisions += h.decisions;
         total += h.moved;
-        if (timer.on)
-            st.k_bytes += 40.0 * h.decisions + (8.0 + wbytes(g.wk)) * h.entries + 8.0 * h.candidates + 12.0 * h.moved;
-    }
-    if (timer.on) {
-        st.k_ms += timer.collect_ms();
-        unsigned long long ns[3];
-        CD_CUDA(cudaMemcpy(ns, stage.p, sizeof(ns), cudaMemcpyDeviceToHost));
-        for (int i = 0; i < 3; i++) st.stage_ms[i] += ns[i] * 1e-6;
+        if (r.profile)
+            st.k_bytes += 40.0 * h.decisions + (8.0 + wbytes(r.wk)) * h.entries + 8.0 * h.candidates + 12.0 * h.moved;
     }
     if (!conv) st.converged = 0;
-    (void)sweeps;
     return total;
 }
 
-__global__ void k_prolong(int32_t *zeta, const int64_t *rank, const int32_t *up, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        zeta[i] = up[rank[zeta[i]]];
-}
-
-__global__ void k_comm_volumes(const int32_t *zeta, const int64_t *vol, int64_t n, int64_t *volc) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(reinterpret_cast<unsigned long long *>(volc + zeta[i]), (unsigned long long)vol[i]);
-}
-
-struct Level {
-    OwnedGraph own;
-    GraphView g;
-    Schedule S;
-    DBuf<int32_t> zeta;
-    DBuf<int64_t> rank;
-};
-
-void run_plm(const GraphView &g0, bool refine, const RunOpts &o, int32_t *labels, RunStats &st, cudaStream_t s) {
-    const auto t_all = Clock::now();
-    LaunchTimer timer;
-    timer.on = o.profile;
-    std::vector<std::unique_ptr<Level>> L;
-    L.push_back(std::make_unique<Level>());
-    L[0]->g = g0;
-    for (int depth = 0;; depth++) {
-        Level &lv = *L.back();
-        const int64_t n = lv.g.n;
-        auto t = Clock::now();
-        build_schedule(lv.g, o.seed, lv.S, s);
-        st.ms_color += ms_since(t);
-        if (depth == 0 && st.colors0 < 0) st.colors0 = lv.S.ncol;
-        lv.zeta.alloc(n, s);
-        iota32(lv.zeta.p, n, s);
-        DBuf<int64_t> volc(n, s);
-        if (n) CD_CUDA(cudaMemcpyAsync(volc.p, lv.g.vol, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-        t = Clock::now();
-        const int64_t moved = move_phase(lv.g, lv.S, lv.zeta.p, volc.p, o, st, timer, s);
-        st.ms_move += ms_since(t);
-        if (moved == 0 || depth + 1 >= o.max_levels) break;
-        t = Clock::now();
-        lv.rank.alloc(n, s);
-        auto nx = std::make_unique<Level>();
-        coarsen_graph(lv.g, lv.zeta.p, lv.rank.p, nx->own, s);
-        nx->g = nx->own.view;
-        L.push_back(std::move(nx));
-        st.ms_coarsen += ms_since(t);
-    }
-    st.levels += (int32_t)L.size();
-    int64_t k = compact_labels(L.back()->zeta.p, L.back()->g.n, s);
-    for (int d = (int)L.size() - 2; d >= 0; d--) {
-        Level &lv = *L[d];
-        const int64_t n = lv.g.n;
-        if (n)
-            { k_prolong<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(lv.zeta.p, lv.rank.p, L[d + 1]->zeta.p, n); ::cd::note_launch(); }
-        CD_LAUNCH_CHECK();
-        if (refine) {
-            DBuf<int64_t> volc(n, s);
-            volc.zero();
-            if (n) { k_comm_volumes<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(lv.zeta.p, lv.g.vol, n, volc.p); ::cd::note_launch(); }
-            CD_LAUNCH_CHECK();
-            auto t = Clock::now();
-            move_phase(lv.g, lv.S, lv.zeta.p, volc.p, o, st, timer, s);
-            st.ms_move += ms_since(t);
-            k = compact_labels(lv.zeta.p, n, s);
-        }
-        L.pop_back();
-    }
-    if (g0.n)
-        CD_CUDA(cudaMemcpyAsync(labels, L[0]->zeta.p, g0.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    CD_CUDA(cudaStreamSynchronize(s));
-    st.k_launches += timer.launches;
-    st.ncomm = (int32_t)k;
-    st.ms_total += ms_since(t_all);
-}
-
-// ---------------------------------------------------------------------------
-// PLP (Algorithm 1)
-// ---------------------------------------------------------------------------
-static void plp_iterate(const GraphView &g, const Schedule &S, const RunOpts &o, double theta, int32_t *zeta,
-                        RunStats &st, LaunchTimer &timer, cudaStream_t s) {
-    const bool big = needs_big(g.W);
-    DBuf<uint8_t> active(g.n, s);
-    if (g.n) CD_CUDA(cudaMemsetAsync(active.p, 1, g.n, s));
+// PLP run on g from the singleton labelling, labels in zeta.
+static std::unique_ptr<PhaseRun> prepare_plp(const GraphView &g, const Schedule &S, int32_t *zeta, uint64_t seed,
+                                             double theta, const RunOpts &o, cudaStream_t s) {
+    auto r = std::make_unique<PhaseRun>();
+    r->plp = true;
+    r->wk = g.wk;
+    r->big = needs_big(g.W);
+    r->profile = o.profile;
+    r->work = g.nnz + g.n;
+    r->quantum = o.team_quantum;
+    r->team_min = o.team_min;
+    r->listed = S.off[(int64_t)S.ncol * NBINS];
+    r->a = phase_args(g, S, zeta);
+    r->active.alloc(g.n, s);
+    if (g.n) CD_CUDA(cudaMemsetAsync(r->active.p, 1, g.n, s));
     iota32(zeta, g.n, s);
-    DBuf<Counters> cnt(o.max_iters + 1, s);
-    DBuf<GridBarrier> bar(1, s);
-    DBuf<int32_t> result(4, s);
-    cnt.zero();
-    bar.zero();
-    result.zero();
-    PhaseArgs a = phase_args(g, S, zeta);
-    a.cnt = cnt.p;
-    a.bar = bar.p;
-    a.result = result.p;
-    a.active = active.p;
-    a.seed = o.seed;
-    a.theta = theta;
-    a.max_iters = o.max_iters;
-    timer.before(s);
-    launch_plp_run(g.wk, big, a, s);
-    timer.after(s);
+    alloc_counters(*r, o.max_iters + 1, s);
+    r->a.active = r->active.p;
+    r->a.seed = seed;
+    r->a.theta = theta;
+    r->a.max_iters = o.max_iters;
+    return r;
+}
+
+static void finish_plp(PhaseRun &r, RunStats &st, cudaStream_t s) {
     int32_t conv = 0;
     std::vector<Counters> per;
-    const int32_t iters = finish_phase(result, cnt, bar, &conv, per, s);
-    const int64_t listed = S.off[(int64_t)S.ncol * NBINS];
+    const int32_t iters = read_counters(r, &conv, per, st, s);
     for (const Counters &h : per) {
         st.moves += h.moved;
         st.entries += h.entries;
         st.candidates += h.candidates;
         st.decisions += h.decisions;
-        if (timer.on)
-            st.k_bytes += 5.0 * listed + 20.0 * h.decisions + (8.0 + wbytes(g.wk)) * h.entries + 4.0 * h.moved;
+        if (r.profile)
+            st.k_bytes += 5.0 * r.listed + 20.0 * h.decisions + (8.0 + wbytes(r.wk)) * h.entries + 4.0 * h.moved;
     }
-    if (timer.on) st.k_ms += timer.collect_ms();
     st.iters += iters;
     if (!conv) st.converged = 0;
 }
 
-void run_plp(const GraphView &g, const RunOpts &o, double theta, int32_t *labels, RunStats &st, cudaStream_t s) {
-    const auto t_all = Clock::now();
-    LaunchTimer timer;
-    timer.on = o.profile;
-    Schedule S;
-    auto t = Clock::now();
-    build_schedule(g, o.seed, S, s);
-    st.ms_color += ms_since(t);
-    if (st.colors0 < 0) st.colors0 = S.ncol;
-    t = Clock::now();
-    plp_iterate(g, S, o, theta, labels, st, timer, s);
-    st.ms_move += ms_since(t);
-    st.ncomm = (int32_t)compact_labels(labels, g.n, s);
-    st.levels = 1;
-    st.k_launches += timer.launches;
-    st.ms_total += ms_since(t_all);
+// ---------------------------------------------------------------------------
+// Kernels between phases: prolongation and the EPP core (Eq. 2).
+// ---------------------------------------------------------------------------
+__global__ void k_prolong(int32_t *zeta, const int64_t *rank, const int32_t *up, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        zeta[i] = up[rank[zeta[i]]];
 }
 
-// ---------------------------------------------------------------------------
-// EPP (Algorithm 5) with the exact core communities of Eq. (2).
-// ---------------------------------------------------------------------------
 __global__ void k_pair_keys(const int32_t *core, const int32_t *z, int64_t n, uint64_t *key, int32_t *val) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         key[i] = ((uint64_t)(uint32_t)core[i] << 32) | (uint32_t)z[i];
@@ -504,60 +471,570 @@ static void fold_core(int32_t *core, const int32_t *z, int64_t n, cudaStream_t s
     CD_LAUNCH_CHECK();
 }
 
+// ---------------------------------------------------------------------------
+// Jobs
+// ---------------------------------------------------------------------------
+struct Level {
+    OwnedGraph own;
+    GraphView g;
+    Schedule S;
+    DBuf<int32_t> zeta;
+    DBuf<int64_t> rank;
+};
+
+enum Stage {
+    ST_START,      // nothing done yet
+    ST_PLP_WAIT,   // PLP run launched
+    ST_EPP_WAIT,   // EPP base runs launched
+    ST_DOWN_WAIT,  // move phase of the deepest level launched
+    ST_UP,         // prolong to level `up`
+    ST_UP_WAIT,    // refinement move phase of level `up` launched
+    ST_PLM_DONE,   // labels of the PLM graph in L[0]->zeta
+    ST_FINAL,      // labels in place: modularity, release
+};
+
+struct JobState {
+    int stage = ST_START;
+    Clock::time_point t0;
+    GraphView g;                  // graph of the PLM part (input, or EPP's core graph)
+    std::vector<std::unique_ptr<Level>> L;
+    int up = -1;
+    std::unique_ptr<PhaseRun> run;
+    // EPP
+    std::vector<std::unique_ptr<Schedule>> base_S;
+    std::vector<std::unique_ptr<PhaseRun>> base_runs;
+    DBuf<int32_t> base, core;
+    DBuf<int64_t> core_rank;
+    OwnedGraph cg;
+    bool epp_plm = false;
+};
+
+Job::Job(const JobSpec &s) : spec(s), state(std::make_unique<JobState>()) {}
+Job::~Job() = default;
+
+// Level `L.back()`: schedule, singleton labels, move phase.
+static void start_level(Job &j, cudaStream_t s) {
+    JobState &x = *j.state;
+    Level &lv = *x.L.back();
+    auto t = Clock::now();
+    build_schedule(lv.g, j.spec.o.seed, lv.S, s);
+    j.st.ms_color += ms_since(t);
+    if (x.L.size() == 1 && j.st.colors0 < 0) j.st.colors0 = lv.S.ncol;
+    lv.zeta.alloc(lv.g.n, s);
+    iota32(lv.zeta.p, lv.g.n, s);
+    x.run = prepare_move(lv.g, lv.S, lv.zeta.p, lv.g.vol, j.spec.o, s);
+    x.stage = ST_DOWN_WAIT;
+}
+
+static void begin_plm(Job &j, cudaStream_t s) {
+    JobState &x = *j.state;
+    x.L.clear();
+    x.L.push_back(std::make_unique<Level>());
+    x.L[0]->g = x.g;
+    start_level(j, s);
+}
+
+// Advances a job until it waits for a launch or is finished.
+static void advance_impl(Job &j, cudaStream_t s) {
+    JobState &x = *j.state;
+    const JobSpec &sp = j.spec;
+    RunStats &st = j.st;
+    const int64_t n0 = sp.g.n;
+    for (;;) {
+        switch (x.stage) {
+        case ST_START: {
+            x.t0 = Clock::now();
+            if (sp.algo == ALGO_PLP) {
+                x.L.push_back(std::make_unique<Level>());
+                Level &lv = *x.L[0];
+                lv.g = sp.g;
+                auto t = Clock::now();
+                build_schedule(sp.g, sp.o.seed, lv.S, s);
+                st.ms_color += ms_since(t);
+                if (st.colors0 < 0) st.colors0 = lv.S.ncol;
+                x.run = prepare_plp(sp.g, lv.S, j.labels(), sp.o.seed, sp.theta, sp.o, s);
+                x.stage = ST_PLP_WAIT;
+                return;
+            }
+            if (sp.algo == ALGO_EPP) {
+                const int b = sp.ensemble;
+                x.base.alloc((size_t)b * n0, s);
+                for (int i = 0; i < b; i++) {
+                    const uint64_t seed = sp.o.seed + (uint64_t)i;
+                    x.base_S.push_back(std::make_unique<Schedule>());
+                    auto t = Clock::now();
+                    build_schedule(sp.g, seed, *x.base_S[i], s);
+                    st.ms_color += ms_since(t);
+                    if (i == 0) st.colors0 = x.base_S[0]->ncol;
+                    x.base_runs.push_back(
+                        prepare_plp(sp.g, *x.base_S[i], x.base.p + (size_t)i * n0, seed, sp.theta, sp.o, s));
+                }
+                x.stage = ST_EPP_WAIT;
+                return;
+            }
+            x.g = sp.g;
+            begin_plm(j, s);
+            return;
+        }
+        case ST_PLP_WAIT: {
+            finish_plp(*x.run, st, s);
+            x.run.reset();
+            st.ncomm = (int32_t)compact_labels(j.labels(), n0, s);
+            st.levels = 1;
+            x.L.clear();
+            x.stage = ST_FINAL;
+            break;
+        }
+        case ST_EPP_WAIT: {
+            const int b = sp.ensemble;
+            for (int i = 0; i < b; i++) {
+                finish_plp(*x.base_runs[i], st, s);
+                compact_labels(x.base.p + (size_t)i * n0, n0, s);
+            }
+            x.base_runs.clear();
+            x.base_S.clear();
+            x.core.alloc(n0, s);
+            if (n0) {
+                CD_CUDA(cudaMemcpyAsync(x.core.p, x.base.p, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+                for (int i = 1; i < b; i++) fold_core(x.core.p, x.base.p + (size_t)i * n0, n0, s);
+            }
+            x.base.release();
+            auto t = Clock::now();
+            x.core_rank.alloc(n0, s);
+            coarsen_graph(sp.g, x.core.p, x.core_rank.p, x.cg, s);
+            x.core_rank.release();
+            st.ms_coarsen += ms_since(t);
+            x.g = x.cg.view;
+            x.epp_plm = true;
+            begin_plm(j, s);
+            return;
+        }
+        case ST_DOWN_WAIT: {
+            Level &lv = *x.L.back();
+            const int64_t moved = finish_move(*x.run, st, s);
+            x.run.reset();
+            if (moved == 0 || (int)x.L.size() >= sp.o.max_levels) {
+                st.levels += (int32_t)x.L.size();
+                st.ncomm = (int32_t)compact_labels(lv.zeta.p, lv.g.n, s);
+                x.up = (int)x.L.size() - 2;
+                x.stage = ST_UP;
+                break;
+            }
+            auto t = Clock::now();
+            lv.rank.alloc(lv.g.n, s);
+            auto nx = std::make_unique<Level>();
+            coarsen_graph(lv.g, lv.zeta.p, lv.rank.p, nx->own, s);
+            nx->g = nx->own.view;
+            x.L.push_back(std::move(nx));
+            st.ms_coarsen += ms_since(t);
+            start_level(j, s);
+            return;
+        }
+        case ST_UP: {
+            if (x.up < 0) {
+                x.stage = ST_PLM_DONE;
+                break;
+            }
+            Level &lv = *x.L[x.up];
+            const int64_t n = lv.g.n;
+            if (n) { k_prolong<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(lv.zeta.p, lv.rank.p, x.L[x.up + 1]->zeta.p, n); ::cd::note_launch(); }
+            CD_LAUNCH_CHECK();
+            x.L.pop_back();
+            if (sp.refine) {
+                x.run = prepare_move(lv.g, lv.S, lv.zeta.p, nullptr, sp.o, s);
+                x.stage = ST_UP_WAIT;
+                return;
+            }
+            x.up--;
+            break;
+        }
+        case ST_UP_WAIT: {
+            Level &lv = *x.L[x.up];
+            finish_move(*x.run, st, s);
+            x.run.reset();
+            st.ncomm = (int32_t)compact_labels(lv.zeta.p, lv.g.n, s);
+            x.up--;
+            x.stage = ST_UP;
+            break;
+        }
+        case ST_PLM_DONE: {
+            Level &top = *x.L[0];
+            if (x.epp_plm) {
+                if (n0) { k_gather_core<<<grid_for(n0, kBlock, 152 * 32), kBlock, 0, s>>>(top.zeta.p, x.core.p, n0, j.labels()); ::cd::note_launch(); }
+                CD_LAUNCH_CHECK();
+                st.ncomm = (int32_t)compact_labels(j.labels(), n0, s);
+            } else if (n0) {
+                CD_CUDA(cudaMemcpyAsync(j.labels(), top.zeta.p, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            }
+            x.L.clear();
+            x.stage = ST_FINAL;
+            break;
+        }
+        case ST_FINAL: {
+            if (sp.want_mod) j.mod = modularity(sp.g, j.labels(), s);
+            CD_CUDA(cudaStreamSynchronize(s));
+            st.ms_total += ms_since(x.t0);
+            x.cg = OwnedGraph();
+            x.core.release();
+            j.done = true;
+            return;
+        }
+        }
+    }
+}
+
+static void advance(Job &j, cudaStream_t s) {
+    if (j.done) return;
+    try {
+        advance_impl(j, s);
+        CD_CUDA(cudaStreamSynchronize(s));   // the next step may use another stream
+    } catch (const Error &e) {
+        j.status = e.status;
+        j.msg = e.msg;
+    } catch (const std::bad_alloc &) {
+        j.status = CD_ENOMEM;
+        j.msg = "host allocation failed";
+    }
+    if (j.status != CD_OK) {
+        j.state.reset();   // frees the job's device memory (stream-ordered)
+        cudaStreamSynchronize(s);
+        j.done = true;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host worker threads, each with its own stream.
+// ---------------------------------------------------------------------------
+class WorkerPool {
+  public:
+    WorkerPool(int n, int device) : dev_(device) {
+        for (int w = 0; w < n; w++) {
+            cudaStream_t st;
+            CD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            streams_.push_back(st);
+        }
+        for (int w = 0; w < n; w++) threads_.emplace_back([this, w]() { loop(w); });
+    }
+    ~WorkerPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : threads_) t.join();
+        for (cudaStream_t st : streams_) cudaStreamDestroy(st);
+    }
+    int size() const { return (int)threads_.size(); }
+    // fn(i, stream) for i in [0, count); fn must not throw.
+    void run(int count, const std::function<void(int, cudaStream_t)> &fn) {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            fn_ = &fn;
+            count_ = count;
+            next_.store(0);
+            pending_ = (int)threads_.size();
+            gen_++;
+        }
+        cv_.notify_all();
+        std::unique_lock<std::mutex> lk(mu_);
+        done_cv_.wait(lk, [this]() { return pending_ == 0; });
+        fn_ = nullptr;
+    }
+
+  private:
+    void loop(int w) {
+        cudaSetDevice(dev_);
+        uint64_t seen = 0;
+        for (;;) {
+            const std::function<void(int, cudaStream_t)> *fn;
+            int count;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&]() { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+                fn = fn_;
+                count = count_;
+            }
+            for (;;) {
+                const int i = next_.fetch_add(1);
+                if (i >= count) break;
+                (*fn)(i, streams_[w]);
+            }
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--pending_ == 0) done_cv_.notify_all();
+        }
+    }
+    int dev_;
+    std::vector<std::thread> threads_;
+    std::vector<cudaStream_t> streams_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    const std::function<void(int, cudaStream_t)> *fn_ = nullptr;
+    std::atomic<int> next_{0};
+    int count_ = 0, pending_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+// ---------------------------------------------------------------------------
+// Engine
+// ---------------------------------------------------------------------------
+Engine::Engine(cudaStream_t s, int workers) : s_(s) {
+    if (workers > 0) {
+        int dev = 0;
+        CD_CUDA(cudaGetDevice(&dev));
+        pool_ = std::make_unique<WorkerPool>(workers, dev);
+    }
+}
+
+Engine::~Engine() = default;
+
+void Engine::add(Job *j) {
+    // job-owned labels live on the engine's stream: worker streams end with the engine
+    if (!j->spec.labels) {
+        j->own_labels.alloc(j->spec.g.n, s_);
+        CD_CUDA(cudaStreamSynchronize(s_));
+    }
+    active_.push_back(j);
+}
+
+void Engine::step() {
+    std::vector<Job *> act = active_;
+    if (pool_ && act.size() > 1) {
+        pool_->run((int)act.size(), [&](int i, cudaStream_t ws) { advance(*act[i], ws); });
+    } else {
+        for (Job *j : act) advance(*j, s_);
+    }
+    std::vector<PhaseRun *> runs;
+    for (Job *j : act) {
+        if (j->done) continue;
+        JobState &x = *j->state;
+        if (x.run) runs.push_back(x.run.get());
+        for (auto &r : x.base_runs) runs.push_back(r.get());
+    }
+    if (!runs.empty()) launch(runs);
+    active_.erase(std::remove_if(active_.begin(), active_.end(), [](Job *j) { return j->done; }), active_.end());
+}
+
+// Tiers of one launch: runs with the same smallest useful team size share a
+// tier; tiers get blocks in proportion to their work.
+struct LaunchPlan {
+    BatchArgs b{};
+    int grid = 0, nteams = 0;
+    std::vector<PhaseRun *> order;   // runs in tier order
+};
+
+static LaunchPlan plan_launch(std::vector<PhaseRun *> runs, int G) {
+    int64_t quantum = runs[0]->quantum;
+    int team_min = runs[0]->team_min;
+    for (const PhaseRun *r : runs) {
+        quantum = std::min(quantum, r->quantum);
+        team_min = std::max(team_min, r->team_min);
+    }
+    quantum = std::max<int64_t>(quantum, 1);
+    team_min = std::max(team_min, 1);
+    auto need = [&](const PhaseRun *r) {
+        const int64_t q = (r->work + quantum - 1) / quantum;
+        int t = 1;
+        while (t < q && t < G) t <<= 1;
+        return std::min(t, G);
+    };
+    std::stable_sort(runs.begin(), runs.end(), [&](const PhaseRun *x, const PhaseRun *y) {
+        const int nx = need(x), ny = need(y);
+        return nx != ny ? nx > ny : x->work > y->work;
+    });
+    struct T { int need, count = 0, blocks = 0, first = 0; double work = 0; };
+    std::vector<T> tiers;
+    for (int i = 0; i < (int)runs.size(); i++) {
+        const int nd = need(runs[i]);
+        if (tiers.empty() || tiers.back().need != nd) {
+            if ((int)tiers.size() == MAX_TIERS) {
+                // merge into the last tier (cannot happen for power-of-two sizes <= 2048)
+                tiers.back().count++;
+                tiers.back().work += (double)runs[i]->work + 1;
+                continue;
+            }
+            tiers.push_back(T{nd, 0, 0, i, 0});
+        }
+        tiers.back().count++;
+        tiers.back().work += (double)runs[i]->work + 1;
+    }
+    double W = 0;
+    for (auto &t : tiers) W += t.work;
+    int total = 0;
+    for (auto &t : tiers) {
+        t.blocks = std::max(1, (int)std::floor(G * t.work / W));
+        total += t.blocks;
+    }
+    while (total > G) {
+        int j = 0;
+        for (int i = 1; i < (int)tiers.size(); i++) if (tiers[i].blocks > tiers[j].blocks) j = i;
+        tiers[j].blocks--;
+        total--;
+    }
+    while (total < G) {
+        int j = 0;
+        for (int i = 1; i < (int)tiers.size(); i++)
+            if (tiers[i].work / tiers[i].blocks > tiers[j].work / tiers[j].blocks) j = i;
+        tiers[j].blocks++;
+        total++;
+    }
+    LaunchPlan p;
+    p.order = runs;
+    p.b.ntiers = (int32_t)tiers.size();
+    int begin = 0, team0 = 0;
+    for (int i = 0; i < (int)tiers.size(); i++) {
+        const T &t = tiers[i];
+        int ts = std::min(t.need, std::max(1, t.blocks / std::min(t.count, team_min)));
+        if ((int64_t)t.count * ts < t.blocks) ts = t.blocks / t.count;
+        const int teams = std::max(1, t.blocks / ts);
+        Tier &d = p.b.tiers[i];
+        d.begin = begin;
+        d.blocks = teams * ts;
+        d.team_size = ts;
+        d.team0 = team0;
+        d.first = t.first;
+        d.count = t.count;
+        begin += d.blocks;
+        team0 += teams;
+    }
+    p.grid = begin;
+    p.nteams = team0;
+    return p;
+}
+
+void Engine::launch(std::vector<PhaseRun *> &runs) {
+    const auto t = Clock::now();
+    // group by kernel instantiation, keeping the order of first appearance
+    std::vector<std::vector<PhaseRun *>> groups;
+    auto key = [](const PhaseRun *r) { return (r->plp ? 8 : 0) + r->wk * 2 + (r->big ? 1 : 0); };
+    for (PhaseRun *r : runs) {
+        bool placed = false;
+        for (auto &g : groups)
+            if (key(g[0]) == key(r)) { g.push_back(r); placed = true; break; }
+        if (!placed) groups.push_back({r});
+    }
+    struct Issued {
+        LaunchPlan plan;
+        DBuf<PhaseArgs> args;
+        DBuf<GridBarrier> bars;
+        DBuf<unsigned int> queues;
+        DBuf<int32_t> team_graph;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~Issued() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    };
+    std::vector<std::unique_ptr<Issued>> issued;
+    try {
+        for (auto &g : groups) {
+            const void *kern = g[0]->plp ? plp_batch_kernel(g[0]->wk, g[0]->big) : move_batch_kernel(g[0]->wk, g[0]->big);
+            const int G = persistent_grid(kern);
+            auto is = std::make_unique<Issued>();
+            is->plan = plan_launch(g, G);
+            LaunchPlan &p = is->plan;
+            std::vector<PhaseArgs> host(p.order.size());
+            for (size_t i = 0; i < p.order.size(); i++) host[i] = p.order[i]->a;
+            is->args.alloc(host.size(), s_);
+            CD_CUDA(cudaMemcpyAsync(is->args.p, host.data(), host.size() * sizeof(PhaseArgs), cudaMemcpyHostToDevice, s_));
+            is->bars.alloc(p.nteams, s_);
+            is->bars.zero();
+            is->queues.alloc(p.b.ntiers, s_);
+            is->queues.zero();
+            is->team_graph.alloc(p.nteams, s_);
+            p.b.graphs = is->args.p;
+            p.b.bars = is->bars.p;
+            p.b.queues = is->queues.p;
+            p.b.team_graph = is->team_graph.p;
+            bool prof = false;
+            for (PhaseRun *r : g) prof = prof || r->profile;
+            if (prof) {
+                CD_CUDA(cudaEventCreate(&is->e0));
+                CD_CUDA(cudaEventCreate(&is->e1));
+                CD_CUDA(cudaEventRecord(is->e0, s_));
+            }
+            launch_batch(kern, p.b, p.grid, s_);
+            if (prof) CD_CUDA(cudaEventRecord(is->e1, s_));
+            CD_CUDA(cudaStreamSynchronize(s_));   // host vector `host` goes out of scope
+            issued.push_back(std::move(is));
+            launches++;
+        }
+        CD_CUDA(cudaStreamSynchronize(s_));
+        const double wall = ms_since(t);
+        for (auto &is : issued) {
+            std::vector<GridBarrier> hb(is->plan.nteams);
+            CD_CUDA(cudaMemcpyAsync(hb.data(), is->bars.p, hb.size() * sizeof(GridBarrier), cudaMemcpyDeviceToHost, s_));
+            CD_CUDA(cudaStreamSynchronize(s_));
+            bool timeout = false;
+            for (const GridBarrier &b : hb) timeout = timeout || b.err != 0;
+            float ms = 0;
+            if (is->e0) CD_CUDA(cudaEventElapsedTime(&ms, is->e0, is->e1));
+            for (PhaseRun *r : is->plan.order) {
+                r->wall_ms = wall;
+                r->launch_ms = ms;
+                if (timeout) {
+                    r->fail = CD_ETIMEOUT;
+                    r->fail_msg = "a team barrier of the persistent kernel timed out";
+                }
+            }
+        }
+    } catch (const Error &e) {
+        for (PhaseRun *r : runs) {
+            r->fail = e.status;
+            r->fail_msg = e.msg;
+        }
+        cudaStreamSynchronize(s_);
+    }
+}
+
+void run_jobs(std::vector<Job *> &jobs, cudaStream_t s, int workers) {
+    Engine e(s, (int)jobs.size() > 1 ? workers : 0);
+    for (Job *j : jobs) e.add(j);
+    while (e.busy()) e.step();
+    for (Job *j : jobs)
+        if (j->status != CD_OK) raise(j->status, "%s", j->msg.c_str());
+}
+
+static void run_single(JobSpec sp, RunStats &st, cudaStream_t s) {
+    Job j(sp);
+    std::vector<Job *> v{&j};
+    run_jobs(v, s, 0);
+    st = j.st;
+}
+
+void run_plm(const GraphView &g, bool refine, const RunOpts &o, int32_t *labels, RunStats &st, cudaStream_t s) {
+    JobSpec sp;
+    sp.g = g;
+    sp.algo = ALGO_PLM;
+    sp.refine = refine;
+    sp.o = o;
+    sp.labels = labels;
+    run_single(sp, st, s);
+}
+
+void run_plp(const GraphView &g, const RunOpts &o, double theta, int32_t *labels, RunStats &st, cudaStream_t s) {
+    JobSpec sp;
+    sp.g = g;
+    sp.algo = ALGO_PLP;
+    sp.theta = theta;
+    sp.o = o;
+    sp.labels = labels;
+    run_single(sp, st, s);
+}
+
 void run_epp(const GraphView &g, int b, bool final_refine, const RunOpts &o, double theta, int32_t *labels,
              RunStats &st, cudaStream_t s) {
-    const auto t_all = Clock::now();
-    const int64_t n = g.n;
-    DBuf<int32_t> base((size_t)b * n, s), core(n, s);
-    for (int i = 0; i < b; i++) {
-        RunOpts oi = o;
-        oi.seed = o.seed + (uint64_t)i;
-        RunStats si;
-        run_plp(g, oi, theta, base.p + (size_t)i * n, si, s);
-        st.iters += si.iters;
-        st.moves += si.moves;
-        st.entries += si.entries;
-        st.candidates += si.candidates;
-        st.decisions += si.decisions;
-        st.k_ms += si.k_ms;
-        st.k_bytes += si.k_bytes;
-        st.k_launches += si.k_launches;
-        st.ms_color += si.ms_color;
-        st.ms_move += si.ms_move;
-        if (!si.converged) st.converged = 0;
-        if (i == 0) st.colors0 = si.colors0;
-    }
-    if (n) {
-        CD_CUDA(cudaMemcpyAsync(core.p, base.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-        for (int i = 1; i < b; i++) fold_core(core.p, base.p + (size_t)i * n, n, s);
-    }
-    auto t = Clock::now();
-    OwnedGraph cg;
-    DBuf<int64_t> rank(n, s);
-    coarsen_graph(g, core.p, rank.p, cg, s);
-    st.ms_coarsen += ms_since(t);
-    DBuf<int32_t> zc(cg.view.n, s);
-    RunStats sf;
-    run_plm(cg.view, final_refine, o, zc.p, sf, s);
-    st.levels = sf.levels;
-    st.sweeps += sf.sweeps;
-    st.moves += sf.moves;
-    st.entries += sf.entries;
-    st.candidates += sf.candidates;
-    st.decisions += sf.decisions;
-    st.k_ms += sf.k_ms;
-    st.k_bytes += sf.k_bytes;
-    st.k_launches += sf.k_launches;
-    for (int i = 0; i < 3; i++) st.stage_ms[i] += sf.stage_ms[i];
-    st.ms_color += sf.ms_color;
-    st.ms_move += sf.ms_move;
-    st.ms_coarsen += sf.ms_coarsen;
-    if (!sf.converged) st.converged = 0;
-    if (n) { k_gather_core<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(zc.p, core.p, n, labels); ::cd::note_launch(); }
-    CD_LAUNCH_CHECK();
-    st.ncomm = (int32_t)compact_labels(labels, n, s);
-    CD_CUDA(cudaStreamSynchronize(s));
-    st.ms_total += ms_since(t_all);
+    JobSpec sp;
+    sp.g = g;
+    sp.algo = ALGO_EPP;
+    sp.ensemble = b;
+    sp.refine = final_refine;
+    sp.theta = theta;
+    sp.o = o;
+    sp.labels = labels;
+    run_single(sp, st, s);
 }
 
 }  // namespace cd

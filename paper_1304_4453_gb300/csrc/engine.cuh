@@ -1,5 +1,14 @@
-// Host drivers of PLP, PLM/PLMR and EPP (engine.cu).
+// Host engine (engine.cu): jobs that run PLP (Algorithm 1), PLM / PLMR
+// (Algorithms 3, 4) or EPP (Algorithm 5) on one graph each.  A job advances
+// through its stages on a host worker thread (colouring, schedule,
+// coarsening, prolongation, compaction) until it needs a persistent phase
+// (a PLM move phase or a PLP run); every phase pending at that point joins
+// one batched launch, after which the jobs advance again.
 #pragma once
+#include <memory>
+#include <string>
+#include <vector>
+
 #include "common.cuh"
 
 namespace cd {
@@ -17,9 +26,70 @@ struct RunOpts {
     uint64_t seed = 1;
     int32_t max_sweeps = 256, max_levels = 64, max_iters = 1000;
     bool profile = false;
+    int64_t team_quantum = int64_t(1) << 18;   // launch shape (speed only)
+    int32_t team_min = 8;
 };
 
-// Labels are written to `labels` (device, g.n entries), compacted.
+enum Algo { ALGO_PLP = 0, ALGO_PLM = 1, ALGO_EPP = 2 };
+
+struct JobSpec {
+    GraphView g;
+    int algo = ALGO_PLM;
+    bool refine = false;        // PLM: PLMR; EPP: refinement in the final PLM
+    int ensemble = 1;           // EPP: number of PLP base runs
+    double theta = 0;           // PLP / EPP bases: stop once at most theta labels change
+    RunOpts o;
+    int32_t *labels = nullptr;  // device, g.n entries; nullptr: the job keeps its own
+    bool want_mod = false;      // compute the modularity of the result
+};
+
+struct JobState;
+
+struct Job {
+    JobSpec spec;
+    RunStats st;
+    cd_status status = CD_OK;   // CD_OK until a step fails
+    std::string msg;
+    bool done = false;
+    double mod = 0;
+    DBuf<int32_t> own_labels;   // used when spec.labels is nullptr
+    std::unique_ptr<JobState> state;
+    explicit Job(const JobSpec &s);
+    ~Job();
+    int32_t *labels() const { return spec.labels ? spec.labels : own_labels.p; }
+};
+
+struct PhaseRun;
+class WorkerPool;
+
+
+class Engine {
+  public:
+    // Batched launches run on `s`; `workers` host threads (0: the caller's
+    // thread, on `s`) advance the jobs.
+    Engine(cudaStream_t s, int workers);
+    ~Engine();
+    Engine(const Engine &) = delete;
+    Engine &operator=(const Engine &) = delete;
+    void add(Job *j);            // the caller keeps ownership; j stays valid until done
+    void step();                 // advances every unfinished job through one phase
+    bool busy() const { return !active_.empty(); }
+    size_t active() const { return active_.size(); }
+    int64_t launches = 0;        // batched launches so far
+
+  private:
+    void launch(std::vector<PhaseRun *> &runs);
+    cudaStream_t s_;
+    std::unique_ptr<WorkerPool> pool_;
+    std::vector<Job *> active_;
+};
+
+// Runs the jobs to completion; the first failure (in job order) is raised
+// after every job has stopped.
+void run_jobs(std::vector<Job *> &jobs, cudaStream_t s, int workers);
+
+// Single-graph drivers (one job on the caller's thread).  Labels are written
+// to `labels` (device, g.n entries), compacted.
 void run_plm(const GraphView &g, bool refine, const RunOpts &o, int32_t *labels, RunStats &st, cudaStream_t s);
 void run_plp(const GraphView &g, const RunOpts &o, double theta, int32_t *labels, RunStats &st, cudaStream_t s);
 void run_epp(const GraphView &g, int b, bool final_refine, const RunOpts &o, double theta, int32_t *labels,

@@ -1,17 +1,16 @@
-// Cooperative launches of the persistent phase kernels (move_plm.cu,
+// Cooperative launches of the persistent batch kernels (move_plm.cu,
 // move_plp.cu), instantiated per weight kind and gain width.
 #pragma once
 #include "phase.cuh"
 
 namespace cd {
 
-// Runs a whole PLM move phase; a.result receives {sweeps, converged, ...}.
-void launch_move_phase(int wk, bool big, const PhaseArgs &a, cudaStream_t s);
-// Runs a whole PLP; a.result receives {iterations, converged}.
-void launch_plp_run(int wk, bool big, const PhaseArgs &a, cudaStream_t s);
+// Batch kernel of a PLM move phase / a PLP run for a weight kind and gain width.
+const void *move_batch_kernel(int wk, bool big);
+const void *plp_batch_kernel(int wk, bool big);
 
-// Grid of a persistent kernel: every block resident at once (required by
-// the grid barrier), at most BARRIER_FAN * BARRIER_SUBS blocks.
+// Largest grid of a persistent kernel: every block resident at once
+// (required by the team barriers), at most BARRIER_FAN * BARRIER_SUBS blocks.
 inline int persistent_grid(const void *kernel) {
     int dev = 0, sms = 0, per_sm = 0;
     CD_CUDA(cudaGetDevice(&dev));
@@ -23,9 +22,9 @@ inline int persistent_grid(const void *kernel) {
     return g;
 }
 
-inline void launch_persistent(const void *kernel, const PhaseArgs &a, cudaStream_t s) {
-    const int grid = persistent_grid(kernel);
-    void *args[] = {const_cast<PhaseArgs *>(&a)};
+// grid must not exceed persistent_grid(kernel).
+inline void launch_batch(const void *kernel, const BatchArgs &b, int grid, cudaStream_t s) {
+    void *args[] = {const_cast<BatchArgs *>(&b)};
     CD_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kBlock), args, PHASE_SMEM, s));
     note_launch();
 }

@@ -1,13 +1,15 @@
-// Persistent kernels: one cooperative launch runs a whole PLM move phase
-// (every sweep, every colour class) or a whole PLP run (every iteration).
-// Colour classes follow each other in order, separated by grid barriers;
-// inside a class, blocks take work items (group / block / hub roles, then
-// hub-decide slices) in a grid-stride loop.  Late PLM sweeps end each class
-// with the sequential re-check, done by block 0 between two barriers.
+// Persistent kernels: one cooperative launch runs whole PLM move phases
+// (every sweep, every colour class) or whole PLP runs (every iteration) of
+// one or many graphs.  A team of blocks works on one graph at a time: colour
+// classes follow each other in order, separated by team barriers; inside a
+// class, the team's blocks take work items (group / block / hub roles, then
+// hub-decide slices) in a strided loop.  Late PLM sweeps end each class with
+// the sequential re-check, done by the team's first block between two
+// barriers.
 //
-// The grid barrier is a generation counter; a block that waits longer than
-// BARRIER_TIMEOUT_NS sets an error flag and every block leaves the kernel,
-// which the host reports as CD_ETIMEOUT.
+// The team barrier is a generation counter; a block that waits longer than
+// BARRIER_TIMEOUT_NS sets an error flag and the team's blocks leave the
+// kernel, which the host reports as CD_ETIMEOUT.
 #pragma once
 #include "move_kernels.cuh"
 
@@ -48,7 +50,6 @@ struct PhaseArgs {
     int32_t *part_id;
     uint32_t *part_tk;
     Counters *cnt;                         // one per sweep / iteration
-    GridBarrier *bar;
     int32_t *result;                       // [0] sweeps / iterations run, [1] converged
     // PLM
     int64_t *vol_a, *vol_b;                // launch t reads vol[t & 1], writes vol[(t+1) & 1]
@@ -603,18 +604,28 @@ __device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<P
 }
 
 // ---------------------------------------------------------------------------
-// Kernels.  Single graph: the whole grid is one team.  Batch: teams of
-// team_size consecutive blocks pull graph indices from a device queue and
-// run each graph's phase on their own barrier, so graphs of uneven size
-// share one launch.
+// Batch kernels.  The grid is cut into tiers of consecutive blocks; a tier's
+// blocks form teams of team_size blocks that pull graph indices from the
+// tier's queue and run each graph's phase on the team's own barrier.  A
+// single graph is one tier holding one team that spans the grid.  Graphs of
+// uneven size share one launch: each tier holds graphs of similar size, and
+// the host sizes tiers by their share of the work.
 // ---------------------------------------------------------------------------
+constexpr int MAX_TIERS = 16;
+
+struct Tier {
+    int32_t begin, blocks;     // block range [begin, begin + blocks)
+    int32_t team_size, team0;  // blocks per team; index of the tier's first team
+    int32_t first, count;      // graphs [first, first + count) of the batch
+};
+
 struct BatchArgs {
-    const PhaseArgs *graphs;   // device array
-    int32_t ngraphs;
-    int32_t team_size;
+    const PhaseArgs *graphs;   // device array, tier by tier
     GridBarrier *bars;         // one per team
-    unsigned int *queue;       // next graph index
+    unsigned int *queues;      // one per tier: next graph
     int32_t *team_graph;       // current graph of each team
+    int32_t ntiers;
+    Tier tiers[MAX_TIERS];
 };
 
 #define CD_BLOCK_SHARED(BT)                                                     \
@@ -623,70 +634,59 @@ struct BatchArgs {
     __shared__ unsigned s_cand, s_gen;                                          \
     __shared__ int s_last, s_ok, s_nb2;                                         \
     __shared__ SweepCtx s_ctx;                                                  \
+    __shared__ __align__(16) unsigned long long s_args[sizeof(PhaseArgs) / 8];  \
     if (threadIdx.x == 0) s_gen = 0;                                            \
     __syncthreads();                                                            \
     const BlockShared<BT> sh{smem, s_best, &s_cand, &s_gen, &s_last, &s_ok, &s_nb2, &s_ctx};
 
-template <int WK, bool BIG>
-__global__ void __launch_bounds__(kBlock, 4) k_move_phase(PhaseArgs a) {
-    CD_BLOCK_SHARED(PlmBest<BIG>)
-    const Team tm{(int32_t)blockIdx.x, (int32_t)gridDim.x, a.bar};
-    move_phase_body<WK, BIG>(a, tm, sh);
-}
-
-template <int WK, bool BIG>
-__global__ void __launch_bounds__(kBlock, 4) k_plp_run(PhaseArgs a) {
-    CD_BLOCK_SHARED(PlpBest)
-    const Team tm{(int32_t)blockIdx.x, (int32_t)gridDim.x, a.bar};
-    plp_body<WK, BIG>(a, tm, sh);
-}
-
-// Assigns the team's next graph; all blocks of the team read it after the barrier.
-__device__ __forceinline__ int32_t next_graph(const BatchArgs &b, const Team &tm, int32_t team, unsigned *s_gen,
-                                              int *s_ok) {
-    if (tm.rank == 0 && threadIdx.x == 0) b.team_graph[team] = (int32_t)atomicAdd(b.queue, 1u);
-    if (!team_sync(tm, s_gen, s_ok)) return -1;
-    const int32_t g = __ldcg(b.team_graph + team);
-    // everyone has read the assignment before it can change
-    if (!team_sync(tm, s_gen, s_ok)) return -1;
-    return g < b.ngraphs ? g : -1;
-}
-
 static_assert(sizeof(PhaseArgs) % 8 == 0, "PhaseArgs is copied in 64-bit words");
 
-// Copies a graph's arguments into shared memory (read many times per class).
-__device__ __forceinline__ void load_args(const PhaseArgs *src, unsigned long long *dst) {
-    const unsigned long long *w = reinterpret_cast<const unsigned long long *>(src);
-    for (int i = threadIdx.x; i < (int)(sizeof(PhaseArgs) / 8); i += blockDim.x) dst[i] = w[i];
+// This block's tier and team.
+__device__ __forceinline__ void find_team(const BatchArgs &b, int32_t *tier, int32_t *team, Team *tm) {
+    int32_t j = 0;
+    while (j + 1 < b.ntiers && (int32_t)blockIdx.x >= b.tiers[j + 1].begin) j++;
+    const Tier &t = b.tiers[j];
+    const int32_t r = (int32_t)blockIdx.x - t.begin;
+    *tier = j;
+    *team = t.team0 + r / t.team_size;
+    *tm = Team{r % t.team_size, t.team_size, b.bars + *team};
+}
+
+// The team's next graph (-1 when the tier's queue is empty or a barrier
+// failed); its arguments are copied into shared memory.
+__device__ __forceinline__ int32_t next_graph(const BatchArgs &b, int32_t tier, int32_t team, const Team &tm,
+                                              unsigned *s_gen, int *s_ok, unsigned long long *s_args) {
+    if (tm.rank == 0 && threadIdx.x == 0) b.team_graph[team] = (int32_t)atomicAdd(b.queues + tier, 1u);
+    if (!team_sync(tm, s_gen, s_ok)) return -1;
+    const int32_t q = __ldcg(b.team_graph + team);
+    // every block has read the assignment before the leader can replace it
+    if (!team_sync(tm, s_gen, s_ok)) return -1;
+    if (q >= b.tiers[tier].count) return -1;
+    const int32_t g = b.tiers[tier].first + q;
+    const unsigned long long *w = reinterpret_cast<const unsigned long long *>(b.graphs + g);
+    for (int i = threadIdx.x; i < (int)(sizeof(PhaseArgs) / 8); i += blockDim.x) s_args[i] = w[i];
     __syncthreads();
+    return g;
 }
 
 template <int WK, bool BIG>
 __global__ void __launch_bounds__(kBlock, 4) k_move_phase_batch(BatchArgs b) {
     CD_BLOCK_SHARED(PlmBest<BIG>)
-    const int32_t team = blockIdx.x / b.team_size;
-    const Team tm{(int32_t)(blockIdx.x % b.team_size), b.team_size, b.bars + team};
-    __shared__ __align__(16) unsigned long long s_args[sizeof(PhaseArgs) / 8];
-    while (true) {
-        const int32_t g = next_graph(b, tm, team, &s_gen, &s_ok);
-        if (g < 0) return;
-        load_args(b.graphs + g, s_args);
+    int32_t tier, team;
+    Team tm;
+    find_team(b, &tier, &team, &tm);
+    while (next_graph(b, tier, team, tm, &s_gen, &s_ok, s_args) >= 0)
         if (!move_phase_body<WK, BIG>(*reinterpret_cast<const PhaseArgs *>(s_args), tm, sh)) return;
-    }
 }
 
 template <int WK, bool BIG>
 __global__ void __launch_bounds__(kBlock, 4) k_plp_batch(BatchArgs b) {
     CD_BLOCK_SHARED(PlpBest)
-    const int32_t team = blockIdx.x / b.team_size;
-    const Team tm{(int32_t)(blockIdx.x % b.team_size), b.team_size, b.bars + team};
-    __shared__ __align__(16) unsigned long long s_args[sizeof(PhaseArgs) / 8];
-    while (true) {
-        const int32_t g = next_graph(b, tm, team, &s_gen, &s_ok);
-        if (g < 0) return;
-        load_args(b.graphs + g, s_args);
+    int32_t tier, team;
+    Team tm;
+    find_team(b, &tier, &team, &tm);
+    while (next_graph(b, tier, team, tm, &s_gen, &s_ok, s_args) >= 0)
         if (!plp_body<WK, BIG>(*reinterpret_cast<const PhaseArgs *>(s_args), tm, sh)) return;
-    }
 }
 
 }  // namespace cd

@@ -72,11 +72,44 @@ void dev_free(void *p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);  // never throws (destructors)
 }
 
+namespace {
+struct PinnedCache {
+    std::vector<std::pair<size_t, void *>> blocks;   // (capacity, pointer), free
+    ~PinnedCache() {
+        for (auto &b : blocks) cudaFreeHost(b.second);
+    }
+};
+thread_local PinnedCache t_pinned;
+constexpr size_t PINNED_KEEP = 16;   // free blocks kept per thread
+}  // namespace
+
 Pinned::Pinned(size_t bytes) {
-    CD_CUDA(cudaHostAlloc(&p, bytes ? bytes : 8, cudaHostAllocDefault));
+    auto &fl = t_pinned.blocks;
+    int best = -1;
+    for (int i = 0; i < (int)fl.size(); i++)
+        if (fl[i].first >= bytes && (best < 0 || fl[i].first < fl[best].first)) best = i;
+    if (best >= 0) {
+        cap = fl[best].first;
+        p = fl[best].second;
+        fl.erase(fl.begin() + best);
+        return;
+    }
+    cap = 256;
+    while (cap < bytes) cap <<= 1;
+    CD_CUDA(cudaHostAlloc(&p, cap, cudaHostAllocDefault));
 }
+
 Pinned::~Pinned() {
-    if (p) cudaFreeHost(p);
+    if (!p) return;
+    auto &fl = t_pinned.blocks;
+    if (fl.size() >= PINNED_KEEP) {
+        int small = 0;
+        for (int i = 1; i < (int)fl.size(); i++)
+            if (fl[i].first < fl[small].first) small = i;
+        cudaFreeHost(fl[small].second);
+        fl.erase(fl.begin() + small);
+    }
+    fl.push_back({cap, p});
 }
 
 }  // namespace cd
