@@ -42,6 +42,15 @@ def args_():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-run", action="store_true",
                    help="timed steps only (no e2e, PLP or CPU baseline): for ncu captures")
+    p.add_argument("--workload", default="plm", choices=["plm", "batch", "serve"],
+                   help="plm: R-MAT PLM (default); batch: 512 planted-partition graphs in one batched "
+                        "call vs one call per graph; serve: Poisson request stream, continuous-batching "
+                        "server vs a one-at-a-time FIFO server")
+    p.add_argument("--batch-graphs", type=int, default=512)
+    p.add_argument("--serve-requests", type=int, default=400)
+    p.add_argument("--serve-rate", type=float, default=200.0)
+    p.add_argument("--serve-pool", type=int, default=256)
+    p.add_argument("--serve-slots", type=int, default=64)
     return p.parse_args()
 
 
@@ -291,7 +300,7 @@ def run_ours(a):
     achieved = (k_bytes / 1e9) / (k_ms / 1e3) if k_ms > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "traffic": traffic_from_profiles(),
-            "kernel": "local-move decide kernels (k_decide_group/block, k_hub_*)",
+            "kernel": "k_move_phase_batch (persistent PLM move phase: every sweep and colour class)",
             "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
             "launches_timed": k_launches, "avg_launch_us": 1000.0 * k_ms / max(k_launches, 1),
@@ -329,10 +338,323 @@ def run_ours(a):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# batched workload: many planted-partition graphs in one call
+# ---------------------------------------------------------------------------
+
+BATCH_METRIC = "graphs/s (PLM on 512 planted-partition graphs, n log-uniform 1e3..1e6, one batched call)"
+
+
+def batch_graph_list(count, device):
+    from paper_1304_4453_gb300 import synth
+    return [(spec, lambda spec=spec: synth.planted_partition_fast(spec[0], spec[1], spec[2], spec[3],
+                                                                  seed=spec[4], device=device))
+            for spec in synth.batch_planted_specs(count)]
+
+
+def batch_config(count, n_tot, m_tot):
+    return {"workload": f"batch{count}_planted_partition_plm",
+            "graphs": f"{count} planted-partition graphs, seeds 1000+j, n log-uniform in [1e3, 1e6], "
+                      "k uniform in [8, 64], p_in/p_out = 20, expected average degree 16, unit weights",
+            "n_total": n_tot, "m_total": m_tot,
+            "algorithm": "PLM (Algorithms 2-3) on every graph, seed 1",
+            "l2": "inputs larger than L2 (the batch's adjacency is several GB); no flush",
+            "parallelism": "replicas"}
+
+
+def run_batch_workload(a):
+    import torch
+    from paper_1304_4453_gb300 import build, cd
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    cd.lib()
+    t0 = time.perf_counter()
+    Gs = []
+    for spec, make in batch_graph_list(a.batch_graphs, dev):
+        g = make()
+        Gs.append(cd.Graph(g.row_ptr, g.col, g.w))
+        del g
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    n_tot = sum(G.n for G in Gs)
+    m_tot = sum(G.m for G in Gs)
+    handles = [G.h for G in Gs]
+    outs_plain = [torch.empty(max(G.n, 1), dtype=torch.int32, device=dev)[:G.n] for G in Gs]
+    outs_batch = [torch.empty(max(G.n, 1), dtype=torch.int32, device=dev)[:G.n] for G in Gs]
+    task = cd.make_task(cd.CD_ALGO_PLM)
+    opts = cd.default_opts(seed=1)
+
+    def plain_pass():
+        for G, o in zip(Gs, outs_plain):
+            cd.cd_plm(G.h, o, False, opts)
+
+    for _ in range(a.warmup):
+        cd.cd_run_batch(handles, task, outs_batch, opts)
+    plain_pass()   # warm-up of the one-call-per-graph path
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    l0 = cd.cd_launch_count()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        mods, sts, status = cd.cd_run_batch(handles, task, outs_batch, opts)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = cd.cd_launch_count() - l0
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    t = time.perf_counter()
+    plain_pass()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t
+    same = all(torch.equal(x, y) for x, y in zip(outs_plain, outs_batch))
+    value = len(Gs) / (ms / 1000.0)
+    # end to end: host CSR in pinned memory -> handles -> batched run -> labels to host, every step
+    host = []
+    for G in Gs:
+        rp, col, w = cd.cd_graph_export(G.h)
+        host.append((torch.from_numpy(rp).pin_memory(), torch.from_numpy(col).pin_memory()))
+    lab_h = [torch.empty(G.n, dtype=torch.int32).pin_memory() for G in Gs]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    hs = [cd.cd_graph_create(rp, col, None) for rp, col in host]
+    cd.cd_run_batch(hs, task, lab_h, opts)
+    for h in hs:
+        cd.cd_graph_destroy(h)
+    e2e_s = time.perf_counter() - t
+    e2e_same = all(torch.equal(lh, ob.cpu()) for lh, ob in zip(lab_h, outs_batch))
+    h2d = sum(8 * (G.n + 1) + 4 * 2 * G.m for G in Gs)
+    if rank != 0:
+        return
+    line = {
+        "metric": BATCH_METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": batch_config(len(Gs), n_tot, m_tot),
+        "plain": {"graphs_per_s": len(Gs) / plain_s, "s": plain_s,
+                  "how": "one cd_plm call per graph, in order, same handles and options"},
+        "speedup_vs_plain": (len(Gs) / (ms / 1000.0)) / (len(Gs) / plain_s),
+        "edges_per_s": m_tot / (ms / 1000.0),
+        "labels_identical_to_plain": same,
+        "mean_modularity": sum(mods) / len(mods),
+        "e2e": {"value": len(Gs) / e2e_s, "unit": "graphs/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 4 * n_tot, "labels_match_device_run": e2e_same},
+        "gpu_launches": launches / a.steps,
+        "generation_s": gen_s,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# serving workload: Poisson request stream
+# ---------------------------------------------------------------------------
+
+SERVE_METRIC = "graphs/s and p50/p99 latency (Poisson stream, R-MAT 14-22 and planted partitions 1e3-4e6, PLM)"
+
+
+def serve_pool_specs(count):
+    """(kind, params, seed) of the pool: even j R-MAT with scale uniform in
+    14..22, odd j planted partition with n log-uniform in [1e3, 4e6], k uniform
+    in [8, 64], expected degree 16."""
+    import math as _m
+    import torch
+    from paper_1304_4453_gb300 import synth
+    out = []
+    for j in range(count):
+        sd = 5000 + j
+        r = synth.rand_u53(sd, 0x5E7E, torch.arange(3, dtype=torch.int64)).tolist()
+        if j % 2 == 0:
+            out.append(("rmat", 14 + r[0] % 9, sd))
+        else:
+            u = r[1] / float(1 << 53)
+            n = int(round(_m.exp(_m.log(1e3) + u * (_m.log(4e6) - _m.log(1e3)))))
+            k = 8 + r[2] % 57
+            s = n / k
+            p_out = 16.0 / (20.0 * (s - 1) + (n - s))
+            out.append(("pp", (n, k, min(1.0, 20 * p_out), p_out), sd))
+    return out
+
+
+def serve_requests(count, rate, pool):
+    """Arrival times (s, exponential gaps, seed 7) and pool indices."""
+    import math as _m
+    import torch
+    from paper_1304_4453_gb300 import synth
+    idx = torch.arange(count, dtype=torch.int64)
+    u = synth.rand_unit(7, 0xA771, idx).tolist()
+    pick = synth.rand_u53(7, 0x9001, idx).tolist()
+    t, arr = 0.0, []
+    for x in u:
+        t += -_m.log1p(-x) / rate
+        arr.append(t)
+    return arr, [p % pool for p in pick]
+
+
+def run_serve_workload(a):
+    import torch
+    from paper_1304_4453_gb300 import build, cd, synth
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    cd.lib()
+    t0 = time.perf_counter()
+    pool = []
+    for kind, par, sd in serve_pool_specs(a.serve_pool):
+        if kind == "rmat":
+            g = synth.rmat(par, EDGE_FACTOR, *ABC, seed=sd, device=dev)
+        else:
+            g = synth.planted_partition_fast(*par, seed=sd, device=dev)
+        pool.append(cd.Graph(g.row_ptr, g.col, g.w))
+        del g
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    arrivals, picks = serve_requests(a.serve_requests, a.serve_rate, len(pool))
+    opts = cd.default_opts(seed=1)
+    # warm-up: one run of every size class through both paths
+    for G in pool[:4]:
+        G.plm()
+
+    def pct(xs, q):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, int(q * len(xs)))]
+
+    # plain FIFO server: one request at a time, in arrival order
+    ref_labels = {}
+    lat_plain = []
+    torch.cuda.synchronize()
+    base = time.perf_counter()
+    for arr, p in zip(arrivals, picks):
+        now = time.perf_counter() - base
+        if now < arr:
+            time.sleep(arr - now)
+        G = pool[p]
+        out = torch.empty(max(G.n, 1), dtype=torch.int32, device=dev)[:G.n]
+        cd.cd_plm(G.h, out, False, opts)
+        lat_plain.append(time.perf_counter() - base - arr)
+        ref_labels.setdefault(p, out)
+    plain_span = time.perf_counter() - base
+    # continuous-batching server
+    S = cd.Server(max_slots=a.serve_slots, max_queue=max(a.serve_requests, 1))
+    sampler = ClockSampler(local)
+    l0 = cd.cd_launch_count()
+    tickets = []
+    base = time.perf_counter()
+    for arr, p in zip(arrivals, picks):
+        now = time.perf_counter() - base
+        if now < arr:
+            time.sleep(arr - now)
+        ts = time.perf_counter() - base
+        tickets.append((ts, S.submit(pool[p], cd.CD_ALGO_PLM, seed=1)))
+    lat_srv, same, done_at = [], True, []
+    for (ts, tk), arr, p in zip(tickets, arrivals, picks):
+        G = pool[p]
+        out = torch.empty(max(G.n, 1), dtype=torch.int32, device=dev)[:G.n]
+        status, mod, lat_ms, st = S.poll(tk, out, timeout_ms=-1)
+        done = ts + lat_ms / 1000.0
+        done_at.append(done)
+        lat_srv.append(done - arr)
+        same = same and torch.equal(out, ref_labels[p])
+    srv_span = max(done_at)
+    launches = cd.cd_launch_count() - l0
+    clocks = sampler.stop()
+    S.close()
+    if rank != 0:
+        return
+    nreq = len(arrivals)
+    m_req = sum(pool[p].m for p in picks)
+    line = {
+        "metric": SERVE_METRIC, "value": nreq / srv_span, "unit": "graphs/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": 1000.0 * srv_span, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"serve{nreq}_poisson{a.serve_rate:g}",
+                   "requests": f"first {nreq} requests of a Poisson stream (rate {a.serve_rate:g}/s, seed 7), "
+                               f"each a PLM run on one of {len(pool)} pooled graphs: even pool slots R-MAT "
+                               "scale uniform 14..22 ef16, odd slots planted partition n log-uniform "
+                               "[1e3, 4e6], k in [8, 64], degree 16",
+                   "edges_requested": m_req, "slots": a.serve_slots,
+                   "l2": "inputs larger than L2 for most requests; no flush", "parallelism": "replicas"},
+        "latency_ms": {"p50": 1000 * pct(lat_srv, 0.5), "p99": 1000 * pct(lat_srv, 0.99),
+                       "max": 1000 * max(lat_srv)},
+        "plain_fifo": {"graphs_per_s": nreq / plain_span, "p50_ms": 1000 * pct(lat_plain, 0.5),
+                       "p99_ms": 1000 * pct(lat_plain, 0.99)},
+        "labels_identical_to_plain": same,
+        "e2e": {"value": nreq / srv_span, "unit": "graphs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0,
+                "note": "requests reference resident graphs; labels stay on the device"},
+        "gpu_launches": launches, "generation_s": gen_s, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_other(a):
+    """Oracle arm of the batch and serve workloads: sequential oracle PLM on a
+    bounded prefix of the same graphs."""
+    rank, local, world = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_1304_4453_gb300 import synth
+    oracle.build()
+    # (expected edges, generator) per graph of the workload, in order
+    if a.workload == "batch":
+        makers = [(8 * spec[0], m) for spec, m in batch_graph_list(a.batch_graphs, "cpu")]
+        metric, cfg = BATCH_METRIC, {"workload": f"batch{a.batch_graphs}_planted_partition_plm"}
+    else:
+        pool = serve_pool_specs(a.serve_pool)
+        _, picks = serve_requests(a.serve_requests, a.serve_rate, len(pool))
+
+        def mk(kind, par, sd):
+            if kind == "rmat":
+                return EDGE_FACTOR << par, lambda: synth.rmat(par, EDGE_FACTOR, *ABC, seed=sd)
+            return 8 * par[0], lambda: synth.planted_partition_fast(*par, seed=sd)
+        makers = [mk(*pool[p]) for p in picks]
+        metric, cfg = SERVE_METRIC, {"workload": f"serve{a.serve_requests}_poisson{a.serve_rate:g}"}
+    times, count, budget = [], 0, 20.0
+    for i in range(a.warmup + a.steps):
+        tot, cnt = 0.0, 0
+        for est, make in makers:
+            if est > 2_000_000:
+                continue   # keep the sample bounded: graphs above about 2M edges are skipped
+            rp, c, w = make().numpy()
+            t = time.perf_counter()
+            oracle.plm(rp, c, w, seed=1)
+            tot += time.perf_counter() - t
+            cnt += 1
+            if tot > budget / max(a.steps + a.warmup, 1):
+                break
+        if i >= a.warmup:
+            times.append(tot)
+            count += cnt
+    value = count / sum(times)
+    sample = (f"sequential oracle PLM on the workload's graphs in order, skipping those above about 2M edges, "
+              f"until {budget / max(a.steps + a.warmup, 1):.1f} s per step")
+    print(json.dumps({
+        "impl": "reference", "metric": metric, "value": value, "unit": "graphs/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model(), "nproc": os.cpu_count()},
+        "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
 def main():
     a = args_()
     if a.impl == "reference":
-        run_reference(a)
+        if a.workload == "plm":
+            run_reference(a)
+        else:
+            run_reference_other(a)
+    elif a.workload == "batch":
+        run_batch_workload(a)
+    elif a.workload == "serve":
+        run_serve_workload(a)
     else:
         run_ours(a)
 

@@ -510,7 +510,18 @@ struct JobState {
 };
 
 Job::Job(const JobSpec &s) : spec(s), state(std::make_unique<JobState>()) {}
-Job::~Job() = default;
+
+void Job::release() {
+    state.reset();   // stream-ordered frees on `stream`
+    if (own_stream) {
+        cudaStreamSynchronize(stream);
+        cudaStreamDestroy(stream);
+        own_stream = false;
+    }
+    stream = nullptr;
+}
+
+Job::~Job() { release(); }
 
 // Level `L.back()`: schedule, singleton labels, move phase.
 static void start_level(Job &j, cudaStream_t s) {
@@ -674,8 +685,6 @@ static void advance_impl(Job &j, cudaStream_t s) {
             if (sp.want_mod) j.mod = modularity(sp.g, j.labels(), s);
             CD_CUDA(cudaStreamSynchronize(s));
             st.ms_total += ms_since(x.t0);
-            x.cg = OwnedGraph();
-            x.core.release();
             j.done = true;
             return;
         }
@@ -683,11 +692,14 @@ static void advance_impl(Job &j, cudaStream_t s) {
     }
 }
 
-static void advance(Job &j, cudaStream_t s) {
+static std::atomic<int64_t> g_fail_order{0};
+
+static void advance(Job &j) {
     if (j.done) return;
     try {
-        advance_impl(j, s);
-        CD_CUDA(cudaStreamSynchronize(s));   // the next step may use another stream
+        advance_impl(j, j.stream);
+        // the batched launch (another stream) reads what this step wrote
+        CD_CUDA(cudaStreamSynchronize(j.stream));
     } catch (const Error &e) {
         j.status = e.status;
         j.msg = e.msg;
@@ -696,10 +708,10 @@ static void advance(Job &j, cudaStream_t s) {
         j.msg = "host allocation failed";
     }
     if (j.status != CD_OK) {
-        j.state.reset();   // frees the job's device memory (stream-ordered)
-        cudaStreamSynchronize(s);
+        j.fail_order = g_fail_order.fetch_add(1);
         j.done = true;
     }
+    if (j.done) j.release();
 }
 
 // ---------------------------------------------------------------------------
@@ -708,12 +720,7 @@ static void advance(Job &j, cudaStream_t s) {
 class WorkerPool {
   public:
     WorkerPool(int n, int device) : dev_(device) {
-        for (int w = 0; w < n; w++) {
-            cudaStream_t st;
-            CD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-            streams_.push_back(st);
-        }
-        for (int w = 0; w < n; w++) threads_.emplace_back([this, w]() { loop(w); });
+        for (int w = 0; w < n; w++) threads_.emplace_back([this]() { loop(); });
     }
     ~WorkerPool() {
         {
@@ -722,11 +729,10 @@ class WorkerPool {
         }
         cv_.notify_all();
         for (auto &t : threads_) t.join();
-        for (cudaStream_t st : streams_) cudaStreamDestroy(st);
     }
     int size() const { return (int)threads_.size(); }
-    // fn(i, stream) for i in [0, count); fn must not throw.
-    void run(int count, const std::function<void(int, cudaStream_t)> &fn) {
+    // fn(i) for i in [0, count); fn must not throw.
+    void run(int count, const std::function<void(int)> &fn) {
         {
             std::lock_guard<std::mutex> lk(mu_);
             fn_ = &fn;
@@ -742,11 +748,11 @@ class WorkerPool {
     }
 
   private:
-    void loop(int w) {
+    void loop() {
         cudaSetDevice(dev_);
         uint64_t seen = 0;
         for (;;) {
-            const std::function<void(int, cudaStream_t)> *fn;
+            const std::function<void(int)> *fn;
             int count;
             {
                 std::unique_lock<std::mutex> lk(mu_);
@@ -759,7 +765,7 @@ class WorkerPool {
             for (;;) {
                 const int i = next_.fetch_add(1);
                 if (i >= count) break;
-                (*fn)(i, streams_[w]);
+                (*fn)(i);
             }
             std::lock_guard<std::mutex> lk(mu_);
             if (--pending_ == 0) done_cv_.notify_all();
@@ -767,10 +773,9 @@ class WorkerPool {
     }
     int dev_;
     std::vector<std::thread> threads_;
-    std::vector<cudaStream_t> streams_;
     std::mutex mu_;
     std::condition_variable cv_, done_cv_;
-    const std::function<void(int, cudaStream_t)> *fn_ = nullptr;
+    const std::function<void(int)> *fn_ = nullptr;
     std::atomic<int> next_{0};
     int count_ = 0, pending_ = 0;
     uint64_t gen_ = 0;
@@ -791,10 +796,16 @@ Engine::Engine(cudaStream_t s, int workers) : s_(s) {
 Engine::~Engine() = default;
 
 void Engine::add(Job *j) {
-    // job-owned labels live on the engine's stream: worker streams end with the engine
+    // labels the job keeps after it finishes live on the engine's stream
     if (!j->spec.labels) {
         j->own_labels.alloc(j->spec.g.n, s_);
         CD_CUDA(cudaStreamSynchronize(s_));
+    }
+    if (pool_) {
+        CD_CUDA(cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking));
+        j->own_stream = true;
+    } else {
+        j->stream = s_;
     }
     active_.push_back(j);
 }
@@ -802,9 +813,9 @@ void Engine::add(Job *j) {
 void Engine::step() {
     std::vector<Job *> act = active_;
     if (pool_ && act.size() > 1) {
-        pool_->run((int)act.size(), [&](int i, cudaStream_t ws) { advance(*act[i], ws); });
+        pool_->run((int)act.size(), [&](int i) { advance(*act[i]); });
     } else {
-        for (Job *j : act) advance(*j, s_);
+        for (Job *j : act) advance(*j);
     }
     std::vector<PhaseRun *> runs;
     for (Job *j : act) {
@@ -993,8 +1004,10 @@ void run_jobs(std::vector<Job *> &jobs, cudaStream_t s, int workers) {
     Engine e(s, (int)jobs.size() > 1 ? workers : 0);
     for (Job *j : jobs) e.add(j);
     while (e.busy()) e.step();
-    for (Job *j : jobs)
-        if (j->status != CD_OK) raise(j->status, "%s", j->msg.c_str());
+    const Job *first = nullptr;
+    for (const Job *j : jobs)
+        if (j->status != CD_OK && (!first || j->fail_order < first->fail_order)) first = j;
+    if (first) raise(first->status, "%s", first->msg.c_str());
 }
 
 static void run_single(JobSpec sp, RunStats &st, cudaStream_t s) {

@@ -45,17 +45,25 @@ struct JobSpec {
 
 struct JobState;
 
+// A job's kernels, copies and stream-ordered allocations all go to one
+// stream for the job's whole life, whichever host thread advances it, so a
+// buffer freed by the job is never reused while the job's own earlier work
+// on it is still queued.
 struct Job {
     JobSpec spec;
     RunStats st;
     cd_status status = CD_OK;   // CD_OK until a step fails
     std::string msg;
+    int64_t fail_order = -1;    // order of the failure among all jobs (earliest first)
     bool done = false;
     double mod = 0;
     DBuf<int32_t> own_labels;   // used when spec.labels is nullptr
     std::unique_ptr<JobState> state;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
     explicit Job(const JobSpec &s);
     ~Job();
+    void release();             // frees the job's working memory and stream
     int32_t *labels() const { return spec.labels ? spec.labels : own_labels.p; }
 };
 
@@ -84,8 +92,8 @@ class Engine {
     std::vector<Job *> active_;
 };
 
-// Runs the jobs to completion; the first failure (in job order) is raised
-// after every job has stopped.
+// Runs the jobs to completion; the earliest failure is raised after every
+// job has stopped.
 void run_jobs(std::vector<Job *> &jobs, cudaStream_t s, int workers);
 
 // Single-graph drivers (one job on the caller's thread).  Labels are written

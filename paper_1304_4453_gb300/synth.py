@@ -257,6 +257,51 @@ def planted_partition(n: int, k: int, p_in: float, p_out: float, seed: int = 1,
     return csr_from_undirected(n, a, b, None, name=f"pp_n{n}_k{len(sizes)}")
 
 
+def _tri_rc(pos: torch.Tensor):
+    """Strictly-lower-triangle index -> (r, c) with r > c >= 0."""
+    r = torch.floor((1.0 + torch.sqrt(1.0 + 8.0 * pos.to(torch.float64))) / 2.0).to(torch.int64)
+    r = torch.where(r * (r - 1) // 2 > pos, r - 1, r)
+    r = torch.where((r + 1) * r // 2 <= pos, r + 1, r)
+    return r, pos - r * (r - 1) // 2
+
+
+def planted_partition_fast(n: int, k: int, p_in: float, p_out: float, seed: int = 1,
+                           device="cpu") -> Graph:
+    """G(n, p_in, p_out) with k equal blocks (remainder spread over the first
+    blocks), sampled in two passes instead of one per block pair: the
+    intra-block pairs of all blocks, laid end to end, with probability p_in,
+    and every unordered pair with probability p_out, keeping only pairs whose
+    ends lie in different blocks.  Each pair is still an edge independently
+    with p_in inside a block and p_out across (same distribution as
+    ``planted_partition``, different random stream), with a few large
+    operations per graph, so big batches generate quickly on a GPU."""
+    sizes = _block_sizes(n, k)
+    sz = torch.tensor(sizes, dtype=torch.int64, device=device)
+    starts = torch.cumsum(sz, 0) - sz
+    tri = sz * (sz - 1) // 2
+    tri_end = torch.cumsum(tri, 0)
+    us, vs = [], []
+    total_in = int(tri_end[-1]) if k > 0 else 0
+    if total_in > 0 and p_in > 0.0:
+        pos = _skip_sample(total_in, p_in, seed, 0x0F00001, device)
+        blk = torch.searchsorted(tri_end, pos, right=True)
+        r, c = _tri_rc(pos - (tri_end[blk] - tri[blk]))
+        us.append(starts[blk] + r)
+        vs.append(starts[blk] + c)
+    if n > 1 and p_out > 0.0:
+        pos = _skip_sample(n * (n - 1) // 2, p_out, seed, 0x0F00002, device)
+        r, c = _tri_rc(pos)
+        ends = starts + sz
+        cross = torch.searchsorted(ends, r, right=True) != torch.searchsorted(ends, c, right=True)
+        us.append(r[cross])
+        vs.append(c[cross])
+    if us:
+        a, b = torch.cat(us), torch.cat(vs)
+    else:
+        a = b = torch.zeros(0, dtype=torch.int64, device=device)
+    return csr_from_undirected(n, a, b, None, name=f"ppf_n{n}_k{k}")
+
+
 def _skip_sample(npairs: int, p: float, seed: int, stream: int, device) -> torch.Tensor:
     """Sorted positions in [0, npairs) kept with probability p (geometric gaps)."""
     if p >= 1.0:

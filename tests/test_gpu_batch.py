@@ -101,18 +101,21 @@ def test_launch_shape_changes_nothing(quantum, team_min):
 
 
 def test_batch_many_small_graphs():
+    """Many jobs on many host threads over several levels each (the stream
+    a job's buffers are freed on must order after the job's own work)."""
     rng = np.random.default_rng(11)
     specs = []
-    for j in range(48):
-        n = int(np.exp(rng.uniform(np.log(200), np.log(8000))))
+    for j in range(96):
+        n = int(np.exp(rng.uniform(np.log(200), np.log(50000))))
         k = int(rng.integers(4, 17))
         s = n // k
         p_out = 16 / (20 * (s - 1) + n - s)
         specs.append(synth.planted_partition(n, k, min(1.0, 20 * p_out), p_out, seed=1000 + j))
     Gs = [cd.Graph.from_synth(g, device="cuda") for g in specs]
-    res = cd.run_batch(Gs, cd.CD_ALGO_PLM, False, seed=1)
-    for G, r in zip(Gs, res):
-        _same(r, G.plm(seed=1))
+    for refine in (False, True):
+        res = cd.run_batch(Gs, cd.CD_ALGO_PLM, refine, seed=1)
+        for G, r in zip(Gs, res):
+            _same(r, G.plm(refine=refine, seed=1))
 
 
 def test_batch_repeated_handle_and_host_labels():
