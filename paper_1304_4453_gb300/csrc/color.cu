@@ -14,11 +14,14 @@
 // count and once when its row's vertex is coloured (plus a rescan per extra
 // window of 64 colours).  Frontier vertices of degree <= 64 are handled by one
 // warp each, up to 4096 by one block each, and the adjacency of larger ones
-// is cut into chunks spread over all blocks (k_color_round_hubs): a round
-// lasts as long as its slowest vertex.  Rounds run back to back on
-// the device (frontier lengths live in device memory); the host checks for
-// completion every few rounds.
-#include "common.cuh"
+// is cut into chunks spread over all blocks (color_hub_items): a round lasts
+// as long as its slowest vertex.  All rounds run inside one persistent
+// cooperative kernel, separated by a grid barrier; the frontiers rotate over
+// three buffers so that the buffer a round pushes into was cleared a round
+// earlier, and the kernel stops at the first round whose frontier is empty.
+#include <algorithm>
+
+#include "barrier.cuh"
 
 namespace cd {
 
@@ -82,18 +85,12 @@ __device__ __forceinline__ unsigned long long window_bits(const int64_t *rp, con
     return b;
 }
 
-// One warp per frontier vertex (degree <= COLOR_BIG_DEG).
-__global__ void k_color_round_warp(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                   const uint32_t *__restrict__ hash, const int32_t *list,
-                                   const unsigned long long *count_in, int32_t *wait, int32_t *color, Frontier nf,
-                                   unsigned long long *done) {
-    __shared__ int64_t s_count;
+// One warp per frontier vertex (degree <= COLOR_WARP_DEG).
+__device__ __forceinline__ void color_warp_items(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                                 const uint32_t *__restrict__ hash, const int32_t *list,
+                                                 int64_t count, int32_t *wait, int32_t *color, const Frontier &nf,
+                                                 unsigned long long *done) {
     const int lane = threadIdx.x & 31;
-    // one read of the frontier length per block: every warp reading it would
-    // queue thousands of requests on one L2 line
-    if (threadIdx.x == 0) s_count = (int64_t)*count_in;
-    __syncthreads();
-    const int64_t count = s_count;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < count; i += nwarps) {
@@ -125,15 +122,10 @@ __global__ void k_color_round_warp(const int64_t *__restrict__ rp, const int32_t
 }
 
 // One block per frontier vertex (COLOR_WARP_DEG < degree <= COLOR_BIG_DEG).
-__global__ void k_color_round_block(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                    const uint32_t *__restrict__ hash, const int32_t *list,
-                                    const unsigned long long *count_in, int32_t *wait, int32_t *color, Frontier nf,
-                                    unsigned long long *done) {
-    __shared__ unsigned long long sbits;
-    __shared__ int64_t s_count;
-    if (threadIdx.x == 0) s_count = (int64_t)*count_in;
-    __syncthreads();
-    const int64_t count = s_count;
+__device__ __forceinline__ void color_block_items(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                                  const uint32_t *__restrict__ hash, const int32_t *list,
+                                                  int64_t count, int32_t *wait, int32_t *color, const Frontier &nf,
+                                                  unsigned long long *done, unsigned long long &sbits) {
     for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
         const int32_t v = list[i];
         const uint32_t hv = hash[v];
@@ -184,18 +176,19 @@ constexpr int COLOR_CHUNK = 2048;
 constexpr int COLOR_BITS = 4096;
 constexpr int COLOR_WORDS = COLOR_BITS / 32;
 
-__global__ void k_color_round_hubs(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                   const uint32_t *__restrict__ hash, const int32_t *list,
-                                   const unsigned long long *count_in, const int32_t *hub_slot, uint32_t *bitmaps,
-                                   unsigned int *chunks_done, int32_t *wait, int32_t *color, Frontier nf,
-                                   unsigned long long *done) {
-    __shared__ uint32_t sbm[COLOR_WORDS];
-    __shared__ int s_last;
-    __shared__ unsigned long long sbits;
-    __shared__ int64_t s_count;
-    if (threadIdx.x == 0) s_count = (int64_t)*count_in;
-    __syncthreads();
-    const int64_t count = s_count;
+struct HubShared {
+    uint32_t sbm[COLOR_WORDS];
+    int last;
+};
+
+__device__ __forceinline__ void color_hub_items(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                                const uint32_t *__restrict__ hash, const int32_t *list,
+                                                int64_t count, const int32_t *hub_slot, uint32_t *bitmaps,
+                                                unsigned int *chunks_done, int32_t *wait, int32_t *color,
+                                                const Frontier &nf, unsigned long long *done, HubShared &hs,
+                                                unsigned long long &sbits) {
+    uint32_t *sbm = hs.sbm;
+    int &s_last = hs.last;
     int64_t item0 = 0;
     for (int64_t i = 0; i < count; i++) {
         const int32_t v = list[i];
@@ -273,21 +266,79 @@ __global__ void k_color_max(const int32_t *color, int64_t n, unsigned int *maxc)
     if ((threadIdx.x & 31) == 0) atomicMax(maxc, m);
 }
 
+// Every round of the colouring in one cooperative launch.  Frontier side r%3
+// is read in round r, side (r+1)%3 receives the next frontier, and block 0
+// clears side (r+2)%3, which round r-1 read and round r+1 fills.  All blocks
+// leave together at the first round whose frontier is empty (every vertex is
+// coloured then), or after max_rounds rounds.
+struct ColorArgs {
+    const int64_t *rp;
+    const int32_t *col;
+    const uint32_t *hash;
+    int64_t n;
+    int32_t *wait, *color;
+    int32_t *lists;                // [3 sides][3 tiers][n]
+    unsigned long long *counts;    // [3 sides][3 tiers]
+    unsigned long long *done;
+    const int32_t *hub_slot;
+    uint32_t *bitmaps;
+    unsigned int *chunks_done;
+    GridBarrier *bar;
+    int64_t max_rounds;
+    int64_t *rounds;               // out: rounds run
+};
+
+__device__ __forceinline__ Frontier frontier_side(const ColorArgs &a, int side) {
+    Frontier f;
+    for (int t = 0; t < 3; t++) {
+        f.list[t] = a.lists + (size_t)(3 * side + t) * a.n;
+        f.count[t] = a.counts + 3 * side + t;
+    }
+    return f;
+}
+
+__global__ void __launch_bounds__(kBlock) k_color_persistent(ColorArgs a) {
+    __shared__ unsigned s_gen;
+    __shared__ int s_ok;
+    __shared__ unsigned long long s_cnt[3];
+    __shared__ unsigned long long sbits;
+    __shared__ HubShared hs;
+    const Team tm{(int32_t)blockIdx.x, (int32_t)gridDim.x, a.bar};
+    if (threadIdx.x == 0) s_gen = 0;
+    __syncthreads();
+    int64_t r = 0;
+    for (;; r++) {
+        const int cur = (int)(r % 3), nx = (int)((r + 1) % 3), old = (int)((r + 2) % 3);
+        if (threadIdx.x < 3) s_cnt[threadIdx.x] = __ldcg(a.counts + 3 * cur + threadIdx.x);
+        if (blockIdx.x == 0 && threadIdx.x < 3) a.counts[3 * old + threadIdx.x] = 0;
+        __syncthreads();
+        if (s_cnt[0] + s_cnt[1] + s_cnt[2] == 0 || r >= a.max_rounds) break;
+        const Frontier fc = frontier_side(a, cur), fn = frontier_side(a, nx);
+        if (s_cnt[0])
+            color_warp_items(a.rp, a.col, a.hash, fc.list[0], (int64_t)s_cnt[0], a.wait, a.color, fn, a.done);
+        if (s_cnt[1])
+            color_block_items(a.rp, a.col, a.hash, fc.list[1], (int64_t)s_cnt[1], a.wait, a.color, fn, a.done,
+                              sbits);
+        if (s_cnt[2])
+            color_hub_items(a.rp, a.col, a.hash, fc.list[2], (int64_t)s_cnt[2], a.hub_slot, a.bitmaps,
+                            a.chunks_done, a.wait, a.color, fn, a.done, hs, sbits);
+        if (!team_sync(tm, &s_gen, &s_ok)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.rounds = r;
+}
+
 int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStream_t s) {
     if (g.n == 0) return 0;
     const uint32_t sw = seed_word(seed);
-    constexpr int ROUNDS_PER_CHECK = 8;
     DBuf<uint32_t> hash(g.n, s);
     DBuf<int32_t> wait(g.n, s);
-    DBuf<int32_t> lists(6 * g.n, s);          // three tiers, current and next
-    DBuf<unsigned long long> cnt(7, s);       // [tier * 2 + side], [6] coloured
+    DBuf<int32_t> lists(9 * g.n, s);          // three sides of three tiers
+    DBuf<unsigned long long> cnt(10, s);      // [side * 3 + tier], [9] coloured
+    DBuf<GridBarrier> bar(1, s);
+    DBuf<int64_t> rounds(1, s);
     cnt.zero();
-    Frontier F[2];
-    for (int side = 0; side < 2; side++)
-        for (int t = 0; t < 3; t++) {
-            F[side].list[t] = lists.p + (size_t)(2 * t + side) * g.n;
-            F[side].count[t] = cnt.p + 2 * t + side;
-        }
+    bar.zero();
+    rounds.zero();
     // every chunked hub has more than COLOR_BIG_DEG entries
     const int64_t max_hubs = g.nnz / (COLOR_BIG_DEG + 1) + 1;
     DBuf<int32_t> hub_slot(g.n, s);
@@ -296,42 +347,59 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     bitmaps.zero();
     chunks_done.zero();
     nhubs.zero();
-    { k_color_init<<<grid_for(g.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(g.rp, g.col, g.n, sw, hash.p, wait.p, color,
-                                                                          F[0], hub_slot.p, nhubs.p); ::cd::note_launch(); }
-    CD_LAUNCH_CHECK();
-    Pinned h(sizeof(unsigned long long));
-    int cur = 0;
-    int64_t rounds = 0;
-    while (true) {
-        for (int r = 0; r < ROUNDS_PER_CHECK; r++) {
-            const int nx = 1 - cur;
-            for (int t = 0; t < 3; t++) CD_CUDA(cudaMemsetAsync(F[nx].count[t], 0, sizeof(unsigned long long), s));
-            { k_color_round_warp<<<152 * 4, kBlock, 0, s>>>(g.rp, g.col, hash.p, F[cur].list[0], F[cur].count[0],
-                                                          wait.p, color, F[nx], cnt.p + 6); ::cd::note_launch(); }
-            { k_color_round_block<<<152 * 4, kBlock, 0, s>>>(g.rp, g.col, hash.p, F[cur].list[1], F[cur].count[1],
-                                                           wait.p, color, F[nx], cnt.p + 6); ::cd::note_launch(); }
-            { k_color_round_hubs<<<152 * 2, kBlock, 0, s>>>(g.rp, g.col, hash.p, F[cur].list[2], F[cur].count[2],
-                                                          hub_slot.p, bitmaps.p, chunks_done.p, wait.p, color, F[nx],
-                                                          cnt.p + 6); ::cd::note_launch(); }
-            CD_LAUNCH_CHECK();
-            cur = nx;
-            rounds++;
-        }
-        CD_CUDA(cudaMemcpyAsync(h.p, cnt.p + 6, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        CD_CUDA(cudaStreamSynchronize(s));
-        const int64_t coloured = (int64_t)*h.as<unsigned long long>();
-        if (coloured >= g.n) break;
-        // every round colours at least one vertex
-        if (rounds > g.n + 64) raise(CD_ECUDA, "colouring did not finish after %lld rounds", (long long)rounds);
+    ColorArgs a{};
+    a.rp = g.rp;
+    a.col = g.col;
+    a.hash = hash.p;
+    a.n = g.n;
+    a.wait = wait.p;
+    a.color = color;
+    a.lists = lists.p;
+    a.counts = cnt.p;
+    a.done = cnt.p + 9;
+    a.hub_slot = hub_slot.p;
+    a.bitmaps = bitmaps.p;
+    a.chunks_done = chunks_done.p;
+    a.bar = bar.p;
+    a.max_rounds = g.n + 64;   // every round colours at least one vertex
+    a.rounds = rounds.p;
+    Frontier f0;
+    for (int t = 0; t < 3; t++) {
+        f0.list[t] = lists.p + (size_t)t * g.n;
+        f0.count[t] = cnt.p + t;
     }
+    { k_color_init<<<grid_for(g.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(g.rp, g.col, g.n, sw, hash.p, wait.p, color,
+                                                                          f0, hub_slot.p, nhubs.p); ::cd::note_launch(); }
+    CD_LAUNCH_CHECK();
+    // grid: every block resident (the barrier needs it); small graphs take
+    // fewer blocks so that concurrent colourings of a batch fit side by side
+    int dev = 0, sms = 0, per_sm = 0;
+    CD_CUDA(cudaGetDevice(&dev));
+    CD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_color_persistent, kBlock, 0));
+    if (per_sm < 1) raise(CD_ECUDA, "colouring kernel does not fit on an SM");
+    int grid = std::min(sms * per_sm, BARRIER_FAN * BARRIER_SUBS);
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (g.n + 2047) / 2048));
+    Residency res((const void *)k_color_persistent, grid, 0);   // held until the stream is synchronised below
+    void *args[] = {&a};
+    CD_CUDA(cudaLaunchCooperativeKernel((const void *)k_color_persistent, dim3(grid), dim3(kBlock), args, 0, s));
+    note_launch();
     DBuf<unsigned int> maxc(1, s);
     maxc.zero();
     { k_color_max<<<grid_for(g.n, kBlock, 152 * 32), kBlock, 0, s>>>(color, g.n, maxc.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
-    Pinned hm(sizeof(unsigned int));
-    CD_CUDA(cudaMemcpyAsync(hm.p, maxc.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    Pinned h(4 * sizeof(unsigned long long));
+    CD_CUDA(cudaMemcpyAsync(h.p, cnt.p + 9, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaMemcpyAsync(h.as<unsigned long long>() + 1, maxc.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaMemcpyAsync(h.as<unsigned long long>() + 2, &bar.p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CD_CUDA(cudaStreamSynchronize(s));
-    return (int32_t)*hm.as<unsigned int>();
+    const unsigned long long coloured = h.as<unsigned long long>()[0];
+    const unsigned int k = *reinterpret_cast<unsigned int *>(h.as<unsigned long long>() + 1);
+    const int err = *reinterpret_cast<int *>(h.as<unsigned long long>() + 2);
+    if (err) raise(CD_ETIMEOUT, "a grid barrier of the colouring kernel timed out");
+    if ((int64_t)coloured != g.n)
+        raise(CD_ECUDA, "colouring stopped with %llu of %lld vertices coloured", coloured, (long long)g.n);
+    return (int32_t)k;
 }
 
 }  // namespace cd

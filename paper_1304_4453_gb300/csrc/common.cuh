@@ -50,6 +50,26 @@ void dev_free(void *p, cudaStream_t s);
 // Test hook: make the k-th next allocation fail with CD_ENOMEM (k <= 0: off).
 void set_alloc_failure(int k);
 
+// Persistent kernels (cooperative launches with grid barriers) of this
+// library that run at the same time, from any host thread, must fit on the
+// device together, or two partly resident grids could each wait for room the
+// other holds.  A Residency guard reserves the SM share of one launch
+// (blocks / resident blocks per SM) and is held until the kernel has
+// finished (the holder synchronises its stream before releasing); it waits
+// while the reservations of the other holders leave too little room.
+class Residency {
+  public:
+    Residency(const void *kernel, int blocks, size_t dyn_smem);
+    ~Residency();
+    Residency(const Residency &) = delete;
+    Residency &operator=(const Residency &) = delete;
+    int max_blocks() const { return max_blocks_; }   // blocks of this kernel that fit at once
+  private:
+    int dev_ = 0;
+    double share_ = 0;
+    int max_blocks_ = 0;
+};
+
 template <typename T>
 struct DBuf {
     T *p = nullptr;

@@ -966,9 +966,12 @@ void Engine::launch(std::vector<PhaseRun *> &runs) {
                 CD_CUDA(cudaEventCreate(&is->e1));
                 CD_CUDA(cudaEventRecord(is->e0, s_));
             }
-            launch_batch(kern, p.b, p.grid, s_);
-            if (prof) CD_CUDA(cudaEventRecord(is->e1, s_));
-            CD_CUDA(cudaStreamSynchronize(s_));   // host vector `host` goes out of scope
+            {
+                Residency res(kern, p.grid, PHASE_SMEM);
+                launch_batch(kern, p.b, p.grid, s_);
+                if (prof) CD_CUDA(cudaEventRecord(is->e1, s_));
+                CD_CUDA(cudaStreamSynchronize(s_));
+            }
             issued.push_back(std::move(is));
             launches++;
         }

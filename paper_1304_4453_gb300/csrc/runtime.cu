@@ -1,5 +1,6 @@
 // Runtime support: error reporting, the device memory pool, pinned staging.
 #include <atomic>
+#include <condition_variable>
 #include <mutex>
 
 #include "common.cuh"
@@ -70,6 +71,36 @@ void *dev_alloc(size_t bytes, cudaStream_t s) {
 
 void dev_free(void *p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);  // never throws (destructors)
+}
+
+static std::mutex g_res_mu;
+static std::condition_variable g_res_cv;
+static double g_res_used[64] = {};
+
+Residency::Residency(const void *kernel, int blocks, size_t dyn_smem) {
+    int sms = 0, per_sm = 0;
+    CD_CUDA(cudaGetDevice(&dev_));
+    if (dev_ < 0 || dev_ >= 64) raise(CD_ECUDA, "device ordinal %d out of range", dev_);
+    CD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_));
+    CD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, dyn_smem));
+    if (per_sm < 1) raise(CD_ECUDA, "persistent kernel does not fit on an SM");
+    max_blocks_ = sms * per_sm;
+    if (blocks > max_blocks_) raise(CD_ECUDA, "persistent grid of %d blocks exceeds %d resident blocks", blocks,
+                                    max_blocks_);
+    share_ = (double)blocks / per_sm;
+    std::unique_lock<std::mutex> lk(g_res_mu);
+    // a launch that needs the whole device still proceeds when it is alone
+    g_res_cv.wait(lk, [&]() { return g_res_used[dev_] == 0.0 || g_res_used[dev_] + share_ <= sms + 1e-9; });
+    g_res_used[dev_] += share_;
+}
+
+Residency::~Residency() {
+    {
+        std::lock_guard<std::mutex> lk(g_res_mu);
+        g_res_used[dev_] -= share_;
+        if (g_res_used[dev_] < 1e-9) g_res_used[dev_] = 0.0;
+    }
+    g_res_cv.notify_all();
 }
 
 namespace {
