@@ -188,7 +188,7 @@ def run_reference(a):
 def traffic_from_profiles():
     """Per-launch DRAM bytes of the decide kernels from the committed ncu
     summary (a line 'traffic_bytes_per_launch: X'), else None."""
-    path = os.path.join(ROOT, "profiles", "plm_decide_rmat22.md")
+    path = os.path.join(ROOT, "profiles", "move_phase_batch_rmat.md")
     try:
         for line in open(path):
             if line.strip().startswith("traffic_bytes_per_launch:"):
