@@ -24,7 +24,6 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "PLM edges/s (R-MAT scale 22 ef16, complete run incl. all levels)"
 UNIT = "edges/s"
 SCALE = 22
 EDGE_FACTOR = 16
@@ -42,7 +41,7 @@ def args_():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-run", action="store_true",
                    help="timed steps only (no e2e, PLP or CPU baseline): for ncu captures")
-    p.add_argument("--workload", default="plm", choices=["plm", "batch", "serve"],
+    p.add_argument("--workload", default="plm", choices=["plm", "chunglu", "epp", "batch", "serve"],
                    help="plm: R-MAT PLM (default); batch: 512 planted-partition graphs in one batched "
                         "call vs one call per graph; serve: Poisson request stream, continuous-batching "
                         "server vs a one-at-a-time FIFO server")
@@ -59,14 +58,49 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
-def workload_config(g, scale):
+CHUNGLU_N = 16_000_000
+EPP_SCALE, EPP_B = 24, 8
+
+
+def workload_spec(a):
+    """Graph, algorithm and names of a single-graph workload."""
+    rmat_desc = ("R-MAT scale {s}, edge factor 16, abcd=(0.57,0.19,0.19,0.05), seeded vertex permutation, "
+                 "symmetrised, deduplicated, loops dropped, unit weights, seed 1")
+    if a.workload == "chunglu":
+        return {"name": "chunglu16m_plmr", "algo": "plm", "refine": True, "graph": ("chunglu", CHUNGLU_N),
+                "sample": ("chunglu", 1 << 17),
+                "metric": "PLMR edges/s (Chung-Lu 16M, exponent 2.1, degrees 4..1e5, weights 1..100, complete run)",
+                "desc": f"Chung-Lu n={CHUNGLU_N}, degree exponent 2.1, expected degrees in [4, 1e5], integer "
+                        "weights uniform in 1..100, seeded permutation, deduplicated, loops dropped, seed 1",
+                "alg": "PLMR (Algorithms 2-4, refinement after every prolongation), seed 1"}
+    if a.workload == "epp":
+        return {"name": f"rmat{EPP_SCALE}_ef16_epp{EPP_B}", "algo": "epp", "refine": False,
+                "graph": ("rmat", EPP_SCALE), "sample": ("rmat", SAMPLE_SCALE),
+                "metric": f"EPP edges/s (R-MAT scale {EPP_SCALE} ef16, {EPP_B} PLP bases, core clustering, "
+                          "final PLM, complete run)",
+                "desc": rmat_desc.format(s=EPP_SCALE),
+                "alg": f"EPP (Algorithm 5): {EPP_B} PLP bases (seeds 1..{EPP_B}) in one batched launch, exact core "
+                       "communities, coarsening, PLM on the core graph, prolongation"}
+    return {"name": f"rmat{a.scale}_ef16_plm", "algo": "plm", "refine": False, "graph": ("rmat", a.scale),
+            "sample": ("rmat", SAMPLE_SCALE),
+            "metric": f"PLM edges/s (R-MAT scale {a.scale} ef16, complete run incl. all levels)",
+            "desc": rmat_desc.format(s=a.scale), "alg": "PLM (Algorithms 2-3), colour-class schedule, seed 1"}
+
+
+def make_graph(kind, size, device):
+    from paper_1304_4453_gb300 import synth
+    if kind == "chunglu":
+        return synth.chung_lu(size, seed=1, device=device)
+    return synth.rmat(size, EDGE_FACTOR, *ABC, seed=1, device=device)
+
+
+def workload_config(wl, g):
     return {
-        "workload": f"rmat{scale}_ef{EDGE_FACTOR}_plm",
-        "graph": f"R-MAT scale {scale}, edge factor {EDGE_FACTOR}, abcd=(0.57,0.19,0.19,0.05), "
-                 "seeded vertex permutation, symmetrised, deduplicated, loops dropped, unit weights, seed 1",
+        "workload": wl["name"],
+        "graph": wl["desc"],
         "n": g.n if g is not None else None,
         "m": g.m if g is not None else None,
-        "algorithm": "PLM (Algorithms 2-3), colour-class schedule, seed 1",
+        "algorithm": wl["alg"],
         "l2": "inputs larger than L2 (adjacency alone 4*nnz bytes > 129 MB); no flush",
         "parallelism": "replicas",
     }
@@ -117,16 +151,29 @@ class ClockSampler:
 # CPU baseline: the oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
 
-def oracle_sample_rate():
+def oracle_call(wl, rp, c, w):
     from oracle import oracle
-    from paper_1304_4453_gb300 import synth
+    if wl["algo"] == "epp":
+        return oracle.epp(rp, c, w, b=EPP_B, final_refine=wl["refine"], seed=1)
+    return oracle.plm(rp, c, w, refine=wl["refine"], seed=1)
+
+
+def oracle_sample_rate(wl):
+    from oracle import oracle
     oracle.build()
-    g = synth.rmat(SAMPLE_SCALE, EDGE_FACTOR, *ABC, seed=1)
+    g = make_graph(*wl["sample"], "cpu")
     rp, c, w = g.numpy()
     t = time.perf_counter()
-    r = oracle.plm(rp, c, w, seed=1)
+    r = oracle_call(wl, rp, c, w)
     dt = time.perf_counter() - t
     return g.m / dt, dt, g, r
+
+
+def sample_desc(wl, g):
+    kind, size = wl["sample"]
+    what = f"R-MAT scale {size} ef16" if kind == "rmat" else f"Chung-Lu n={size}"
+    return (f"one complete sequential oracle {wl['algo'].upper()}{'R' if wl['refine'] else ''} run on {what} "
+            f"(same generator and parameters; n={g.n}, m={g.m})")
 
 
 def cpu_model():
@@ -143,11 +190,10 @@ def cpu_model():
     return "unknown"
 
 
-def cpu_baseline_obj():
-    rate, dt, g, r = oracle_sample_rate()
+def cpu_baseline_obj(wl):
+    rate, dt, g, r = oracle_sample_rate(wl)
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one complete sequential oracle PLM run on R-MAT scale {SAMPLE_SCALE} ef{EDGE_FACTOR} "
-                      f"(same generator and parameters; n={g.n}, m={g.m}; {dt:.1f} s, modularity {r.modularity:.4f})",
+            "sample": sample_desc(wl, g) + f"; {dt:.1f} s, modularity {r.modularity:.4f}",
             "cpu": cpu_model(), "nproc": os.cpu_count()}
 
 
@@ -159,22 +205,22 @@ def run_reference(a):
     rank, local, world = dist_env()
     if rank != 0:
         return
+    wl = workload_spec(a)
     times = []
     rate = None
     for i in range(a.warmup + a.steps):
-        rate, dt, g, r = oracle_sample_rate()
+        rate, dt, g, r = oracle_sample_rate(wl)
         if i >= a.warmup:
             times.append(dt)
     tot = sum(times)
     value = g.m * len(times) / tot
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "impl": "reference", "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": workload_config(None, a.scale),
+        "data": "synthetic", "config": workload_config(wl, None),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step: one complete sequential oracle PLM run on R-MAT scale "
-                                   f"{SAMPLE_SCALE} ef{EDGE_FACTOR} (n={g.n}, m={g.m})",
+                         "sample": "each step: " + sample_desc(wl, g),
                          "cpu": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -218,15 +264,22 @@ def run_ours(a):
     build.build()
     cd.lib()
 
-    g = synth.rmat(a.scale, EDGE_FACTOR, *ABC, seed=1, device=dev)
+    wl = workload_spec(a)
+    g = make_graph(*wl["graph"], dev)
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()   # the generator's scratch goes back before the library allocates
     G = cd.Graph(g.row_ptr, g.col, g.w)
     labels = torch.empty(g.n, dtype=torch.int32, device=dev)
     opts_plain = cd.default_opts(seed=1)
     opts_prof = cd.default_opts(seed=1, profile=True)
 
+    def run(h, out, opts):
+        if wl["algo"] == "epp":
+            return cd.cd_epp(h, out, EPP_B, wl["refine"], opts)
+        return cd.cd_plm(h, out, wl["refine"], opts)
+
     for _ in range(a.warmup):
-        mod, st, status = cd.cd_plm(G.h, labels, False, opts_plain)
+        mod, st, status = run(G.h, labels, opts_plain)
     torch.cuda.synchronize()
 
     def barrier():
@@ -245,7 +298,7 @@ def run_ours(a):
     k_launches = 0
     stats = []
     for _ in range(a.steps):
-        mod, st, status = cd.cd_plm(G.h, labels, False, opts_prof)
+        mod, st, status = run(G.h, labels, opts_prof)
         k_ms += st["k_ms"]
         k_bytes += st["k_bytes"]
         k_launches += st["k_launches"]
@@ -275,13 +328,14 @@ def run_ours(a):
     # graph creation, PLM, D2H of the labels, every step
     rp_h = g.row_ptr.cpu().pin_memory()
     col_h = g.col.cpu().pin_memory()
+    w_h = None if g.w is None else g.w.cpu().pin_memory()
     lab_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
     e2e_t = []
     for i in range(max(1, min(a.steps, 3)) + 1):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        h = cd.cd_graph_create(rp_h, col_h, None)
-        cd.cd_plm(h, lab_h, False, opts_plain)
+        h = cd.cd_graph_create(rp_h, col_h, w_h)
+        run(h, lab_h, opts_plain)
         cd.cd_graph_destroy(h)
         torch.cuda.synchronize()
         if i > 0:
@@ -295,12 +349,15 @@ def run_ours(a):
     plp_mod, plp_st, _ = cd.cd_plp(G.h, torch.empty_like(labels), cd.default_opts(seed=1))
     torch.cuda.synchronize()
     plp_s = time.perf_counter() - t
+    kernel_name = ("k_plp_batch + k_move_phase_batch (persistent PLP runs and PLM move phases)"
+                   if wl["algo"] == "epp" else
+                   "k_move_phase_batch (persistent PLM move phase: every sweep and colour class)")
 
     peak, peak_kind = measured_hbm_peak()
     achieved = (k_bytes / 1e9) / (k_ms / 1e3) if k_ms > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak if achieved else None, "traffic": traffic_from_profiles(),
-            "kernel": "k_move_phase_batch (persistent PLM move phase: every sweep and colour class)",
+            "frac": achieved / peak if achieved else None, "traffic": traffic_from_profiles() if wl["name"] == "rmat22_ef16_plm" else None,
+            "kernel": kernel_name,
             "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
             "launches_timed": k_launches, "avg_launch_us": 1000.0 * k_ms / max(k_launches, 1),
@@ -311,13 +368,13 @@ def run_ours(a):
         return
     cpu = None
     if not a.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline_obj()
+        cpu = cpu_baseline_obj(wl)
     st = stats[-1]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": workload_config(g, a.scale),
+        "config": workload_config(wl, g),
         "modularity": mod,
         "plm": {"levels": st["levels"], "colors0": st["colors0"], "sweeps": st["sweeps"],
                 "communities": st["ncomm"], "ms_color": st["ms_color"], "ms_move": st["ms_move"],
@@ -326,7 +383,8 @@ def run_ours(a):
                                          "recheck": st["stage_recheck_ms"]}},
         "plp": {"edges_per_s": g.m / plp_s, "modularity": plp_mod, "iters": plp_st["iters"],
                 "communities": plp_st["ncomm"]},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz + (0 if g.w is None else 4 * g.nnz),
                 "d2h_bytes_per_step": 4 * g.n, "labels_match_device_run": e2e_ok},
         "gpu_launches": launches,
         "roofline": roof,
@@ -647,7 +705,7 @@ def run_reference_other(a):
 def main():
     a = args_()
     if a.impl == "reference":
-        if a.workload == "plm":
+        if a.workload in ("plm", "chunglu", "epp"):
             run_reference(a)
         else:
             run_reference_other(a)

@@ -42,6 +42,10 @@ struct Schedule {
     std::vector<int32_t> nb1, nb2;     // per class H1 / H2 block totals
     DBuf<HubInfo> hubs;
     DBuf<int32_t> hb1, hb2;            // per hub, block prefix inside its class
+    DBuf<int32_t> item_hub, slice_hub; // class-relative hub of each aggregation item / decide slice
+    DBuf<int32_t> d_it0, d_sl0;        // per class, first item / slice in those arrays
+    DBuf<int32_t> hub_occ;             // occupied-slot lists (laid out like hub_keys)
+    DBuf<unsigned int> hub_nocc;
     int64_t nhubs = 0, max_tab = 0, max_nb2 = 0;
     DBuf<int32_t> hub_keys;
     DBuf<unsigned long long> hub_vals, hub_wc;
@@ -134,6 +138,10 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     S.nhubs = H;
     S.max_tab = S.max_nb2 = 0;
     if (H == 0) {
+        S.d_it0.alloc(S.ncol + 1, s);
+        S.d_sl0.alloc(S.ncol + 1, s);
+        S.d_it0.zero();
+        S.d_sl0.zero();
         upload_class_meta(S, s);
         return;
     }
@@ -159,16 +167,22 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     }
     std::vector<HubInfo> info(H);
     std::vector<int32_t> b1(H), b2(H);
+    std::vector<int32_t> it0(S.ncol + 1, 0), sl0(S.ncol + 1, 0), ihub, shub;
     for (int32_t k = 0; k < S.ncol; k++) {
         int64_t tab = 0;
         int32_t c1 = 0, c2 = 0;
+        it0[k] = (int32_t)ihub.size();
+        sl0[k] = (int32_t)shub.size();
         for (int32_t h = S.hub_start[k]; h < S.hub_start[k + 1]; h++) {
             int64_t slots = BLK_SLOTS;
             while (slots < 2 * hd[h]) slots <<= 1;
             HubInfo &x = info[h];
             x.v = hv[h];
             x.nb1 = (int32_t)((hd[h] + HUB_CHUNK - 1) / HUB_CHUNK);
-            x.nb2 = (int32_t)((slots + HUB_SCAN - 1) / HUB_SCAN);
+            // hubs up to HUB_LAST are decided by their last aggregation item
+            x.nb2 = hd[h] <= HUB_LAST ? 0 : (int32_t)((slots + HUB_SCAN - 1) / HUB_SCAN);
+            for (int32_t j = 0; j < x.nb1; j++) ihub.push_back(h - S.hub_start[k]);
+            for (int32_t j = 0; j < x.nb2; j++) shub.push_back(h - S.hub_start[k]);
             x.pad = 0;
             x.tab = tab;
             x.slots = slots;
@@ -183,9 +197,21 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
         S.max_tab = std::max(S.max_tab, tab);
         S.max_nb2 = std::max<int64_t>(S.max_nb2, c2);
     }
+    it0[S.ncol] = (int32_t)ihub.size();
+    sl0[S.ncol] = (int32_t)shub.size();
     S.hubs.alloc(H, s);
     S.hb1.alloc(H, s);
     S.hb2.alloc(H, s);
+    S.item_hub.alloc(ihub.size(), s);
+    S.slice_hub.alloc(shub.size(), s);
+    S.d_it0.alloc(S.ncol + 1, s);
+    S.d_sl0.alloc(S.ncol + 1, s);
+    if (!ihub.empty())
+        CD_CUDA(cudaMemcpyAsync(S.item_hub.p, ihub.data(), ihub.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (!shub.empty())
+        CD_CUDA(cudaMemcpyAsync(S.slice_hub.p, shub.data(), shub.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CD_CUDA(cudaMemcpyAsync(S.d_it0.p, it0.data(), it0.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CD_CUDA(cudaMemcpyAsync(S.d_sl0.p, sl0.data(), sl0.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     CD_CUDA(cudaMemcpyAsync(S.hubs.p, info.data(), H * sizeof(HubInfo), cudaMemcpyHostToDevice, s));
     CD_CUDA(cudaMemcpyAsync(S.hb1.p, b1.data(), H * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     CD_CUDA(cudaMemcpyAsync(S.hb2.p, b2.data(), H * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -194,6 +220,9 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     S.hub_vals.alloc(S.max_tab, s);
     S.hub_vals.zero();
     S.hub_wc.alloc(H, s);
+    S.hub_occ.alloc(S.max_tab, s);
+    S.hub_nocc.alloc(H, s);
+    S.hub_nocc.zero();
     S.done1.alloc(H, s);
     S.done1.zero();
     S.done2.alloc(H, s);
@@ -251,6 +280,12 @@ static PhaseArgs phase_args(const GraphView &g, const Schedule &S, int32_t *zeta
     a.hubs = S.hubs.p;
     a.hb1 = S.hb1.p;
     a.hb2 = S.hb2.p;
+    a.item_hub = S.item_hub.p;
+    a.slice_hub = S.slice_hub.p;
+    a.class_it0 = S.d_it0.p;
+    a.class_sl0 = S.d_sl0.p;
+    a.hub_occ = S.hub_occ.p;
+    a.hub_nocc = S.hub_nocc.p;
     a.hub_keys = S.hub_keys.p;
     a.hub_vals = S.hub_vals.p;
     a.hub_wc = S.hub_wc.p;

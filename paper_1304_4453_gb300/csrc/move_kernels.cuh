@@ -23,8 +23,12 @@
 //              deg <= 1024;
 //   role 4     hub aggregation: a chunk of a hub's adjacency is merged in a
 //              shared table, then into the hub's global open-addressing
-//              table; hub-decide items then scan the tables in slices and
-//              the last slice of each hub takes the decision.
+//              table, and every slot it fills is appended to the hub's
+//              occupied-slot list.  For hubs of degree <= HUB_LAST the block
+//              that merges the last chunk decides from that list at once;
+//              larger hubs are decided after a team barrier by hub-decide
+//              items that scan their tables in slices, the last slice of each
+//              hub taking the decision.
 #pragma once
 #include <type_traits>
 
@@ -38,6 +42,7 @@ constexpr int BLK_SLOTS = 2048;     // block role table (deg <= 1024)
 constexpr int HUB_CHUNK = 256;      // adjacency entries per hub-aggregation item
 constexpr int HUB_CHUNK_SLOTS = 512;  // shared table of one hub-aggregation item
 constexpr int HUB_SCAN = 1024;      // hub table slots per hub-decide item
+constexpr int HUB_LAST = 2048;      // hubs up to this degree: decided by their last aggregation item
 constexpr int SMEM_BYTES = 24576;   // shared table union of every role
 
 __host__ __device__ inline int degree_bin(int64_t d) {
@@ -51,7 +56,7 @@ struct Counters {              // per sweep / iteration, device
 
 struct HubInfo {               // one hub vertex of a class
     int32_t v;
-    int32_t nb1, nb2;          // aggregation / decide block counts
+    int32_t nb1, nb2;          // aggregation / decide block counts (nb2 = 0: decided by the last aggregation item)
     int32_t pad;
     int64_t tab;               // first slot of its global table
     int64_t slots;             // table size (power of two)
@@ -82,7 +87,10 @@ struct SweepCtx {
     // hubs of this class
     const HubInfo *hubs;
     const int32_t *hub_b1, *hub_b2;      // exclusive prefix of hub blocks
+    const int32_t *item_hub, *slice_hub; // hub of each aggregation item / decide slice
     int32_t nhubs;
+    int32_t *hub_occ;          // occupied-slot lists (at each hub's table offset)
+    unsigned int *hub_nocc;    // their lengths (0 between uses)
     int32_t *hub_keys;         // global tables (all -1 between uses)
     void *hub_vals;            //   values (all 0 between uses)
     void *hub_wc;              // omega(u, C) per hub
@@ -115,6 +123,25 @@ __device__ __forceinline__ void tab_insert(int32_t *keys, VT *vals, uint32_t mas
         s = (s + 1) & mask;
     }
     atomicAdd(overflow, 1ull);
+}
+
+// tab_insert that returns the slot when this call created the key, else -1.
+template <typename VT>
+__device__ __forceinline__ int32_t tab_insert_new(int32_t *keys, VT *vals, uint32_t mask, int32_t key, VT w,
+                                                  unsigned long long *overflow) {
+    uint32_t s = hmix(key) & mask;
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+        int32_t k = ((volatile int32_t *)keys)[s];
+        if (k == key) { atomicAdd(&vals[s], w); return -1; }
+        if (k == -1) {
+            int32_t prev = atomicCAS(&keys[s], -1, key);
+            if (prev == -1) { atomicAdd(&vals[s], w); return (int32_t)s; }
+            if (prev == key) { atomicAdd(&vals[s], w); return -1; }
+        }
+        s = (s + 1) & mask;
+    }
+    atomicAdd(overflow, 1ull);
+    return -1;
 }
 
 template <typename VT>
@@ -449,25 +476,103 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
 // ---------------------------------------------------------------------------
 // Hub roles (deg > 1024).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_hub(const int32_t *prefix, int nhubs, int32_t b) {
-    int lo = 0, hi = nhubs - 1;
-    while (lo < hi) {            // last h with prefix[h] <= b
-        int mid = (lo + hi + 1) >> 1;
-        if (prefix[mid] <= b) lo = mid; else hi = mid - 1;
+
+// Takes the decision of hub u from its best candidate (one block; r, C and
+// wC are the same in every thread).
+template <bool BIG, bool PLP>
+__device__ __forceinline__ void hub_finish(const SweepCtx &c, int32_t u, int32_t C, int64_t wC,
+                                           const typename BestOf<PLP, BIG>::T &r, int *s_last) {
+    if (threadIdx.x == 0) {
+        if constexpr (!PLP) {
+            const bool want = r.id >= 0 && r.g > 0;
+            if (want) take_move(c, atomicAdd(c.late ? c.ncand : c.nmv, 1ull), u, C, r.id, r.w, wC);
+            atomicAdd(&c.cnt->wanted, (unsigned long long)want);
+            atomicAdd(&c.cnt->moved, (unsigned long long)(want && !c.late));
+            *s_last = 1;
+        } else {
+            const bool adopt = r.id >= 0 && r.w > wC;
+            if (adopt) c.zeta[u] = r.id;
+            else c.active[u] = 0;
+            atomicAdd(&c.cnt->moved, (unsigned long long)adopt);
+            *s_last = adopt ? 2 : 1;
+        }
+        atomicAdd(&c.cnt->decisions, 1ull);
     }
-    return lo;
+    __syncthreads();
+    if constexpr (PLP) {
+        if (*s_last == 2) {
+            const int64_t rb = c.g.rp[u], re = c.g.rp[u + 1];
+            for (int64_t e = rb + threadIdx.x; e < re; e += kBlock) c.active[c.g.col[e]] = 1;
+        }
+    }
+    __syncthreads();
+}
+
+// Decision of hub h (degree <= HUB_LAST) by the block that merged its last
+// chunk: every other chunk has published its slots (fence, then the chunk
+// counter), so the occupied-slot list is complete.  Scans the list, clears
+// the slots it used, and decides.
+template <int WK, bool BIG, bool PLP>
+__device__ __forceinline__ void hub_decide_occ(const SweepCtx &c, int h, const HubInfo &hi,
+                                               typename BestOf<PLP, BIG>::T *s_best, int *s_last) {
+    using VT = ValT<BIG>;
+    using BT = typename BestOf<PLP, BIG>::T;
+    __threadfence();
+    int32_t *gk = c.hub_keys + hi.tab;
+    VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
+    const int32_t *occ = c.hub_occ + hi.tab;
+    const uint32_t gmask = (uint32_t)(hi.slots - 1);
+    const int32_t u = hi.v;
+    const int32_t C = c.zeta[u];
+    const int64_t nocc = (int64_t)__ldcg(c.hub_nocc + h);
+    const int64_t wC = (int64_t)tab_lookup_cg<VT>(gk, gv, gmask, C);
+    BT b;
+    b.init();
+    if constexpr (!PLP) {
+        const int64_t vu = c.g.vol[u], volC = c.volc[C], twoW = 2 * c.g.W;
+        for (int64_t i = threadIdx.x; i < nocc; i += kBlock) {
+            const int32_t sl = __ldcg(occ + i);
+            const int32_t key = __ldcg(gk + sl);
+            const int64_t val = (int64_t)__ldcg(gv + sl);
+            if (key != C) b.offer(plm_gain<BIG>(twoW, val, wC, vu, c.volc[key], volC), key, val);
+        }
+    } else {
+        for (int64_t i = threadIdx.x; i < nocc; i += kBlock) {
+            const int32_t sl = __ldcg(occ + i);
+            const int32_t key = __ldcg(gk + sl);
+            b.offer((int64_t)__ldcg(gv + sl), fmix32((uint32_t)key ^ c.tie_salt), key);
+        }
+    }
+    __syncthreads();   // every lookup of C is done before slots are cleared
+    for (int64_t i = threadIdx.x; i < nocc; i += kBlock) {
+        const int32_t sl = __ldcg(occ + i);
+        gk[sl] = -1;
+        gv[sl] = 0;
+    }
+    b = block_best(b, s_best);
+    if (threadIdx.x == 0) {
+        c.hub_done1[h] = 0;
+        c.hub_nocc[h] = 0;
+        atomicAdd(&c.cnt->candidates, (unsigned long long)nocc);
+    }
+    hub_finish<BIG, PLP>(c, u, C, wC, b, s_last);
 }
 
 template <int WK, bool BIG, bool PLP>
-__device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb, unsigned char *smem, int *s_last) {
+__device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb, unsigned char *smem,
+                                                   typename BestOf<PLP, BIG>::T *s_best, int *s_last) {
     using VT = ValT<BIG>;
+    constexpr int PER = HUB_CHUNK_SLOTS / kBlock;
+    static_assert(HUB_CHUNK_SLOTS % kBlock == 0, "chunk table slots per thread");
     int32_t *keys = reinterpret_cast<int32_t *>(smem);
     VT *vals = reinterpret_cast<VT *>(smem + HUB_CHUNK_SLOTS * 4);
-    const int h = find_hub(c.hub_b1, c.nhubs, rb);
+    int32_t *wsum = reinterpret_cast<int32_t *>(smem + HUB_CHUNK_SLOTS * 12);   // [kBlock / 32 + 2]
+    static_assert(HUB_CHUNK_SLOTS * 12 + (kBlock / 32 + 2) * 4 <= SMEM_BYTES, "hub chunk scratch");
+    const int h = c.item_hub[rb];
     const HubInfo hi = c.hubs[h];
     const int32_t u = hi.v;
     if constexpr (PLP) {
-        if (!c.active[u]) return;   // whole block; k_hub_decide sees it too
+        if (!c.active[u]) return;   // whole block; the decision skips it too
     }
     const int j = rb - c.hub_b1[h];
     const int64_t rbeg = c.g.rp[u], rend = c.g.rp[u + 1];
@@ -482,8 +587,42 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
     int32_t *gk = c.hub_keys + hi.tab;
     VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
     const uint32_t gmask = (uint32_t)(hi.slots - 1);
-    for (int s = threadIdx.x; s < HUB_CHUNK_SLOTS; s += kBlock)
-        if (keys[s] >= 0) tab_insert<VT>(gk, gv, gmask, keys[s], vals[s], &c.cnt->overflow);
+    if (hi.nb2 != 0) {
+        // decided later by slices that scan the whole table
+        for (int s = threadIdx.x; s < HUB_CHUNK_SLOTS; s += kBlock)
+            if (keys[s] >= 0) tab_insert<VT>(gk, gv, gmask, keys[s], vals[s], &c.cnt->overflow);
+    } else {
+        // merge into the hub table; slots created here go to the occupied list
+        int32_t fresh[PER];
+        int nf = 0;
+#pragma unroll
+        for (int i = 0; i < PER; i++) {
+            const int s = threadIdx.x + i * kBlock;
+            fresh[i] = -1;
+            if (keys[s] >= 0) fresh[i] = tab_insert_new<VT>(gk, gv, gmask, keys[s], vals[s], &c.cnt->overflow);
+            nf += fresh[i] >= 0;
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int incl = nf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int w = 0; w < kBlock / 32; w++) { const int t = wsum[w]; wsum[w] = run; run += t; }
+            wsum[kBlock / 32] = run ? (int)atomicAdd(c.hub_nocc + h, (unsigned)run) : 0;
+        }
+        __syncthreads();
+        int pos = wsum[kBlock / 32] + wsum[warp] + incl - nf;
+        int32_t *occ = c.hub_occ + hi.tab;
+#pragma unroll
+        for (int i = 0; i < PER; i++)
+            if (fresh[i] >= 0) occ[pos++] = fresh[i];
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -492,7 +631,10 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
         atomicAdd(&c.cnt->entries, (unsigned long long)(end - beg));
     }
     __syncthreads();
-    if (*s_last && threadIdx.x == 0) {
+    if (!*s_last) return;
+    if (hi.nb2 == 0) {
+        hub_decide_occ<WK, BIG, PLP>(c, h, hi, s_best, s_last);
+    } else if (threadIdx.x == 0) {
         __threadfence();
         c.hub_done1[h] = 0;
         static_cast<VT *>(c.hub_wc)[h] = tab_lookup_cg<VT>(gk, gv, gmask, c.zeta[u]);

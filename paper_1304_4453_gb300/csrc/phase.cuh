@@ -28,6 +28,10 @@ struct PhaseArgs {
     const int32_t *class_nb1, *class_nb2;  // [ncol]
     const HubInfo *hubs;
     const int32_t *hb1, *hb2;
+    const int32_t *item_hub, *slice_hub;   // class-relative hub of each aggregation item / decide slice
+    const int32_t *class_it0, *class_sl0;  // [ncol] first item / slice of each class in those arrays
+    int32_t *hub_occ;                      // occupied-slot lists, laid out like the hub tables
+    unsigned int *hub_nocc;                // per hub
     int32_t *hub_keys;
     void *hub_vals, *hub_wc;
     unsigned int *done1, *done2;
@@ -65,6 +69,10 @@ __device__ __forceinline__ int32_t class_ctx(const PhaseArgs &a, int32_t k, Swee
     c.hubs = a.hubs + h0;
     c.hub_b1 = a.hb1 + h0;
     c.hub_b2 = a.hb2 + h0;
+    c.item_hub = a.item_hub + a.class_it0[k];
+    c.slice_hub = a.slice_hub + a.class_sl0[k];
+    c.hub_occ = a.hub_occ;
+    c.hub_nocc = a.hub_nocc + h0;
     c.hub_keys = a.hub_keys;
     c.hub_vals = a.hub_vals;
     c.hub_wc = static_cast<char *>(a.hub_wc) + (size_t)h0 * 8;
@@ -92,7 +100,7 @@ __device__ __forceinline__ void run_item(const SweepCtx &c, int32_t b, unsigned 
     else if (b < c.bend[1]) role_group<8, 16, WK, BIG, PLP>(c, b - c.bend[0], c.order + c.off[1], c.off[2] - c.off[1], smem);
     else if (b < c.bend[2]) role_group<32, 128, WK, BIG, PLP>(c, b - c.bend[1], c.order + c.off[2], c.off[3] - c.off[2], smem);
     else if (b < c.bend[3]) role_block<WK, BIG, PLP>(c, b - c.bend[2], c.order + c.off[3], smem, s_best, s_cand);
-    else role_hub_aggregate<WK, BIG, PLP>(c, b - c.bend[3], smem, s_last);
+    else role_hub_aggregate<WK, BIG, PLP>(c, b - c.bend[3], smem, s_best, s_last);
 }
 
 // Hub decide: slice `item` of a hub table; the last slice of a hub decides.
@@ -101,7 +109,7 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
                                                 unsigned *s_cand, int *s_last) {
     using VT = ValT<BIG>;
     using BT = typename BestOf<PLP, BIG>::T;
-    const int h = find_hub(c.hub_b2, c.nhubs, item);
+    const int h = c.slice_hub[item];
     const HubInfo hi = c.hubs[h];
     const int32_t u = hi.v;
     if constexpr (PLP) {
@@ -189,32 +197,8 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
         }
         b = block_best(r, s_best);
     }
-    if (threadIdx.x == 0) {
-        c.hub_done2[h] = 0;
-        const BT r = b;
-        if constexpr (!PLP) {
-            const bool want = r.id >= 0 && r.g > 0;
-            if (want) take_move(c, atomicAdd(c.late ? c.ncand : c.nmv, 1ull), u, C, r.id, r.w, wC);
-            atomicAdd(&c.cnt->wanted, (unsigned long long)want);
-            atomicAdd(&c.cnt->moved, (unsigned long long)(want && !c.late));
-            *s_last = 1;
-        } else {
-            const bool adopt = r.id >= 0 && r.w > wC;
-            if (adopt) c.zeta[u] = r.id;
-            else c.active[u] = 0;
-            atomicAdd(&c.cnt->moved, (unsigned long long)adopt);
-            *s_last = adopt ? 2 : 1;
-        }
-        atomicAdd(&c.cnt->decisions, 1ull);
-    }
-    __syncthreads();
-    if constexpr (PLP) {
-        if (*s_last == 2) {
-            const int64_t rb = c.g.rp[u], re = c.g.rp[u + 1];
-            for (int64_t e = rb + threadIdx.x; e < re; e += kBlock) c.active[c.g.col[e]] = 1;
-        }
-    }
-    __syncthreads();
+    if (threadIdx.x == 0) c.hub_done2[h] = 0;
+    hub_finish<BIG, PLP>(c, u, C, wC, b, s_last);
 }
 
 // ---------------------------------------------------------------------------
