@@ -42,8 +42,9 @@ struct Schedule {
     std::vector<int32_t> nb1, nb2;     // per class H1 / H2 block totals
     DBuf<HubInfo> hubs;
     DBuf<int32_t> hb1, hb2;            // per hub, block prefix inside its class
-    DBuf<int32_t> item_hub, slice_hub; // class-relative hub of each aggregation item / decide slice
-    DBuf<int32_t> d_it0, d_sl0;        // per class, first item / slice in those arrays
+    DBuf<ChunkDesc> chunks;            // aggregation items, class by class
+    DBuf<SliceDesc> slices;            // decide slices, class by class
+    DBuf<ClassMeta> meta;              // per class
     DBuf<int32_t> hub_occ;             // occupied-slot lists (laid out like hub_keys)
     DBuf<unsigned int> hub_nocc;
     int64_t nhubs = 0, max_tab = 0, max_nb2 = 0;
@@ -78,9 +79,11 @@ __global__ void k_bucket_bounds(const uint32_t *key, int64_t n, int64_t nbk, int
     }
 }
 
-__global__ void k_degrees(const int64_t *rp, const int32_t *v, int64_t cnt, int64_t *deg) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+__global__ void k_rows(const int64_t *rp, const int32_t *v, int64_t cnt, int64_t *beg, int64_t *deg) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        beg[i] = rp[v[i]];
         deg[i] = rp[v[i] + 1] - rp[v[i]];
+    }
 }
 
 static int bits_for(int64_t x) {
@@ -89,7 +92,23 @@ static int bits_for(int64_t x) {
     return b;
 }
 
-static void upload_class_meta(Schedule &S, cudaStream_t s) {
+static void upload_class_meta(Schedule &S, const std::vector<int32_t> &it0, const std::vector<int32_t> &sl0,
+                              cudaStream_t s) {
+    std::vector<ClassMeta> meta(S.ncol);
+    for (int32_t k = 0; k < S.ncol; k++) {
+        ClassMeta &m = meta[k];
+        m = ClassMeta{};
+        for (int b = 0; b <= NBINS; b++) m.off[b] = S.off[(int64_t)k * NBINS + b];
+        m.h0 = S.hub_start[k];
+        m.nhubs = S.hub_start[k + 1] - S.hub_start[k];
+        m.nb1 = S.nb1[k];
+        m.nb2 = S.nb2[k];
+        m.it0 = it0[k];
+        m.sl0 = sl0[k];
+    }
+    S.meta.alloc(S.ncol, s);
+    if (S.ncol)
+        CD_CUDA(cudaMemcpyAsync(S.meta.p, meta.data(), S.ncol * sizeof(ClassMeta), cudaMemcpyHostToDevice, s));
     S.d_off.alloc(S.off.size(), s);
     S.d_hub0.alloc(S.hub_start.size(), s);
     S.d_nb1.alloc(S.ncol + 1, s);
@@ -138,17 +157,13 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     S.nhubs = H;
     S.max_tab = S.max_nb2 = 0;
     if (H == 0) {
-        S.d_it0.alloc(S.ncol + 1, s);
-        S.d_sl0.alloc(S.ncol + 1, s);
-        S.d_it0.zero();
-        S.d_sl0.zero();
-        upload_class_meta(S, s);
+        upload_class_meta(S, std::vector<int32_t>(S.ncol + 1, 0), std::vector<int32_t>(S.ncol + 1, 0), s);
         return;
     }
     std::vector<int32_t> hv(H);
-    std::vector<int64_t> hd(H);
+    std::vector<int64_t> hd(H), hb(H);
     {
-        Pinned pv(H * sizeof(int32_t)), pd(H * sizeof(int64_t));
+        Pinned pv(H * sizeof(int32_t)), pd(2 * H * sizeof(int64_t));
         for (int32_t k = 0; k < S.ncol; k++) {
             const int64_t a = S.off[(int64_t)k * NBINS + 4], e = S.off[(int64_t)k * NBINS + 5];
             if (e > a)
@@ -157,22 +172,28 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
         }
         CD_CUDA(cudaStreamSynchronize(s));
         DBuf<int32_t> dv(H, s);
-        DBuf<int64_t> dd(H, s);
+        DBuf<int64_t> dd(2 * H, s);
         CD_CUDA(cudaMemcpyAsync(dv.p, pv.p, H * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        { k_degrees<<<grid_for(H, kBlock), kBlock, 0, s>>>(g.rp, dv.p, H, dd.p); ::cd::note_launch(); }
+        { k_rows<<<grid_for(H, kBlock), kBlock, 0, s>>>(g.rp, dv.p, H, dd.p, dd.p + H); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
-        CD_CUDA(cudaMemcpyAsync(pd.p, dd.p, H * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CD_CUDA(cudaMemcpyAsync(pd.p, dd.p, 2 * H * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CD_CUDA(cudaStreamSynchronize(s));
-        for (int64_t i = 0; i < H; i++) { hv[i] = pv.as<int32_t>()[i]; hd[i] = pd.as<int64_t>()[i]; }
+        for (int64_t i = 0; i < H; i++) {
+            hv[i] = pv.as<int32_t>()[i];
+            hb[i] = pd.as<int64_t>()[i];
+            hd[i] = pd.as<int64_t>()[H + i];
+        }
     }
     std::vector<HubInfo> info(H);
     std::vector<int32_t> b1(H), b2(H);
-    std::vector<int32_t> it0(S.ncol + 1, 0), sl0(S.ncol + 1, 0), ihub, shub;
+    std::vector<int32_t> it0(S.ncol + 1, 0), sl0(S.ncol + 1, 0);
+    std::vector<ChunkDesc> chunks;
+    std::vector<SliceDesc> slices;
     for (int32_t k = 0; k < S.ncol; k++) {
         int64_t tab = 0;
         int32_t c1 = 0, c2 = 0;
-        it0[k] = (int32_t)ihub.size();
-        sl0[k] = (int32_t)shub.size();
+        it0[k] = (int32_t)chunks.size();
+        sl0[k] = (int32_t)slices.size();
         for (int32_t h = S.hub_start[k]; h < S.hub_start[k + 1]; h++) {
             int64_t slots = BLK_SLOTS;
             while (slots < 2 * hd[h]) slots <<= 1;
@@ -181,11 +202,34 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
             x.nb1 = (int32_t)((hd[h] + HUB_CHUNK - 1) / HUB_CHUNK);
             // hubs up to HUB_LAST are decided by their last aggregation item
             x.nb2 = hd[h] <= HUB_LAST ? 0 : (int32_t)((slots + HUB_SCAN - 1) / HUB_SCAN);
-            for (int32_t j = 0; j < x.nb1; j++) ihub.push_back(h - S.hub_start[k]);
-            for (int32_t j = 0; j < x.nb2; j++) shub.push_back(h - S.hub_start[k]);
             x.pad = 0;
             x.tab = tab;
             x.slots = slots;
+            const int32_t hr = h - S.hub_start[k];
+            for (int32_t j = 0; j < x.nb1; j++) {
+                ChunkDesc d{};
+                d.beg = hb[h] + (int64_t)j * HUB_CHUNK;
+                d.end = std::min(hb[h] + hd[h], d.beg + HUB_CHUNK);
+                d.tab = tab;
+                d.slots = slots;
+                d.u = hv[h];
+                d.h = hr;
+                d.nb1 = x.nb1;
+                d.nb2 = x.nb2;
+                chunks.push_back(d);
+            }
+            for (int32_t j = 0; j < x.nb2; j++) {
+                SliceDesc d{};
+                d.tab = tab;
+                d.s0 = (int64_t)j * HUB_SCAN;
+                d.s1 = std::min(slots, d.s0 + HUB_SCAN);
+                d.u = hv[h];
+                d.h = hr;
+                d.nb1 = x.nb1;
+                d.nb2 = x.nb2;
+                d.p0 = c2;
+                slices.push_back(d);
+            }
             b1[h] = c1;
             b2[h] = c2;
             c1 += x.nb1;
@@ -197,21 +241,18 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
         S.max_tab = std::max(S.max_tab, tab);
         S.max_nb2 = std::max<int64_t>(S.max_nb2, c2);
     }
-    it0[S.ncol] = (int32_t)ihub.size();
-    sl0[S.ncol] = (int32_t)shub.size();
+    it0[S.ncol] = (int32_t)chunks.size();
+    sl0[S.ncol] = (int32_t)slices.size();
+    S.chunks.alloc(chunks.size(), s);
+    S.slices.alloc(slices.size(), s);
+    if (!chunks.empty())
+        CD_CUDA(cudaMemcpyAsync(S.chunks.p, chunks.data(), chunks.size() * sizeof(ChunkDesc), cudaMemcpyHostToDevice, s));
+    if (!slices.empty())
+        CD_CUDA(cudaMemcpyAsync(S.slices.p, slices.data(), slices.size() * sizeof(SliceDesc), cudaMemcpyHostToDevice,
+                                s));
     S.hubs.alloc(H, s);
     S.hb1.alloc(H, s);
     S.hb2.alloc(H, s);
-    S.item_hub.alloc(ihub.size(), s);
-    S.slice_hub.alloc(shub.size(), s);
-    S.d_it0.alloc(S.ncol + 1, s);
-    S.d_sl0.alloc(S.ncol + 1, s);
-    if (!ihub.empty())
-        CD_CUDA(cudaMemcpyAsync(S.item_hub.p, ihub.data(), ihub.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    if (!shub.empty())
-        CD_CUDA(cudaMemcpyAsync(S.slice_hub.p, shub.data(), shub.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    CD_CUDA(cudaMemcpyAsync(S.d_it0.p, it0.data(), it0.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    CD_CUDA(cudaMemcpyAsync(S.d_sl0.p, sl0.data(), sl0.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     CD_CUDA(cudaMemcpyAsync(S.hubs.p, info.data(), H * sizeof(HubInfo), cudaMemcpyHostToDevice, s));
     CD_CUDA(cudaMemcpyAsync(S.hb1.p, b1.data(), H * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     CD_CUDA(cudaMemcpyAsync(S.hb2.p, b2.data(), H * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -220,6 +261,7 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     S.hub_vals.alloc(S.max_tab, s);
     S.hub_vals.zero();
     S.hub_wc.alloc(H, s);
+    S.hub_wc.zero();   // omega(u, C) slots: written by a decide slice, reset by the last one
     S.hub_occ.alloc(S.max_tab, s);
     S.hub_nocc.alloc(H, s);
     S.hub_nocc.zero();
@@ -232,7 +274,7 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     S.part_w.alloc(S.max_nb2, s);
     S.part_id.alloc(S.max_nb2, s);
     S.part_tk.alloc(S.max_nb2, s);
-    upload_class_meta(S, s);
+    upload_class_meta(S, it0, sl0, s);
     CD_CUDA(cudaStreamSynchronize(s));   // host vectors above go out of scope
 }
 
@@ -260,6 +302,7 @@ struct PhaseRun {
     DBuf<uint64_t> tmp_a, tmp_b;
     DBuf<unsigned long long> nmv, ncand;
     DBuf<uint8_t> active;
+    DBuf<unsigned long long> sched;   // decide-slice and class-finish counters
     // set by the engine after the launch
     double launch_ms = 0, wall_ms = 0;
     cd_status fail = CD_OK;
@@ -280,10 +323,9 @@ static PhaseArgs phase_args(const GraphView &g, const Schedule &S, int32_t *zeta
     a.hubs = S.hubs.p;
     a.hb1 = S.hb1.p;
     a.hb2 = S.hb2.p;
-    a.item_hub = S.item_hub.p;
-    a.slice_hub = S.slice_hub.p;
-    a.class_it0 = S.d_it0.p;
-    a.class_sl0 = S.d_sl0.p;
+    a.chunks = S.chunks.p;
+    a.slices = S.slices.p;
+    a.meta = S.meta.p;
     a.hub_occ = S.hub_occ.p;
     a.hub_nocc = S.hub_nocc.p;
     a.hub_keys = S.hub_keys.p;
@@ -300,6 +342,9 @@ static PhaseArgs phase_args(const GraphView &g, const Schedule &S, int32_t *zeta
 }
 
 static void alloc_counters(PhaseRun &r, int32_t cap, cudaStream_t s) {
+    r.sched.alloc(2, s);
+    r.sched.zero();
+    r.a.sched = r.sched.p;
     r.cap = cap;
     r.cnt.alloc((size_t)cap + 1, s);
     r.cnt.zero();

@@ -26,9 +26,9 @@
 //              table, and every slot it fills is appended to the hub's
 //              occupied-slot list.  For hubs of degree <= HUB_LAST the block
 //              that merges the last chunk decides from that list at once;
-//              larger hubs are decided after a team barrier by hub-decide
-//              items that scan their tables in slices, the last slice of each
-//              hub taking the decision.
+//              larger hubs are decided by hub-decide slices that scan their
+//              tables once every chunk is merged (blocks take them after their
+//              own items), the last slice of each hub taking the decision.
 #pragma once
 #include <type_traits>
 
@@ -62,6 +62,22 @@ struct HubInfo {               // one hub vertex of a class
     int64_t slots;             // table size (power of two)
 };
 
+// Precomputed per work item of the hub roles, so that an item starts from
+// one record instead of a chain of dependent lookups.
+struct ChunkDesc {             // one aggregation item: a chunk of a hub's adjacency
+    int64_t beg, end;          // adjacency entries of the chunk
+    int64_t tab, slots;        // the hub's global table
+    int32_t u, h;              // hub vertex, class-relative hub index
+    int32_t nb1, nb2;          // the hub's aggregation items and decide slices
+};
+struct SliceDesc {             // one decide slice of a hub table
+    int64_t tab;               // the hub's global table
+    int64_t s0, s1;            // slots of the slice
+    int32_t u, h;              // hub vertex, class-relative hub index
+    int32_t nb1, nb2;
+    int32_t p0, pad;           // first slice of the hub inside the class (partial bests)
+};
+
 struct SweepCtx {
     GraphView g;
     int32_t *zeta;
@@ -87,7 +103,8 @@ struct SweepCtx {
     // hubs of this class
     const HubInfo *hubs;
     const int32_t *hub_b1, *hub_b2;      // exclusive prefix of hub blocks
-    const int32_t *item_hub, *slice_hub; // hub of each aggregation item / decide slice
+    const ChunkDesc *chunks;   // aggregation items of the class
+    const SliceDesc *slices;   // decide slices of the class
     int32_t nhubs;
     int32_t *hub_occ;          // occupied-slot lists (at each hub's table offset)
     unsigned int *hub_nocc;    // their lengths (0 between uses)
@@ -513,7 +530,7 @@ __device__ __forceinline__ void hub_finish(const SweepCtx &c, int32_t u, int32_t
 // counter), so the occupied-slot list is complete.  Scans the list, clears
 // the slots it used, and decides.
 template <int WK, bool BIG, bool PLP>
-__device__ __forceinline__ void hub_decide_occ(const SweepCtx &c, int h, const HubInfo &hi,
+__device__ __forceinline__ void hub_decide_occ(const SweepCtx &c, const ChunkDesc &hi,
                                                typename BestOf<PLP, BIG>::T *s_best, int *s_last) {
     using VT = ValT<BIG>;
     using BT = typename BestOf<PLP, BIG>::T;
@@ -522,7 +539,8 @@ __device__ __forceinline__ void hub_decide_occ(const SweepCtx &c, int h, const H
     VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
     const int32_t *occ = c.hub_occ + hi.tab;
     const uint32_t gmask = (uint32_t)(hi.slots - 1);
-    const int32_t u = hi.v;
+    const int32_t u = hi.u;
+    const int h = hi.h;
     const int32_t C = c.zeta[u];
     const int64_t nocc = (int64_t)__ldcg(c.hub_nocc + h);
     const int64_t wC = (int64_t)tab_lookup_cg<VT>(gk, gv, gmask, C);
@@ -568,16 +586,13 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
     VT *vals = reinterpret_cast<VT *>(smem + HUB_CHUNK_SLOTS * 4);
     int32_t *wsum = reinterpret_cast<int32_t *>(smem + HUB_CHUNK_SLOTS * 12);   // [kBlock / 32 + 2]
     static_assert(HUB_CHUNK_SLOTS * 12 + (kBlock / 32 + 2) * 4 <= SMEM_BYTES, "hub chunk scratch");
-    const int h = c.item_hub[rb];
-    const HubInfo hi = c.hubs[h];
-    const int32_t u = hi.v;
+    const ChunkDesc hi = c.chunks[rb];
+    const int h = hi.h;
+    const int32_t u = hi.u;
     if constexpr (PLP) {
         if (!c.active[u]) return;   // whole block; the decision skips it too
     }
-    const int j = rb - c.hub_b1[h];
-    const int64_t rbeg = c.g.rp[u], rend = c.g.rp[u + 1];
-    const int64_t beg = rbeg + (int64_t)j * HUB_CHUNK;
-    const int64_t end = min(rend, beg + HUB_CHUNK);
+    const int64_t beg = hi.beg, end = hi.end;
     for (int s = threadIdx.x; s < HUB_CHUNK_SLOTS; s += kBlock) { keys[s] = -1; vals[s] = 0; }
     __syncthreads();
     for (int64_t e = beg + threadIdx.x; e < end; e += kBlock)
@@ -631,14 +646,8 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
         atomicAdd(&c.cnt->entries, (unsigned long long)(end - beg));
     }
     __syncthreads();
-    if (!*s_last) return;
-    if (hi.nb2 == 0) {
-        hub_decide_occ<WK, BIG, PLP>(c, h, hi, s_best, s_last);
-    } else if (threadIdx.x == 0) {
-        __threadfence();
-        c.hub_done1[h] = 0;
-        static_cast<VT *>(c.hub_wc)[h] = tab_lookup_cg<VT>(gk, gv, gmask, c.zeta[u]);
-    }
+    // hubs with decide slices: the count reaching nb1 releases the slices
+    if (*s_last && hi.nb2 == 0) hub_decide_occ<WK, BIG, PLP>(c, hi, s_best, s_last);
 }
 
 }  // namespace cd

@@ -18,6 +18,15 @@ namespace cd {
 
 constexpr int PHASE_SMEM = 32768;          // dynamic shared memory per block
 constexpr int RC_SMALL = 4096;             // candidates sorted in shared memory
+// Per-class schedule record (read by one thread per block at class start).
+struct ClassMeta {
+    int64_t off[NBINS + 1];    // bucket offsets into the schedule order
+    int32_t h0, nhubs;         // first hub (global index), hubs of the class
+    int32_t nb1, nb2;          // aggregation items, decide slices
+    int32_t it0, sl0;          // first aggregation item / decide slice
+    int32_t pad[2];
+};
+
 struct PhaseArgs {
     GraphView g;
     int32_t *zeta;
@@ -28,8 +37,9 @@ struct PhaseArgs {
     const int32_t *class_nb1, *class_nb2;  // [ncol]
     const HubInfo *hubs;
     const int32_t *hb1, *hb2;
-    const int32_t *item_hub, *slice_hub;   // class-relative hub of each aggregation item / decide slice
-    const int32_t *class_it0, *class_sl0;  // [ncol] first item / slice of each class in those arrays
+    const ChunkDesc *chunks;               // aggregation items, class by class
+    const SliceDesc *slices;               // decide slices, class by class
+    const ClassMeta *meta;                 // [ncol]
     int32_t *hub_occ;                      // occupied-slot lists, laid out like the hub tables
     unsigned int *hub_nocc;                // per hub
     int32_t *hub_keys;
@@ -51,6 +61,7 @@ struct PhaseArgs {
     int32_t max_sweeps, recheck_from;
     // PLP
     uint8_t *active;
+    unsigned long long *sched;             // [1] class finish counter (starts at 0)
     uint64_t seed;
     double theta;
     int32_t max_iters;
@@ -61,16 +72,17 @@ struct PhaseArgs {
 
 // SweepCtx of class k (layout, roles, hubs).
 __device__ __forceinline__ int32_t class_ctx(const PhaseArgs &a, int32_t k, SweepCtx &c) {
-    const int64_t base = a.class_off[(int64_t)k * NBINS];
+    const ClassMeta m = a.meta[k];
+    const int64_t base = m.off[0];
     c.order = a.order + base;
-    for (int b = 0; b <= NBINS; b++) c.off[b] = a.class_off[(int64_t)k * NBINS + b] - base;
-    const int32_t h0 = a.class_hub0[k];
-    c.nhubs = a.class_hub0[k + 1] - h0;
+    for (int b = 0; b <= NBINS; b++) c.off[b] = m.off[b] - base;
+    const int32_t h0 = m.h0;
+    c.nhubs = m.nhubs;
     c.hubs = a.hubs + h0;
     c.hub_b1 = a.hb1 + h0;
     c.hub_b2 = a.hb2 + h0;
-    c.item_hub = a.item_hub + a.class_it0[k];
-    c.slice_hub = a.slice_hub + a.class_sl0[k];
+    c.chunks = a.chunks + m.it0;
+    c.slices = a.slices + m.sl0;
     c.hub_occ = a.hub_occ;
     c.hub_nocc = a.hub_nocc + h0;
     c.hub_keys = a.hub_keys;
@@ -89,8 +101,8 @@ __device__ __forceinline__ int32_t class_ctx(const PhaseArgs &a, int32_t k, Swee
     c.bend[1] = c.bend[0] + (int32_t)((n1 + kBlock / 8 - 1) / (kBlock / 8));
     c.bend[2] = c.bend[1] + (int32_t)((n2 + kBlock / 32 - 1) / (kBlock / 32));
     c.bend[3] = c.bend[2] + (int32_t)n3;
-    c.bend[4] = c.bend[3] + a.class_nb1[k];
-    return a.class_nb2[k];
+    c.bend[4] = c.bend[3] + m.nb1;
+    return m.nb2;
 }
 
 template <int WK, bool BIG, bool PLP>
@@ -104,35 +116,43 @@ __device__ __forceinline__ void run_item(const SweepCtx &c, int32_t b, unsigned 
 }
 
 // Hub decide: slice `item` of a hub table; the last slice of a hub decides.
+// A PLM slice ranks the candidates D != C by 2W omega(u,D) - vol(u) vol(D),
+// which differs from the gain only by a term that is the same for every D,
+// so the slices need not know omega(u, C); the slice that finds C in the
+// table records omega(u, C) for the last slice, which completes the gain of
+// the best candidate.  The hub's aggregation is complete when the slice
+// runs (wait_hub_ready).
 template <int WK, bool BIG, bool PLP>
 __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item, typename BestOf<PLP, BIG>::T *s_best,
                                                 unsigned *s_cand, int *s_last) {
     using VT = ValT<BIG>;
     using BT = typename BestOf<PLP, BIG>::T;
-    const int h = c.slice_hub[item];
-    const HubInfo hi = c.hubs[h];
-    const int32_t u = hi.v;
+    const SliceDesc hi = c.slices[item];
+    const int h = hi.h;
+    const int32_t u = hi.u;
     if constexpr (PLP) {
         if (!c.active[u]) return;
     }
-    const int j = item - c.hub_b2[h];
     int32_t *gk = c.hub_keys + hi.tab;
     VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
-    const int64_t s0 = (int64_t)j * HUB_SCAN, s1 = min(hi.slots, s0 + HUB_SCAN);
+    const int64_t s0 = hi.s0, s1 = hi.s1;
     const int32_t C = c.zeta[u];
-    const int64_t wC = (int64_t)static_cast<const VT *>(c.hub_wc)[h];
+    VT *hwc = static_cast<VT *>(c.hub_wc) + h;
     if (threadIdx.x == 0) *s_cand = 0;
     __syncthreads();
     unsigned ncand = 0;
     BT b;
     b.init();
     if constexpr (!PLP) {
-        const int64_t vu = c.g.vol[u], volC = c.volc[C], twoW = 2 * c.g.W;
+        using T = typename GainT<BIG>::T;
+        const int64_t vu = c.g.vol[u], twoW = 2 * c.g.W;
         for (int64_t s = s0 + threadIdx.x; s < s1; s += kBlock) {
             const int32_t key = gk[s];
             if (key >= 0) {
                 ncand++;
-                if (key != C) b.offer(plm_gain<BIG>(twoW, (int64_t)gv[s], wC, vu, c.volc[key], volC), key, (int64_t)gv[s]);
+                const int64_t w = (int64_t)gv[s];
+                if (key != C) b.offer((T)twoW * (T)w - (T)vu * (T)c.volc[key], key, w);
+                else { *hwc = (VT)w; __threadfence(); }
                 gk[s] = -1;
                 gv[s] = 0;
             }
@@ -142,7 +162,9 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
             const int32_t key = gk[s];
             if (key >= 0) {
                 ncand++;
-                b.offer((int64_t)gv[s], fmix32((uint32_t)key ^ c.tie_salt), key);
+                const int64_t w = (int64_t)gv[s];
+                b.offer(w, fmix32((uint32_t)key ^ c.tie_salt), key);
+                if (key == C) { *hwc = (VT)w; __threadfence(); }
                 gk[s] = -1;
                 gv[s] = 0;
             }
@@ -176,7 +198,7 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
     {   // merge the partial bests of every slice of this hub
         BT r;
         r.init();
-        const int64_t p0 = c.hub_b2[h];
+        const int64_t p0 = hi.p0;
         for (int k = threadIdx.x; k < hi.nb2; k += kBlock) {
             BT o;
             o.id = __ldcg(c.part_id + p0 + k);
@@ -197,8 +219,48 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
         }
         b = block_best(r, s_best);
     }
-    if (threadIdx.x == 0) c.hub_done2[h] = 0;
+    // omega(u, C) is 0 when no neighbour is in C (no slice recorded it)
+    const int64_t wC = (int64_t)__ldcg(hwc);
+    if constexpr (!PLP) {
+        using T = typename GainT<BIG>::T;
+        if (b.id >= 0) b.g = b.g - (T)(2 * c.g.W) * (T)wC + (T)c.g.vol[u] * (T)(c.volc[C] - c.g.vol[u]);
+    }
+    __syncthreads();   // every thread has read omega(u, C)
+    if (threadIdx.x == 0) {
+        c.hub_done2[h] = 0;
+        c.hub_done1[h] = 0;
+        *hwc = 0;
+    }
     hub_finish<BIG, PLP>(c, u, C, wC, b, s_last);
+}
+
+// Spins (thread 0, bounded by BARRIER_TIMEOUT_NS) until every aggregation
+// item of the hub of decide slice `item` has merged its chunk.  The caller
+// has finished all of its own items, and items never wait, so the wait
+// ends.  Returns false on a timeout (or a failure elsewhere in the team).
+template <bool PLP>
+__device__ __forceinline__ bool wait_hub_ready(const SweepCtx &c, int32_t item, GridBarrier *bar, int *s_ok) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const SliceDesc d = c.slices[item];
+        const int h = d.h;
+        const int32_t u = d.u;
+        const unsigned need = (unsigned)d.nb1;
+        bool skip = false;
+        if constexpr (PLP) skip = !c.active[u];   // inactive hubs are neither aggregated nor decided
+        if (!skip) {
+            const uint64_t t0 = global_ns();
+            while (__ldcg(c.hub_done1 + h) != need) {
+                if (*(volatile int *)&bar->err != 0) { ok = 0; break; }
+                if (global_ns() - t0 > BARRIER_TIMEOUT_NS) { atomicExch(&bar->err, 1); ok = 0; break; }
+                __nanosleep(64);
+            }
+            __threadfence();
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -362,8 +424,22 @@ struct BlockShared {
     BT *best;                  // [kBlock / 32]
     unsigned *cand, *gen;
     int *last, *ok, *nb2;
+    long long *grab;           // decide slice taken by the block
     SweepCtx *c;
 };
+
+// Hub-decide slices of a class: block r of the team takes slices r, r +
+// size, ... once it has finished its own items (so that no block waits for a
+// hub chunk that it holds itself).
+template <int WK, bool BIG, bool PLP, typename BT>
+__device__ __forceinline__ bool decide_pool(const Team &tm, const SweepCtx &c, int32_t nb2,
+                                            const BlockShared<BT> &sh) {
+    for (int32_t g = tm.rank; g < nb2; g += tm.size) {
+        if (!wait_hub_ready<PLP>(c, g, tm.bar, sh.ok)) return false;
+        role_hub_decide<WK, BIG, PLP>(c, g, sh.best, sh.cand, sh.last);
+    }
+    return true;
+}
 
 // ---------------------------------------------------------------------------
 // PLM move phase (Algorithm 2) of one graph, run by one team: sweeps until
@@ -377,6 +453,7 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
     int32_t prev_k = -1, prev_par = 0;
     int32_t sw = 0;
     int conv = 0;
+    unsigned long long fin_base = 0;   // same in every block of the team
     const int64_t gtid = (int64_t)tm.rank * kBlock + threadIdx.x, gthreads = (int64_t)tm.size * kBlock;
     for (; sw < a.max_sweeps; sw++) {
         const int par = sw & 1;
@@ -428,36 +505,43 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
                 }
             }
             const bool timed = a.stage_ns && tm.rank == 0 && threadIdx.x == 0;
-            uint64_t t0 = timed ? global_ns() : 0;
+            const uint64_t t0 = timed ? global_ns() : 0;
             // a block walks several items; the barrier keeps one item's warps
             // out of the shared tables of the next
             for (int32_t b = tm.rank; b < c.bend[4]; b += tm.size) {
                 run_item<WK, BIG, false>(c, b, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
             }
-            if (!team_sync(tm, sh.gen, sh.ok)) return false;
-            if (timed) { const uint64_t t1 = global_ns(); a.stage_ns[0] += t1 - t0; t0 = t1; }
             if (nb2 > 0) {
-                for (int32_t b = tm.rank; b < nb2; b += tm.size)
-                    role_hub_decide<WK, BIG, false>(c, b, sh.best, sh.cand, sh.last);
-                if (!team_sync(tm, sh.gen, sh.ok)) return false;
-                if (timed) { const uint64_t t1 = global_ns(); a.stage_ns[1] += t1 - t0; t0 = t1; }
+                if (!decide_pool<WK, BIG, false>(tm, c, nb2, sh)) return false;
             }
             if (late) {
-                if (__ldcg(c.ncand) != 0) {   // same value in every block after the barrier
-                    if (tm.rank == 0) {
+                // the block that finishes the class last re-checks its wanted moves
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    const unsigned long long f = atomicAdd(a.sched + 1, 1ull);
+                    *sh.last = f == fin_base + (unsigned long long)tm.size - 1;
+                }
+                __syncthreads();
+                const bool finisher = *sh.last != 0;
+                fin_base += (unsigned long long)tm.size;
+                if (finisher) {
+                    __threadfence();
+                    if (__ldcg(c.ncand) != 0) {
+                        const uint64_t r0 = a.stage_ns ? global_ns() : 0;
                         RecheckArgs ra{c.cand_u, c.cand_c, c.cand_d, c.cand_wd, c.cand_wc, c.ncand, a.zeta,
                                        a.g.vol, c.volw, 2 * a.g.W, a.tmp_a, a.tmp_b, a.ubits, c.cnt};
                         recheck_block<BIG>(ra, sh.smem);
+                        if (a.stage_ns && threadIdx.x == 0) atomicAdd(a.stage_ns + 2, global_ns() - r0);
                     }
-                    if (!team_sync(tm, sh.gen, sh.ok)) return false;
-                    if (timed) a.stage_ns[2] += global_ns() - t0;
                 }
             } else {
                 prev_k = k;
                 prev_par = par;
                 t++;
             }
+            if (!team_sync(tm, sh.gen, sh.ok)) return false;
+            if (timed) a.stage_ns[0] += global_ns() - t0;
         }
         if (__ldcg(&a.cnt[sw].wanted) == 0) {
             conv = 1;
@@ -502,12 +586,10 @@ __device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<P
                 run_item<WK, BIG, true>(c, b, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
             }
-            if (!team_sync(tm, sh.gen, sh.ok)) return false;
             if (nb2 > 0) {
-                for (int32_t b = tm.rank; b < nb2; b += tm.size)
-                    role_hub_decide<WK, BIG, true>(c, b, sh.best, sh.cand, sh.last);
-                if (!team_sync(tm, sh.gen, sh.ok)) return false;
+                if (!decide_pool<WK, BIG, true>(tm, c, nb2, sh)) return false;
             }
+            if (!team_sync(tm, sh.gen, sh.ok)) return false;
         }
         if (!team_sync(tm, sh.gen, sh.ok)) return false;
         updated = __ldcg(&a.cnt[it].moved);
@@ -550,11 +632,12 @@ struct BatchArgs {
     __shared__ BT s_best[kBlock / 32];                                          \
     __shared__ unsigned s_cand, s_gen;                                          \
     __shared__ int s_last, s_ok, s_nb2;                                         \
+    __shared__ long long s_grab;                                                \
     __shared__ SweepCtx s_ctx;                                                  \
     __shared__ __align__(16) unsigned long long s_args[sizeof(PhaseArgs) / 8];  \
     if (threadIdx.x == 0) s_gen = 0;                                            \
     __syncthreads();                                                            \
-    const BlockShared<BT> sh{smem, s_best, &s_cand, &s_gen, &s_last, &s_ok, &s_nb2, &s_ctx};
+    const BlockShared<BT> sh{smem, s_best, &s_cand, &s_gen, &s_last, &s_ok, &s_nb2, &s_grab, &s_ctx};
 
 static_assert(sizeof(PhaseArgs) % 8 == 0, "PhaseArgs is copied in 64-bit words");
 
