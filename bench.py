@@ -45,6 +45,8 @@ def args_():
                    help="plm: R-MAT PLM (default); batch: 512 planted-partition graphs in one batched "
                         "call vs one call per graph; serve: Poisson request stream, continuous-batching "
                         "server vs a one-at-a-time FIFO server")
+    p.add_argument("--tune", type=int, default=0,
+                   help="autotune the launch shape with this many trial runs (cd_tune) before the warm-up")
     p.add_argument("--batch-graphs", type=int, default=512)
     p.add_argument("--serve-requests", type=int, default=400)
     p.add_argument("--serve-rate", type=float, default=200.0)
@@ -272,6 +274,17 @@ def run_ours(a):
     labels = torch.empty(g.n, dtype=torch.int32, device=dev)
     opts_plain = cd.default_opts(seed=1)
     opts_prof = cd.default_opts(seed=1, profile=True)
+    tuned = None
+    if a.tune:
+        task = cd.make_task(cd.CD_ALGO_EPP if wl["algo"] == "epp" else cd.CD_ALGO_PLM, wl["refine"], EPP_B)
+        t = time.perf_counter()
+        best, best_ms = cd.cd_tune([G.h], task, opts_plain, a.tune)
+        tuned = {"trials": a.tune, "tune_s": time.perf_counter() - t, "best_run_ms": best_ms,
+                 "team_quantum": best.team_quantum, "team_min": best.team_min, "bin_max": list(best.bin_max)}
+        for o in (opts_plain, opts_prof):
+            o.team_quantum, o.team_min = best.team_quantum, best.team_min
+            for i in range(4):
+                o.bin_max[i] = best.bin_max[i]
 
     def run(h, out, opts):
         if wl["algo"] == "epp":
@@ -387,6 +400,7 @@ def run_ours(a):
                 "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz + (0 if g.w is None else 4 * g.nnz),
                 "d2h_bytes_per_step": 4 * g.n, "labels_match_device_run": e2e_ok},
         "gpu_launches": launches,
+        "tuned": tuned,
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": clocks,
@@ -443,6 +457,13 @@ def run_batch_workload(a):
     outs_batch = [torch.empty(max(G.n, 1), dtype=torch.int32, device=dev)[:G.n] for G in Gs]
     task = cd.make_task(cd.CD_ALGO_PLM)
     opts = cd.default_opts(seed=1)
+    tuned = None
+    if a.tune:
+        t = time.perf_counter()
+        best, best_ms = cd.cd_tune(handles, task, opts, a.tune)
+        tuned = {"trials": a.tune, "tune_s": time.perf_counter() - t, "best_run_ms": best_ms,
+                 "team_quantum": best.team_quantum, "team_min": best.team_min, "bin_max": list(best.bin_max)}
+        opts = best
 
     def plain_pass():
         for G, o in zip(Gs, outs_plain):
@@ -501,6 +522,7 @@ def run_batch_workload(a):
         "e2e": {"value": len(Gs) / e2e_s, "unit": "graphs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 4 * n_tot, "labels_match_device_run": e2e_same},
         "gpu_launches": launches / a.steps,
+        "tuned": tuned,
         "generation_s": gen_s,
         "clocks": clocks,
     }

@@ -56,7 +56,8 @@ typedef enum {
 enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1 };
 
 /* Options.  cd_opts_default() fills: seed 1, max_sweeps 256, max_levels 64,
- * max_iters 1000, profile 0, team_quantum 262144, team_min 8.
+ * max_iters 1000, profile 0, team_quantum 262144, team_min 8,
+ * bin_max {4, 16, 128, 1024}.
  *   seed        colouring priorities (Jones-Plassmann) and the PLP tie order
  *               derive from it; EPP base i uses seed+i.
  *   max_sweeps  cap on sweeps of one move phase (Algorithm 2 "repeat").
@@ -69,7 +70,13 @@ enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1 };
  *               + vertices) is w gets teams of at least
  *               ceil(w / team_quantum) blocks rounded up to a power of two,
  *               and up to team_min graphs of a tier run side by side.  They
- *               change speed only, never results. */
+ *               change speed only, never results.
+ *   bin_max     degree limits of the schedule's vertex roles: degree <=
+ *               bin_max[0] -> 4 lanes, <= bin_max[1] -> 8 lanes, <= bin_max[2]
+ *               -> a warp, <= bin_max[3] -> a block, above -> multi-block hub
+ *               path.  Limits may not exceed 4, 16, 128, 1024 and must not
+ *               decrease (0 keeps the default).  Speed only, never results.
+ * cd_tune picks team_quantum, team_min and bin_max by measurement. */
 typedef struct {
     uint64_t seed;
     int32_t max_sweeps;
@@ -79,6 +86,7 @@ typedef struct {
     int64_t team_quantum;
     int32_t team_min;
     int32_t reserved;   /* 0 */
+    int32_t bin_max[4];
 } cd_opts;
 
 /* Run statistics (all optional: pass NULL to skip). */
@@ -191,6 +199,18 @@ typedef struct {
  * when some run hit its cap (results still valid). */
 cd_status cd_run_batch(cd_graph *const *gs, int count, const cd_task *task, const cd_opts *o,
                        int32_t *const *labels, int labels_mem, double *mods, cd_stats *st, void *stream);
+
+/* Launch-shape autotuner: runs `task` on the count graphs (together, as
+ * cd_run_batch does, when count > 1) under candidate values of team_quantum,
+ * team_min (only when launches are shared: count > 1 or EPP) and bin_max,
+ * one option at a time, keeping a candidate when its complete run is at
+ * least 1% faster than the current choice, until max_trials runs have been
+ * made.  *best receives `base` (NULL: defaults) with the chosen shape and
+ * *best_ms (may be NULL) the wall time of its run.  These options never
+ * change results, so tuning is safe on the caller's own workload.
+ * Synchronous.  Errors: CD_EINVAL, then those of the runs. */
+cd_status cd_tune(cd_graph *const *gs, int count, const cd_task *task, const cd_opts *base, int max_trials,
+                  cd_opts *best, double *best_ms, void *stream);
 
 /* cd_run_batch of PLM (refine 0) or PLMR (refine 1) on the stream of gs[0]. */
 cd_status cd_plm_batch(cd_graph *const *gs, int count, int refine, const cd_opts *o,

@@ -37,7 +37,8 @@ class cd_opts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("max_sweeps", ctypes.c_int32),
                 ("max_levels", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("team_quantum", ctypes.c_int64),
-                ("team_min", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("team_min", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("bin_max", ctypes.c_int32 * 4)]
 
 
 class cd_stats(ctypes.Structure):
@@ -73,7 +74,7 @@ SYMBOLS = ["cd_opts_default", "cd_status_str", "cd_last_error", "cd_graph_create
            "cd_epp", "cd_color", "cd_coarsen", "cd_graph_export", "cd_debug_fail_alloc",
            "cd_launch_count", "cd_modularity_static", "cd_run_batch", "cd_plm_batch",
            "cd_server_create", "cd_server_submit", "cd_server_poll", "cd_server_info",
-           "cd_server_destroy"]
+           "cd_server_destroy", "cd_tune"]
 
 
 def library_path() -> str:
@@ -113,6 +114,7 @@ def lib():
             L.cd_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.c_double, P, c_int, P, P, P]
             L.cd_server_info.argtypes = [P, P, P, P]
             L.cd_server_destroy.argtypes = [P]
+            L.cd_tune.argtypes = [P, c_int, P, P, c_int, P, P, P]
             L.cd_launch_count.argtypes = []
             L.cd_launch_count.restype = ctypes.c_uint64
             for name in SYMBOLS:
@@ -162,7 +164,7 @@ def _stream(stream):
 
 def default_opts(seed: int = 1, max_sweeps: int = 256, max_levels: int = 64,
                  max_iters: int = 1000, profile: bool = False, team_quantum: int = 0,
-                 team_min: int = 0) -> cd_opts:
+                 team_min: int = 0, bin_max=None) -> cd_opts:
     o = cd_opts()
     lib().cd_opts_default(ctypes.byref(o))
     o.seed, o.max_sweeps, o.max_levels, o.max_iters, o.profile = seed, max_sweeps, max_levels, max_iters, int(profile)
@@ -170,6 +172,9 @@ def default_opts(seed: int = 1, max_sweeps: int = 256, max_levels: int = 64,
         o.team_quantum = team_quantum
     if team_min:
         o.team_min = team_min
+    if bin_max is not None:
+        for i, v in enumerate(bin_max):
+            o.bin_max[i] = int(v)
     return o
 
 
@@ -318,6 +323,18 @@ def cd_plm_batch(handles, labels_list, refine: bool = False, opts=None):
     status = lib().cd_plm_batch(hs, count, int(refine), ctypes.byref(o), lps, mem, mods, sts)
     _check(status)
     return [mods[i] for i in range(count)], [sts[i].as_dict() for i in range(count)], status
+
+
+def cd_tune(handles, task: cd_task, opts=None, max_trials: int = 12, stream=None):
+    """Returns (best cd_opts, its run time in ms)."""
+    o = opts or default_opts()
+    count = len(handles)
+    hs = (ctypes.c_void_p * max(count, 1))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    best = cd_opts()
+    ms = ctypes.c_double()
+    _check(lib().cd_tune(hs, count, ctypes.byref(task), ctypes.byref(o), int(max_trials), ctypes.byref(best),
+                         ctypes.byref(ms), _stream(stream)), False)
+    return best, ms.value
 
 
 def cd_server_create(device_mem_budget: int = 0, max_slots: int = 64, max_queue: int = 4096, stream=None):

@@ -59,11 +59,11 @@ struct Schedule {
     DBuf<int32_t> d_hub0, d_nb1, d_nb2;
 };
 
-__global__ void k_sched_keys(const int64_t *rp, int64_t n, const int32_t *color, int32_t ncol, uint32_t *key,
-                             int32_t *val) {
+__global__ void k_sched_keys(const int64_t *rp, int64_t n, const int32_t *color, int32_t ncol, BinLimits bins,
+                             uint32_t *key, int32_t *val) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = rp[i + 1] - rp[i];
-        key[i] = d == 0 ? (uint32_t)ncol * NBINS : (uint32_t)color[i] * NBINS + degree_bin(d);
+        key[i] = d == 0 ? (uint32_t)ncol * NBINS : (uint32_t)color[i] * NBINS + degree_bin(d, bins);
         val[i] = (int32_t)i;
     }
 }
@@ -123,7 +123,7 @@ static void upload_class_meta(Schedule &S, const std::vector<int32_t> &it0, cons
     CD_CUDA(cudaStreamSynchronize(s));   // the host vectors may change after return
 }
 
-static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaStream_t s) {
+static void build_schedule(const GraphView &g, uint64_t seed, const BinLimits &bins, Schedule &S, cudaStream_t s) {
     const int64_t n = g.n;
     DBuf<int32_t> color(n, s);
     S.ncol = color_graph(g, seed, color.p, s);
@@ -133,7 +133,7 @@ static void build_schedule(const GraphView &g, uint64_t seed, Schedule &S, cudaS
     if (n) {
         DBuf<uint32_t> key(n, s), key2(n, s);
         DBuf<int32_t> val2(n, s);
-        { k_sched_keys<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(g.rp, n, color.p, S.ncol, key.p, S.order.p); ::cd::note_launch(); }
+        { k_sched_keys<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(g.rp, n, color.p, S.ncol, bins, key.p, S.order.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
         std::vector<int> digits;
         for (int d = 0; d < bits_for(nbk + 1); d += 8) digits.push_back(d);
@@ -608,7 +608,7 @@ static void start_level(Job &j, cudaStream_t s) {
     JobState &x = *j.state;
     Level &lv = *x.L.back();
     auto t = Clock::now();
-    build_schedule(lv.g, j.spec.o.seed, lv.S, s);
+    build_schedule(lv.g, j.spec.o.seed, j.spec.o.bins, lv.S, s);
     j.st.ms_color += ms_since(t);
     if (x.L.size() == 1 && j.st.colors0 < 0) j.st.colors0 = lv.S.ncol;
     lv.zeta.alloc(lv.g.n, s);
@@ -640,7 +640,7 @@ static void advance_impl(Job &j, cudaStream_t s) {
                 Level &lv = *x.L[0];
                 lv.g = sp.g;
                 auto t = Clock::now();
-                build_schedule(sp.g, sp.o.seed, lv.S, s);
+                build_schedule(sp.g, sp.o.seed, sp.o.bins, lv.S, s);
                 st.ms_color += ms_since(t);
                 if (st.colors0 < 0) st.colors0 = lv.S.ncol;
                 x.run = prepare_plp(sp.g, lv.S, j.labels(), sp.o.seed, sp.theta, sp.o, s);
@@ -654,7 +654,7 @@ static void advance_impl(Job &j, cudaStream_t s) {
                     const uint64_t seed = sp.o.seed + (uint64_t)i;
                     x.base_S.push_back(std::make_unique<Schedule>());
                     auto t = Clock::now();
-                    build_schedule(sp.g, seed, *x.base_S[i], s);
+                    build_schedule(sp.g, seed, sp.o.bins, *x.base_S[i], s);
                     st.ms_color += ms_since(t);
                     if (i == 0) st.colors0 = x.base_S[0]->ncol;
                     x.base_runs.push_back(

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "move_kernels.cuh"
 
 namespace cd {
 
@@ -28,6 +29,7 @@ struct RunOpts {
     bool profile = false;
     int64_t team_quantum = int64_t(1) << 18;   // launch shape (speed only)
     int32_t team_min = 8;
+    BinLimits bins{{4, 16, 128, BLK_MAXDEG}};  // schedule degree bins (speed only)
 };
 
 enum Algo { ALGO_PLP = 0, ALGO_PLM = 1, ALGO_EPP = 2 };

@@ -45,8 +45,17 @@ constexpr int HUB_SCAN = 1024;      // hub table slots per hub-decide item
 constexpr int HUB_LAST = 2048;      // hubs up to this degree: decided by their last aggregation item
 constexpr int SMEM_BYTES = 24576;   // shared table union of every role
 
-__host__ __device__ inline int degree_bin(int64_t d) {
-    return d <= 4 ? 0 : d <= 16 ? 1 : d <= 128 ? 2 : d <= BLK_MAXDEG ? 3 : 4;
+// Degree bins of the schedule: bin b holds degrees in (lim[b-1], lim[b]];
+// degrees above lim[3] are hubs.  The limits are launch-shape options (they
+// move vertices between roles, never change a result) and may not exceed
+// the roles' capacities 4, 16, 128 and BLK_MAXDEG.
+struct BinLimits {
+    int32_t lim[4];
+};
+constexpr int32_t BIN_CAP[4] = {4, 16, 128, BLK_MAXDEG};
+
+__host__ __device__ inline int degree_bin(int64_t d, const BinLimits &b) {
+    return d <= b.lim[0] ? 0 : d <= b.lim[1] ? 1 : d <= b.lim[2] ? 2 : d <= b.lim[3] ? 3 : 4;
 }
 
 struct Counters {              // per sweep / iteration, device

@@ -233,3 +233,43 @@ def test_server_destroy_with_pending_runs():
     # the device is still usable
     r = Gs[0].plm()
     assert r.stats["converged"] == 1
+
+
+# ---------------------------------------------------------------------------
+# Degree-bin limits and the autotuner (speed-only options)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bins", [(4, 4, 4, 4), (1, 2, 3, 4), (2, 8, 32, 256), (4, 16, 128, 1024), (3, 12, 64, 512)])
+def test_bin_limits_change_nothing(O, bins):
+    """Moving vertices between the lane-group, block and hub roles leaves
+    every result and counter unchanged (the (4,4,4,4) case sends every vertex
+    above degree 4 down the multi-block hub path)."""
+    for g in (GRAPHS[0], GRAPHS[5], GRAPHS[7], GRAPHS[8], GRAPHS[9]):
+        G = cd.Graph.from_synth(g, device="cuda")
+        for refine in (False, True):
+            _same(G.plm(refine=refine, seed=2, bin_max=bins), G.plm(refine=refine, seed=2))
+        _same(G.plp(seed=2, bin_max=bins), G.plp(seed=2))
+    g = GRAPHS[5]
+    r = cd.Graph.from_synth(g, device="cuda").plm(refine=True, seed=2, bin_max=bins)
+    o = O.plm(*g.numpy(), refine=True, seed=2)
+    assert np.array_equal(r.labels.cpu().numpy(), o.labels)
+
+
+def test_bin_limits_validated():
+    G = cd.Graph.from_synth(GRAPHS[0], device="cuda")
+    for bad in [(5, 16, 128, 1024), (4, 3, 128, 1024), (4, 16, 129, 1024), (4, 16, 128, 2048), (-1, 16, 128, 1024)]:
+        with pytest.raises(cd.CDError) as e:
+            G.plm(bin_max=bad)
+        assert e.value.status == cd.CD_EINVAL
+
+
+def test_tuner_returns_a_shape_with_identical_results():
+    Gs = [cd.Graph.from_synth(g, device="cuda") for g in GRAPHS[:6]]
+    task = cd.make_task(cd.CD_ALGO_PLM, refine=True)
+    best, ms = cd.cd_tune([G.h for G in Gs], task, cd.default_opts(seed=3), max_trials=6)
+    assert ms > 0 and best.seed == 3 and best.team_min >= 1 and best.team_quantum >= 1
+    kw = dict(seed=3, team_quantum=best.team_quantum, team_min=best.team_min, bin_max=list(best.bin_max))
+    for a, b in zip(cd.run_batch(Gs, cd.CD_ALGO_PLM, True, **kw), cd.run_batch(Gs, cd.CD_ALGO_PLM, True, seed=3)):
+        _same(a, b)
+    best1, _ = cd.cd_tune([Gs[1].h], cd.make_task(cd.CD_ALGO_PLP), None, max_trials=3)
+    assert list(best1.bin_max) != [0, 0, 0, 0]
