@@ -16,19 +16,26 @@
  * parallel schedule is nondeterministic there):
  *   - vol(u) sums the weights to neighbours other than u plus twice the
  *     self-loop (Section III-B, volume definition; read so that sum vol = 2W).
- *   - Schedule: colour classes of a hash-priority Jones-Plassmann distance-1
- *     colouring, processed in ascending colour; inside a class every vertex
- *     decides on the labels and community volumes as they stood when the
- *     class began, then all decisions of the class are applied.
+ *   - Schedule: colour classes of a hash-priority Jones-Plassmann colouring,
+ *     processed in ascending colour; inside a class every vertex decides on
+ *     the labels and community volumes as they stood when the class began,
+ *     then all decisions of the class are applied.  The colouring ignores
+ *     edges between two hubs (vertices with more than HUB_RELAX neighbours),
+ *     so adjacent hubs may share a class and then decide on each other's
+ *     labels from the start of the class: one instance of the stale data the
+ *     paper's parallel threads work with (Section III-B).
  *   - Ties in the argmax of the move rule go to the smallest community id;
  *     a move needs a strictly positive gain (Algorithm 2).  A move phase
  *     ends when no vertex wants to move; from its 5th sweep on, the wanted
  *     moves of a class are re-checked one by one in vertex order against
- *     the volumes already updated (see move_phase).
+ *     the volumes already updated, and a hub adjacent to a hub accepted
+ *     earlier in the class is passed over (see move_phase).
  *   - PLP adopts the dominant label only if its weight strictly exceeds the
  *     weight of the current label; ties between dominant labels follow a
  *     per-iteration pseudo-random order of the labels (fmix32 of the label
- *     xor a salt drawn from the seed and the iteration number).
+ *     xor a salt drawn from the seed and the iteration number).  Hubs are
+ *     evaluated in every iteration (active or not; the active set never
+ *     changes a result).
  *   - Every recursive PLM/PLMR call returns a compacted labelling (dense
  *     ranks in ascending order of raw label); prolongation works in that
  *     space.
@@ -43,6 +50,10 @@
 #include <string.h>
 
 typedef __int128 i128;
+
+/* Hubs for the colouring: more than HUB_RELAX neighbours (self-loop not
+ * counted).  Edges between two hubs do not constrain the colouring. */
+#define HUB_RELAX 1024
 
 /* ---------------------------------------------------------------------- */
 /* Graph: adjacency without self-loops, self-loop weights kept apart.       */
@@ -157,7 +168,8 @@ static int64_t compact(int64_t n, int32_t *z)
 }
 
 /* ---------------------------------------------------------------------- */
-/* Colouring: first-fit Jones-Plassmann with hash priorities.               */
+/* Colouring: first-fit Jones-Plassmann with hash priorities on the graph    */
+/* without its hub-hub edges.                                               */
 /* Priority of v: (fmix32(v ^ fmix32(seed_lo ^ seed_hi)), v), compared      */
 /* lexicographically, larger wins.  fmix32 is the MurmurHash3 32-bit        */
 /* finaliser (Appleby).                                                     */
@@ -173,6 +185,11 @@ static uint32_t fmix32(uint32_t h)
 static int prio_greater(const uint32_t *h, int32_t a, int32_t b)
 {
     return h[a] > h[b] || (h[a] == h[b] && a > b);
+}
+
+static int is_hub(const OG *g, int32_t v)
+{
+    return g->rp[v + 1] - g->rp[v] > HUB_RELAX;
 }
 
 static int32_t color_jp(const OG *g, uint64_t seed, int32_t *color)
@@ -192,14 +209,17 @@ static int32_t color_jp(const OG *g, uint64_t seed, int32_t *color)
         for (int64_t v = 0; v < n; v++) {
             if (color[v] >= 0) continue;
             int best = 1;
+            const int vh = is_hub(g, (int32_t)v);
             for (int64_t e = g->rp[v]; e < g->rp[v + 1] && best; e++) {
                 int32_t x = g->adj[e];
+                if (vh && is_hub(g, x)) continue;
                 if (color[x] < 0 && prio_greater(h, x, (int32_t)v)) best = 0;
             }
             if (best) pick[np++] = (int32_t)v;
         }
-        /* 2. they are pairwise non-adjacent: give each the smallest colour
-         *    not used by its neighbours coloured in earlier rounds */
+        /* 2. they are pairwise non-adjacent, hub pairs aside: give each the
+         *    smallest colour not used by its neighbours coloured in earlier
+         *    rounds (hub neighbours of a hub do not count) */
         for (int64_t i = 0; i < np; i++) {
             int32_t v = pick[i];
             int64_t deg = g->rp[v + 1] - g->rp[v];
@@ -208,7 +228,9 @@ static int32_t color_jp(const OG *g, uint64_t seed, int32_t *color)
                 taken = (char *)realloc(taken, (size_t)taken_cap);
             }
             memset(taken, 0, (size_t)deg + 1);
+            const int vh = is_hub(g, v);
             for (int64_t e = g->rp[v]; e < g->rp[v + 1]; e++) {
+                if (vh && is_hub(g, g->adj[e])) continue;
                 int32_t c = color[g->adj[e]];
                 if (c >= 0 && c <= deg) taken[c] = 1;
             }
@@ -335,9 +357,11 @@ static int32_t decide_move(const OG *g, const int32_t *z, const int64_t *volc,
  * not die out.  From sweep RECHECK_FROM on, the wanted moves of a class are
  * applied one at a time in ascending vertex id, each only if its gain,
  * recomputed with the volumes as updated by the moves applied before it, is
- * still positive (its target stays the one it chose).  Inside an independent
- * set only the volume terms of the gain interact, so each applied move then
- * raises modularity by its recomputed gain and the phase must terminate.
+ * still positive (its target stays the one it chose).  Vertices of a class
+ * are pairwise non-adjacent except hub pairs, and a hub adjacent to a hub
+ * already moved in this class is passed over (its omega(u, .) would be out
+ * of date); so only the volume terms of the gain interact, each applied move
+ * raises modularity by its recomputed gain, and the phase must terminate.
  * The paper lets concurrent threads work on stale data and reports that
  * termination was never a problem in practice (Section III-B). */
 #define RECHECK_FROM 4
@@ -356,12 +380,17 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
     s.acc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     s.touched = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
     for (int64_t u = 0; u < n; u++) volc[z[u]] += g->vol[u];
+    /* stamp[v] = class step in which a hub neighbour of hub v was accepted */
+    int64_t *stamp = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
+    for (int64_t u = 0; u < n; u++) stamp[u] = -1;
+    int64_t step = 0;
     int64_t total = 0;
     int converged = 0;
     for (int32_t sw = 0; sw < max_sweeps; sw++) {
         int64_t wanted = 0, moved = 0;
         for (int32_t k = 0; k < cl->ncol; k++) {
             int64_t a = cl->off[k], b = cl->off[k + 1];
+            step++;
             for (int64_t i = a; i < b; i++) {            /* decide */
                 int32_t u = cl->v[i];
                 prop[u] = decide_move(g, z, volc, u, &s, st, level0, &wprop[u], &wcur[u]);
@@ -384,11 +413,18 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
                 wanted += nc;
                 for (int64_t j = 0; j < nc; j++) {
                     int32_t u = byid[j], C = z[u], D = prop[u];
+                    /* a hub whose omega(u, .) changed with an accepted hub
+                     * neighbour of this class waits for the next sweep */
+                    const int uh = is_hub(g, u);
+                    if (uh && stamp[u] == step) continue;
                     if (gain(g->W, wprop[u], wcur[u], g->vol[u], volc[D], volc[C]) <= 0) continue;
                     volc[C] -= g->vol[u];
                     volc[D] += g->vol[u];
                     z[u] = D;
                     moved++;
+                    if (uh)
+                        for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++)
+                            if (is_hub(g, g->adj[e])) stamp[g->adj[e]] = step;
                 }
             }
         }
@@ -399,7 +435,7 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
     }
     if (!converged) st[ST_CONVERGED] = 0;
     st[ST_MOVES] += total;
-    free(wprop); free(wcur); free(byid);
+    free(wprop); free(wcur); free(byid); free(stamp);
     free(volc); free(prop); free(s.acc); free(s.touched);
     return total;
 }
@@ -540,7 +576,7 @@ static void plp_run(const OG *g, uint64_t seed, double theta, int32_t max_iter,
             for (int64_t i = a; i < b; i++) {
                 int32_t v = cl.v[i];
                 adopt[v] = 0;
-                if (!(use_active ? active[v] : 1)) continue;
+                if (use_active && !active[v] && !is_hub(g, v)) continue;
                 if (g->rp[v + 1] == g->rp[v]) continue;           /* deg(v) = 0 */
                 int64_t nt = gather_weights(g, z, v, &s);
                 int32_t bestl = -1;

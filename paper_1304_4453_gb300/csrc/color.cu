@@ -1,10 +1,12 @@
-// Distance-1 colouring used as the deterministic schedule of the move and
-// label-propagation sweeps: first-fit Jones-Plassmann with hash priorities.
+// Colouring used as the deterministic schedule of the move and label-
+// propagation sweeps: first-fit Jones-Plassmann with hash priorities on the
+// graph without its hub-hub edges (hubs: more than HUB_RELAX neighbours).
 //
 // Priority of v: (fmix32(v ^ s), v), larger wins.  Jones-Plassmann colours a
 // vertex once all of its higher-priority neighbours are coloured, giving it
 // the smallest colour none of them uses; the result equals greedy colouring
-// in descending priority order.
+// in descending priority order.  A hub neither waits for nor avoids the
+// colours of its hub neighbours.
 //
 // Dependency-count form: wait[v] = number of higher-priority neighbours.
 // Vertices with wait 0 form the first frontier.  A frontier vertex reads the
@@ -27,6 +29,8 @@ namespace cd {
 
 constexpr int COLOR_WARP_DEG = 64;     // frontier vertices up to this degree: one warp each
 constexpr int COLOR_BIG_DEG = 4096;    // up to this degree: one block each; above: chunked
+static_assert(COLOR_WARP_DEG <= HUB_RELAX && COLOR_BIG_DEG >= HUB_RELAX,
+              "warp-tier vertices are never hubs; chunked-tier vertices always are");
 
 __device__ __forceinline__ bool prio_gt(uint32_t hx, int32_t x, uint32_t hv, int32_t v) {
     return hx > hv || (hx == hv && x > v);
@@ -54,9 +58,11 @@ __global__ void k_color_init(const int64_t *__restrict__ rp, const int32_t *__re
     for (int64_t v = warp; v < n; v += nwarps) {
         const uint32_t hv = fmix32((uint32_t)v ^ s);
         const int64_t beg = rp[v], end = rp[v + 1];
+        const bool vh = end - beg > HUB_RELAX;
         int cnt = 0;
         for (int64_t e = beg + lane; e < end; e += 32) {
             const int32_t x = col[e];
+            if (vh && relaxed_hub(rp, x)) continue;
             cnt += prio_gt(fmix32((uint32_t)x ^ s), x, hv, (int32_t)v) ? 1 : 0;
         }
         cnt = __reduce_add_sync(0xffffffffu, cnt);
@@ -70,13 +76,15 @@ __global__ void k_color_init(const int64_t *__restrict__ rp, const int32_t *__re
     }
 }
 
-// Colours of higher-priority neighbours falling in [base, base + 64).
+// Colours of higher-priority neighbours falling in [base, base + 64)
+// (hub neighbours of a hub excluded).
 __device__ __forceinline__ unsigned long long window_bits(const int64_t *rp, const int32_t *col, const uint32_t *hash,
                                                           const int32_t *color, int32_t v, uint32_t hv, int64_t e0,
-                                                          int64_t step, uint32_t base) {
+                                                          int64_t step, uint32_t base, bool vh) {
     unsigned long long b = 0;
     for (int64_t e = rp[v] + e0; e < rp[v + 1]; e += step) {
         const int32_t x = col[e];
+        if (vh && relaxed_hub(rp, x)) continue;
         if (prio_gt(hash[x], x, hv, v)) {
             const uint32_t c = (uint32_t)color[x];
             if (c >= base && c < base + 64) b |= 1ull << (c - base);
@@ -111,7 +119,7 @@ __device__ __forceinline__ void color_warp_items(const int64_t *__restrict__ rp,
         uint32_t base = 0;
         while (bits == ~0ull) {
             base += 64;
-            bits = window_bits(rp, col, hash, color, v, hv, lane, 32, base);
+            bits = window_bits(rp, col, hash, color, v, hv, lane, 32, base, false);   // degree <= 64: no hub
             for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
         }
         if (lane == 0) {
@@ -130,11 +138,13 @@ __device__ __forceinline__ void color_block_items(const int64_t *__restrict__ rp
         const int32_t v = list[i];
         const uint32_t hv = hash[v];
         const int64_t beg = rp[v], end = rp[v + 1];
+        const bool vh = end - beg > HUB_RELAX;
         if (threadIdx.x == 0) sbits = 0;
         __syncthreads();
         unsigned long long bits = 0;
         for (int64_t e = beg + threadIdx.x; e < end; e += kBlock) {
             const int32_t x = col[e];
+            if (vh && relaxed_hub(rp, x)) continue;
             if (prio_gt(hash[x], x, hv, v)) {
                 const uint32_t c = (uint32_t)color[x];
                 if (c < 64) bits |= 1ull << c;
@@ -152,7 +162,7 @@ __device__ __forceinline__ void color_block_items(const int64_t *__restrict__ rp
             __syncthreads();
             if (threadIdx.x == 0) sbits = 0;
             __syncthreads();
-            unsigned long long b = window_bits(rp, col, hash, color, v, hv, threadIdx.x, kBlock, base);
+            unsigned long long b = window_bits(rp, col, hash, color, v, hv, threadIdx.x, kBlock, base, vh);
             for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
             if ((threadIdx.x & 31) == 0) atomicOr(&sbits, b);
             __syncthreads();
@@ -206,6 +216,7 @@ __device__ __forceinline__ void color_hub_items(const int64_t *__restrict__ rp, 
             const int64_t cb = beg + j * COLOR_CHUNK, ce = min(end, cb + COLOR_CHUNK);
             for (int64_t e = cb + threadIdx.x; e < ce; e += kBlock) {
                 const int32_t x = col[e];
+                if (relaxed_hub(rp, x)) continue;   // degree > 4096: v is a hub
                 if (prio_gt(hash[x], x, hv, v)) {
                     const uint32_t c = (uint32_t)color[x];
                     if (c < COLOR_BITS) atomicOr(&sbm[c >> 5], 1u << (c & 31));
@@ -238,7 +249,7 @@ __device__ __forceinline__ void color_hub_items(const int64_t *__restrict__ rp, 
                         __syncthreads();
                         if (threadIdx.x == 0) sbits = 0;
                         __syncthreads();
-                        unsigned long long b = window_bits(rp, col, hash, color, v, hv, threadIdx.x, kBlock, base);
+                        unsigned long long b = window_bits(rp, col, hash, color, v, hv, threadIdx.x, kBlock, base, true);
                         for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
                         if ((threadIdx.x & 31) == 0) atomicOr(&sbits, b);
                         __syncthreads();

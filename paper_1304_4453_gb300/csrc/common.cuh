@@ -193,6 +193,16 @@ __device__ __forceinline__ double i128_to_double(__int128 x) {
 
 constexpr int kBlock = 256;
 
+// Hubs of the schedule: vertices with more than HUB_RELAX neighbours
+// (self-loop not counted).  The colouring ignores edges between two hubs, so
+// adjacent hubs may share a colour class and then decide on each other's
+// labels as they stood when the class began.
+constexpr int64_t HUB_RELAX = 1024;
+
+__device__ __forceinline__ bool relaxed_hub(const int64_t *rp, int32_t v) {
+    return rp[v + 1] - rp[v] > HUB_RELAX;
+}
+
 inline unsigned grid_for(int64_t items, int per_block, int64_t cap = (int64_t)1 << 30) {
     int64_t g = (items + per_block - 1) / per_block;
     if (g < 1) g = 1;

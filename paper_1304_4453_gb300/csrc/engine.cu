@@ -40,6 +40,7 @@ struct Schedule {
     std::vector<int64_t> off;          // bucket k*NBINS+b -> [off[i], off[i+1])
     std::vector<int32_t> hub_start;    // per class, into the hub arrays
     std::vector<int32_t> nb1, nb2;     // per class H1 / H2 block totals
+    std::vector<int32_t> nrelax;       // per class, hubs with more than HUB_RELAX neighbours
     DBuf<HubInfo> hubs;
     DBuf<int32_t> hb1, hb2;            // per hub, block prefix inside its class
     DBuf<ChunkDesc> chunks;            // aggregation items, class by class
@@ -105,6 +106,7 @@ static void upload_class_meta(Schedule &S, const std::vector<int32_t> &it0, cons
         m.nb2 = S.nb2[k];
         m.it0 = it0[k];
         m.sl0 = sl0[k];
+        m.nrelax = S.nrelax.empty() ? 0 : S.nrelax[k];
     }
     S.meta.alloc(S.ncol, s);
     if (S.ncol)
@@ -148,6 +150,7 @@ static void build_schedule(const GraphView &g, uint64_t seed, const BinLimits &b
     S.hub_start.assign(S.ncol + 1, 0);
     S.nb1.assign(S.ncol, 0);
     S.nb2.assign(S.ncol, 0);
+    S.nrelax.assign(S.ncol, 0);
     int64_t H = 0;
     for (int32_t k = 0; k < S.ncol; k++) {
         S.hub_start[k] = (int32_t)H;
@@ -216,6 +219,7 @@ static void build_schedule(const GraphView &g, uint64_t seed, const BinLimits &b
                 d.h = hr;
                 d.nb1 = x.nb1;
                 d.nb2 = x.nb2;
+                d.relax = hd[h] > HUB_RELAX;
                 chunks.push_back(d);
             }
             for (int32_t j = 0; j < x.nb2; j++) {
@@ -228,8 +232,10 @@ static void build_schedule(const GraphView &g, uint64_t seed, const BinLimits &b
                 d.nb1 = x.nb1;
                 d.nb2 = x.nb2;
                 d.p0 = c2;
+                d.relax = hd[h] > HUB_RELAX;
                 slices.push_back(d);
             }
+            if (hd[h] > HUB_RELAX) S.nrelax[k]++;
             b1[h] = c1;
             b2[h] = c2;
             c1 += x.nb1;
@@ -303,6 +309,8 @@ struct PhaseRun {
     DBuf<unsigned long long> nmv, ncand;
     DBuf<uint8_t> active;
     DBuf<unsigned long long> sched;   // decide-slice and class-finish counters
+    DBuf<int32_t> dz_u, dz_l, hub_acc;  // deferred hub labels, re-check hub list
+    DBuf<unsigned int> dz_n;
     // set by the engine after the launch
     double launch_ms = 0, wall_ms = 0;
     cd_status fail = CD_OK;
@@ -341,10 +349,19 @@ static PhaseArgs phase_args(const GraphView &g, const Schedule &S, int32_t *zeta
     return a;
 }
 
-static void alloc_counters(PhaseRun &r, int32_t cap, cudaStream_t s) {
+static void alloc_counters(PhaseRun &r, int32_t cap, int64_t nhubs, cudaStream_t s) {
     r.sched.alloc(2, s);
     r.sched.zero();
     r.a.sched = r.sched.p;
+    r.dz_u.alloc(nhubs + 1, s);
+    r.dz_l.alloc(nhubs + 1, s);
+    r.hub_acc.alloc(nhubs + 1, s);
+    r.dz_n.alloc(1, s);
+    r.dz_n.zero();
+    r.a.dz_u = r.dz_u.p;
+    r.a.dz_l = r.dz_l.p;
+    r.a.dz_n = r.dz_n.p;
+    r.a.hub_acc = r.hub_acc.p;
     r.cap = cap;
     r.cnt.alloc((size_t)cap + 1, s);
     r.cnt.zero();
@@ -420,7 +437,7 @@ static std::unique_ptr<PhaseRun> prepare_move(const GraphView &g, const Schedule
         CD_LAUNCH_CHECK();
     }
     if (n) CD_CUDA(cudaMemcpyAsync(r->vol_b.p, r->vol_a.p, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    alloc_counters(*r, o.max_sweeps, s);
+    alloc_counters(*r, o.max_sweeps, S.nhubs, s);
     PhaseArgs &a = r->a;
     a.vol_a = r->vol_a.p;
     a.vol_b = r->vol_b.p;
@@ -477,7 +494,7 @@ static std::unique_ptr<PhaseRun> prepare_plp(const GraphView &g, const Schedule 
     r->active.alloc(g.n, s);
     if (g.n) CD_CUDA(cudaMemsetAsync(r->active.p, 1, g.n, s));
     iota32(zeta, g.n, s);
-    alloc_counters(*r, o.max_iters + 1, s);
+    alloc_counters(*r, o.max_iters + 1, S.nhubs, s);
     r->a.active = r->active.p;
     r->a.seed = seed;
     r->a.theta = theta;

@@ -78,13 +78,14 @@ struct ChunkDesc {             // one aggregation item: a chunk of a hub's adjac
     int64_t tab, slots;        // the hub's global table
     int32_t u, h;              // hub vertex, class-relative hub index
     int32_t nb1, nb2;          // the hub's aggregation items and decide slices
+    int32_t relax, pad;        // 1: more than HUB_RELAX neighbours (may share the class with hub neighbours)
 };
 struct SliceDesc {             // one decide slice of a hub table
     int64_t tab;               // the hub's global table
     int64_t s0, s1;            // slots of the slice
     int32_t u, h;              // hub vertex, class-relative hub index
     int32_t nb1, nb2;
-    int32_t p0, pad;           // first slice of the hub inside the class (partial bests)
+    int32_t p0, relax;         // first slice of the hub inside the class; more than HUB_RELAX neighbours
 };
 
 struct SweepCtx {
@@ -103,6 +104,9 @@ struct SweepCtx {
     const int32_t *rp_u, *rp_c;          // previous class's moves to replay
     const unsigned long long *rp_n;
     int late;                  // 1 from the re-check sweep on
+    int32_t nrelax;            // hubs of the class with more than HUB_RELAX neighbours
+    int32_t *dz_u, *dz_l;      // label writes of those hubs, deferred to the end of the class
+    unsigned int *dz_n;
     int32_t *cand_u, *cand_c, *cand_d;   // late sweeps: wanted moves
     int64_t *cand_wd, *cand_wc;          //   omega(u, D), omega(u, C \ u)
     unsigned long long *ncand;
@@ -284,11 +288,21 @@ __device__ __forceinline__ void vol_add(int64_t *v, int32_t c, int64_t x) {
 }
 
 // Applies a wanted move (early sweeps) or records it for the re-check.
+// A hub that may share its class with hub neighbours defers its label write
+// to the end of the class (defer_label), so that those neighbours decide on
+// the labels the class started from.
+__device__ __forceinline__ void defer_label(const SweepCtx &c, int32_t u, int32_t l) {
+    const unsigned i = atomicAdd(c.dz_n, 1u);
+    c.dz_u[i] = u;
+    c.dz_l[i] = l;
+}
+
 __device__ __forceinline__ void take_move(const SweepCtx &c, unsigned long long pos, int32_t u, int32_t C,
-                                          int32_t D, int64_t wD, int64_t wC) {
+                                          int32_t D, int64_t wD, int64_t wC, bool defer = false) {
     if (!c.late) {
         const int64_t vu = c.g.vol[u];
-        c.zeta[u] = D;
+        if (defer) defer_label(c, u, D);
+        else c.zeta[u] = D;
         c.mv_u[pos] = u;
         c.mv_c[pos] = C;
         vol_add(c.volw, C, -vu);
@@ -507,18 +521,22 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
 // wC are the same in every thread).
 template <bool BIG, bool PLP>
 __device__ __forceinline__ void hub_finish(const SweepCtx &c, int32_t u, int32_t C, int64_t wC,
-                                           const typename BestOf<PLP, BIG>::T &r, int *s_last) {
+                                           const typename BestOf<PLP, BIG>::T &r, int *s_last, bool relax) {
     if (threadIdx.x == 0) {
         if constexpr (!PLP) {
             const bool want = r.id >= 0 && r.g > 0;
-            if (want) take_move(c, atomicAdd(c.late ? c.ncand : c.nmv, 1ull), u, C, r.id, r.w, wC);
+            if (want) take_move(c, atomicAdd(c.late ? c.ncand : c.nmv, 1ull), u, C, r.id, r.w, wC, relax);
             atomicAdd(&c.cnt->wanted, (unsigned long long)want);
             atomicAdd(&c.cnt->moved, (unsigned long long)(want && !c.late));
             *s_last = 1;
         } else {
             const bool adopt = r.id >= 0 && r.w > wC;
-            if (adopt) c.zeta[u] = r.id;
-            else c.active[u] = 0;
+            if (adopt) {
+                if (relax) defer_label(c, u, r.id);
+                else c.zeta[u] = r.id;
+            } else {
+                c.active[u] = 0;
+            }
             atomicAdd(&c.cnt->moved, (unsigned long long)adopt);
             *s_last = adopt ? 2 : 1;
         }
@@ -582,7 +600,7 @@ __device__ __forceinline__ void hub_decide_occ(const SweepCtx &c, const ChunkDes
         c.hub_nocc[h] = 0;
         atomicAdd(&c.cnt->candidates, (unsigned long long)nocc);
     }
-    hub_finish<BIG, PLP>(c, u, C, wC, b, s_last);
+    hub_finish<BIG, PLP>(c, u, C, wC, b, s_last, hi.relax != 0);
 }
 
 template <int WK, bool BIG, bool PLP>
@@ -599,7 +617,9 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
     const int h = hi.h;
     const int32_t u = hi.u;
     if constexpr (PLP) {
-        if (!c.active[u]) return;   // whole block; the decision skips it too
+        // whole block; the decision skips it too.  Hubs that may share the
+        // class with hub neighbours are evaluated every iteration.
+        if (!hi.relax && !c.active[u]) return;
     }
     const int64_t beg = hi.beg, end = hi.end;
     for (int s = threadIdx.x; s < HUB_CHUNK_SLOTS; s += kBlock) { keys[s] = -1; vals[s] = 0; }

@@ -24,7 +24,8 @@ struct ClassMeta {
     int32_t h0, nhubs;         // first hub (global index), hubs of the class
     int32_t nb1, nb2;          // aggregation items, decide slices
     int32_t it0, sl0;          // first aggregation item / decide slice
-    int32_t pad[2];
+    int32_t nrelax;            // hubs with more than HUB_RELAX neighbours
+    int32_t pad;
 };
 
 struct PhaseArgs {
@@ -42,6 +43,9 @@ struct PhaseArgs {
     const ClassMeta *meta;                 // [ncol]
     int32_t *hub_occ;                      // occupied-slot lists, laid out like the hub tables
     unsigned int *hub_nocc;                // per hub
+    int32_t *dz_u, *dz_l;                  // deferred hub label writes of the current class
+    unsigned int *dz_n;                    //   and their count (0 between classes)
+    int32_t *hub_acc;                      // re-check scratch: hubs accepted in the current class
     int32_t *hub_keys;
     void *hub_vals, *hub_wc;
     unsigned int *done1, *done2;
@@ -102,6 +106,10 @@ __device__ __forceinline__ int32_t class_ctx(const PhaseArgs &a, int32_t k, Swee
     c.bend[2] = c.bend[1] + (int32_t)((n2 + kBlock / 32 - 1) / (kBlock / 32));
     c.bend[3] = c.bend[2] + (int32_t)n3;
     c.bend[4] = c.bend[3] + m.nb1;
+    c.nrelax = m.nrelax;
+    c.dz_u = a.dz_u;
+    c.dz_l = a.dz_l;
+    c.dz_n = a.dz_n;
     return m.nb2;
 }
 
@@ -131,7 +139,7 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
     const int h = hi.h;
     const int32_t u = hi.u;
     if constexpr (PLP) {
-        if (!c.active[u]) return;
+        if (!hi.relax && !c.active[u]) return;
     }
     int32_t *gk = c.hub_keys + hi.tab;
     VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
@@ -231,7 +239,7 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
         c.hub_done1[h] = 0;
         *hwc = 0;
     }
-    hub_finish<BIG, PLP>(c, u, C, wC, b, s_last);
+    hub_finish<BIG, PLP>(c, u, C, wC, b, s_last, hi.relax != 0);
 }
 
 // Spins (thread 0, bounded by BARRIER_TIMEOUT_NS) until every aggregation
@@ -247,7 +255,7 @@ __device__ __forceinline__ bool wait_hub_ready(const SweepCtx &c, int32_t item, 
         const int32_t u = d.u;
         const unsigned need = (unsigned)d.nb1;
         bool skip = false;
-        if constexpr (PLP) skip = !c.active[u];   // inactive hubs are neither aggregated nor decided
+        if constexpr (PLP) skip = !d.relax && !c.active[u];   // inactive hubs are neither aggregated nor decided
         if (!skip) {
             const uint64_t t0 = global_ns();
             while (__ldcg(c.hub_done1 + h) != need) {
@@ -284,7 +292,23 @@ struct RecheckArgs {
     uint64_t *tmp_a, *tmp_b;   // class-sized scratch for long candidate lists
     int ubits;                 // bits of the largest vertex id
     Counters *cnt;
+    const int64_t *rp;         // adjacency (sorted rows), for the hub rule
+    const int32_t *col;
+    int32_t *hub_acc;          // hubs accepted so far in this class
 };
+
+// True when sorted row of `a` contains b (binary search on the shorter row).
+__device__ __forceinline__ bool adjacent(const int64_t *rp, const int32_t *col, int32_t a, int32_t b) {
+    if (rp[a + 1] - rp[a] > rp[b + 1] - rp[b]) { const int32_t t = a; a = b; b = t; }
+    int64_t lo = rp[a], hi = rp[a + 1];
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int32_t x = col[mid];
+        if (x == b) return true;
+        if (x < b) lo = mid + 1; else hi = mid;
+    }
+    return false;
+}
 
 __device__ __forceinline__ void rc_radix_pass(const uint64_t *in, uint64_t *out, int64_t m, int shift,
                                               unsigned char *smem) {
@@ -369,6 +393,7 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
     }
     if (tid < 32) {
         unsigned long long moved = 0;
+        int nacc = 0;   // hubs accepted so far in this class (hub_acc[0, nacc))
         for (int64_t w0 = 0; w0 < m; w0 += 32) {
             const int64_t i = w0 + lane;
             const bool valid = i < m;
@@ -377,6 +402,7 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
             const int32_t C = valid ? __ldcg(a.cc + ci) : -1;
             const int32_t D = valid ? __ldcg(a.cd + ci) : -2;
             const int64_t vu = valid ? a.vol[u] : 0;
+            const bool hub = valid && a.rp[u + 1] - a.rp[u] > HUB_RELAX;
             const int64_t wD = valid ? __ldcg(a.cwd + ci) : 0, wC = valid ? __ldcg(a.cwc + ci) : 0;
             int64_t volC = valid ? __ldcg(a.volc + C) : 0;
             int64_t volD = valid ? __ldcg(a.volc + D) : 0;
@@ -384,7 +410,13 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
             const int cnt = (m - w0) < 32 ? (int)(m - w0) : 32;
             for (int k = 0; k < cnt; k++) {
                 int acc = 0;
-                if (lane == k) acc = plm_gain<BIG>(a.twoW, wD, wC, vu, volD, volC) > 0;
+                if (lane == k) {
+                    acc = plm_gain<BIG>(a.twoW, wD, wC, vu, volD, volC) > 0;
+                    // a hub next to a hub moved earlier in this class waits:
+                    // its omega(u, .) would be out of date
+                    for (int j = 0; acc && hub && j < nacc; j++)
+                        if (adjacent(a.rp, a.col, u, a.hub_acc[j])) acc = 0;
+                }
                 acc = __shfl_sync(0xffffffffu, acc, k);
                 if (acc) {
                     const int32_t Ck = __shfl_sync(0xffffffffu, C, k), Dk = __shfl_sync(0xffffffffu, D, k);
@@ -394,6 +426,11 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
                     } else if (lane > k) {
                         if (C == Ck) volC -= vk; else if (C == Dk) volC += vk;
                         if (D == Ck) volD -= vk; else if (D == Dk) volD += vk;
+                    }
+                    if (__shfl_sync(0xffffffffu, (int)hub, k)) {
+                        if (lane == k) a.hub_acc[nacc] = u;
+                        nacc++;
+                        __syncwarp();
                     }
                 }
             }
@@ -427,6 +464,30 @@ struct BlockShared {
     long long *grab;           // decide slice taken by the block
     SweepCtx *c;
 };
+
+// True in the block that finishes the class last (every block of the team
+// calls it once per class; the counter only grows, fin_base tracks it).
+__device__ __forceinline__ bool class_finisher(const PhaseArgs &a, const Team &tm, unsigned long long &fin_base,
+                                               int *s_flag) {
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long f = atomicAdd(a.sched + 1, 1ull);
+        *s_flag = f == fin_base + (unsigned long long)tm.size - 1;
+    }
+    __syncthreads();
+    const bool last = *s_flag != 0;
+    fin_base += (unsigned long long)tm.size;
+    if (last) __threadfence();
+    return last;
+}
+
+// Writes the labels that hubs of the class deferred (one block).
+__device__ __forceinline__ void apply_deferred_labels(const SweepCtx &c) {
+    const unsigned nd = __ldcg(c.dz_n);
+    for (unsigned i = threadIdx.x; i < nd; i += kBlock) c.zeta[__ldcg(c.dz_u + i)] = __ldcg(c.dz_l + i);
+    __syncthreads();
+    if (threadIdx.x == 0 && nd) *c.dz_n = 0;
+}
 
 // Hub-decide slices of a class: block r of the team takes slices r, r +
 // size, ... once it has finished its own items (so that no block waits for a
@@ -515,27 +576,24 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
             if (nb2 > 0) {
                 if (!decide_pool<WK, BIG, false>(tm, c, nb2, sh)) return false;
             }
-            if (late) {
-                // the block that finishes the class last re-checks its wanted moves
-                if (threadIdx.x == 0) {
-                    __threadfence();
-                    const unsigned long long f = atomicAdd(a.sched + 1, 1ull);
-                    *sh.last = f == fin_base + (unsigned long long)tm.size - 1;
-                }
-                __syncthreads();
-                const bool finisher = *sh.last != 0;
-                fin_base += (unsigned long long)tm.size;
+            if (late || c.nrelax > 0) {
+                // the block that finishes the class last re-checks its wanted
+                // moves (late sweeps) or writes the hubs' deferred labels
+                const bool finisher = class_finisher(a, tm, fin_base, sh.last);
                 if (finisher) {
-                    __threadfence();
-                    if (__ldcg(c.ncand) != 0) {
+                    if (!late) {
+                        apply_deferred_labels(c);
+                    } else if (__ldcg(c.ncand) != 0) {
                         const uint64_t r0 = a.stage_ns ? global_ns() : 0;
                         RecheckArgs ra{c.cand_u, c.cand_c, c.cand_d, c.cand_wd, c.cand_wc, c.ncand, a.zeta,
-                                       a.g.vol, c.volw, 2 * a.g.W, a.tmp_a, a.tmp_b, a.ubits, c.cnt};
+                                       a.g.vol, c.volw, 2 * a.g.W, a.tmp_a, a.tmp_b, a.ubits, c.cnt,
+                                       a.g.rp, a.g.col, a.hub_acc};
                         recheck_block<BIG>(ra, sh.smem);
                         if (a.stage_ns && threadIdx.x == 0) atomicAdd(a.stage_ns + 2, global_ns() - r0);
                     }
                 }
-            } else {
+            }
+            if (!late) {
                 prev_k = k;
                 prev_par = par;
                 t++;
@@ -566,6 +624,7 @@ __device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<P
     SweepCtx &c = *sh.c;
     int32_t it = 0;
     unsigned long long updated = (unsigned long long)a.g.n;
+    unsigned long long fin_base = 0;   // same in every block of the team
     while ((double)updated > a.theta && it < a.max_iters) {
         const uint32_t salt = plp_salt_dev(a.seed, it);
         for (int32_t k = 0; k < a.ncol; k++) {
@@ -589,6 +648,7 @@ __device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<P
             if (nb2 > 0) {
                 if (!decide_pool<WK, BIG, true>(tm, c, nb2, sh)) return false;
             }
+            if (c.nrelax > 0 && class_finisher(a, tm, fin_base, sh.last)) apply_deferred_labels(c);
             if (!team_sync(tm, sh.gen, sh.ok)) return false;
         }
         if (!team_sync(tm, sh.gen, sh.ok)) return false;

@@ -297,3 +297,31 @@ def test_sweep_cap_returns_notconv_with_valid_labels(O):
     o = O.plm(*g.numpy(), max_sweeps=2)
     assert r.status == cd.CD_ENOTCONV and o.stats["converged"] == 0
     assert np.array_equal(_np_labels(r.labels), o.labels)
+
+
+@pytest.mark.parametrize("nh,leaves,seed", [(5, 1100, 1), (4, 1030, 3), (12, 1500, 5)])
+def test_adjacent_hubs_share_classes(O, nh, leaves, seed):
+    """Mutually adjacent hubs (more than 1024 neighbours) share colour classes:
+    their label writes are deferred to the end of the class and the re-check
+    passes over a hub next to a hub moved earlier in the class.  Everything
+    must still match the oracle exactly, for PLM, PLMR, PLP and EPP."""
+    from tests.test_oracle_pins import _hub_core_graph
+    g = _hub_core_graph(nh=nh, leaves=leaves, seed=seed)
+    G = gpu_graph(g)
+    for seed_ in (1, 2):
+        k, col = cd.cd_color(G.h, torch.empty(g.n, dtype=torch.int32, device="cuda"), seed_), None
+        k2, col2 = O.color(*g.numpy(), seed_)
+        assert k == k2
+        for refine in (False, True):
+            r = G.plm(refine=refine, seed=seed_)
+            o = O.plm(*g.numpy(), refine=refine, seed=seed_)
+            assert np.array_equal(_np_labels(r.labels), o.labels)
+            assert abs(r.modularity - o.modularity) <= MOD_TOL
+            _same_stats(r.stats, o.stats, ["levels", "sweeps", "moves", "entries", "candidates", "decisions", "ncomm"])
+        r = G.plp(seed=seed_)
+        o = O.plp(*g.numpy(), seed=seed_)
+        assert np.array_equal(_np_labels(r.labels), o.labels)
+        _same_stats(r.stats, o.stats, ["iters", "moves", "entries", "candidates", "decisions", "ncomm"])
+    r = G.epp(b=3, seed=4)
+    o = O.epp(*g.numpy(), b=3, seed=4)
+    assert np.array_equal(_np_labels(r.labels), o.labels)

@@ -172,6 +172,72 @@ def test_colouring_equals_greedy_in_priority_order(oracle_mod, seed):
         assert col.tolist() == _greedy_in_priority_order(rp, c, seed)
 
 
+def _hub_core_graph(nh=5, leaves=1100, seed=1):
+    """nh mutually adjacent hubs (degree > 1024), each with `leaves` private
+    leaves grouped in 5-cliques, plus random leaf-leaf edges across hubs."""
+    rng = np.random.default_rng(seed)
+    n = nh + nh * leaves
+    edges = [(a, b) for a in range(nh) for b in range(a + 1, nh)]
+    for h in range(nh):
+        base = nh + h * leaves
+        for i in range(leaves):
+            edges.append((h, base + i))
+        for q in range(0, leaves - 4, 5):
+            grp = range(base + q, base + q + 5)
+            edges += [(x, y) for x in grp for y in grp if x < y]
+    for _ in range(3 * leaves):
+        x, y = rng.integers(nh, n, size=2)
+        if x != y:
+            edges.append((int(min(x, y)), int(max(x, y))))
+    return synth.from_edge_list(n, sorted(set(edges)))
+
+
+def test_colouring_ignores_only_hub_hub_edges(oracle_mod):
+    """Vertices with more than 1024 neighbours (hubs) do not constrain each
+    other's colours; every other edge is properly coloured, and the result is
+    sequential greedy colouring in priority order on the graph without its
+    hub-hub edges."""
+    g = _hub_core_graph()
+    rp, c, w = csr(g)
+    deg = np.diff(rp)
+    hub = deg > 1024
+    assert hub.sum() == 5
+    for seed in (1, 7):
+        k, col = oracle_mod.color(rp, c, w, seed)
+        same_hub_pair = 0
+        for u in range(g.n):
+            nb = c[rp[u]:rp[u + 1]]
+            for v in nb:
+                if col[u] == col[v]:
+                    assert hub[u] and hub[v], (u, v)
+                    same_hub_pair += 1
+        assert same_hub_pair > 0   # the hub clique shares colours
+        keep = ~(hub[np.repeat(np.arange(g.n), deg)] & hub[c])
+        c2 = c[keep]
+        rp2 = np.zeros(g.n + 1, np.int64)
+        rp2[1:] = np.cumsum(np.bincount(np.repeat(np.arange(g.n), deg)[keep], minlength=g.n))
+        assert col.tolist() == _greedy_in_priority_order(rp2, c2, seed)
+
+
+def test_hub_core_late_sweeps_never_lower_modularity(oracle_mod):
+    """With adjacent hubs in one class, the re-check passes over a hub next to
+    a hub already moved in the class, so late sweeps still never lower the
+    exact modularity and the phase converges."""
+    g = _hub_core_graph(nh=4, leaves=1030, seed=3)
+    rp, c, w = csr(g)
+    ed = exact.edges_of(rp, c, w)
+    full, st = oracle_mod.move_phase(rp, c, w, 2)
+    assert st["converged"] == 1
+    prev = None
+    for sweeps in range(4, st["sweeps"] + 1):
+        z, _ = oracle_mod.move_phase(rp, c, w, 2, max_sweeps=sweeps)
+        q = exact.modularity_fraction(g.n, ed, z)
+        if prev is not None:
+            assert q >= prev, sweeps
+        prev = q
+    assert np.array_equal(z, full)
+
+
 def test_colouring_isolated_and_complete(oracle_mod):
     g = synth.from_edge_list(4, [], self_loops={1: 3})
     rp, c, w = csr(g)
