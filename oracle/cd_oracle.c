@@ -28,8 +28,9 @@
  *     a move needs a strictly positive gain (Algorithm 2).  A move phase
  *     ends when no vertex wants to move; from its 5th sweep on, the wanted
  *     moves of a class are re-checked one by one in vertex order against
- *     the volumes already updated, and a hub adjacent to a hub accepted
- *     earlier in the class is passed over (see move_phase).
+ *     the volumes already updated, and a hub whose current or target
+ *     community a hub accepted earlier in the class left or entered is
+ *     passed over (see move_phase).
  *   - PLP adopts the dominant label only if its weight strictly exceeds the
  *     weight of the current label; ties between dominant labels follow a
  *     per-iteration pseudo-random order of the labels (fmix32 of the label
@@ -53,7 +54,7 @@ typedef __int128 i128;
 
 /* Hubs for the colouring: more than HUB_RELAX neighbours (self-loop not
  * counted).  Edges between two hubs do not constrain the colouring. */
-#define HUB_RELAX 1024
+#define HUB_RELAX 4096
 
 /* ---------------------------------------------------------------------- */
 /* Graph: adjacency without self-loops, self-loop weights kept apart.       */
@@ -358,10 +359,12 @@ static int32_t decide_move(const OG *g, const int32_t *z, const int64_t *volc,
  * applied one at a time in ascending vertex id, each only if its gain,
  * recomputed with the volumes as updated by the moves applied before it, is
  * still positive (its target stays the one it chose).  Vertices of a class
- * are pairwise non-adjacent except hub pairs, and a hub adjacent to a hub
- * already moved in this class is passed over (its omega(u, .) would be out
- * of date); so only the volume terms of the gain interact, each applied move
- * raises modularity by its recomputed gain, and the phase must terminate.
+ * are pairwise non-adjacent except hub pairs.  A hub moved in this class
+ * changes omega(v, .) of an adjacent hub v only for the two communities it
+ * left and entered, so a hub whose own current or target community is one
+ * of those is passed over; the omega terms of every accepted move are then
+ * exact, only the volume terms interact, each applied move raises
+ * modularity by its recomputed gain, and the phase must terminate.
  * The paper lets concurrent threads work on stale data and reports that
  * termination was never a problem in practice (Section III-B). */
 #define RECHECK_FROM 4
@@ -380,7 +383,7 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
     s.acc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     s.touched = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
     for (int64_t u = 0; u < n; u++) volc[z[u]] += g->vol[u];
-    /* stamp[v] = class step in which a hub neighbour of hub v was accepted */
+    /* stamp[X] = class step in which a hub moved into or out of community X */
     int64_t *stamp = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
     for (int64_t u = 0; u < n; u++) stamp[u] = -1;
     int64_t step = 0;
@@ -413,18 +416,17 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
                 wanted += nc;
                 for (int64_t j = 0; j < nc; j++) {
                     int32_t u = byid[j], C = z[u], D = prop[u];
-                    /* a hub whose omega(u, .) changed with an accepted hub
-                     * neighbour of this class waits for the next sweep */
+                    /* a hub whose omega(u, C) or omega(u, D) a hub moved
+                     * earlier in this class may have changed waits for the
+                     * next sweep */
                     const int uh = is_hub(g, u);
-                    if (uh && stamp[u] == step) continue;
+                    if (uh && (stamp[C] == step || stamp[D] == step)) continue;
                     if (gain(g->W, wprop[u], wcur[u], g->vol[u], volc[D], volc[C]) <= 0) continue;
                     volc[C] -= g->vol[u];
                     volc[D] += g->vol[u];
                     z[u] = D;
                     moved++;
-                    if (uh)
-                        for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++)
-                            if (is_hub(g, g->adj[e])) stamp[g->adj[e]] = step;
+                    if (uh) { stamp[C] = step; stamp[D] = step; }
                 }
             }
         }

@@ -197,7 +197,7 @@ constexpr int kBlock = 256;
 // (self-loop not counted).  The colouring ignores edges between two hubs, so
 // adjacent hubs may share a colour class and then decide on each other's
 // labels as they stood when the class began.
-constexpr int64_t HUB_RELAX = 1024;
+constexpr int64_t HUB_RELAX = 4096;
 
 __device__ __forceinline__ bool relaxed_hub(const int64_t *rp, int32_t v) {
     return rp[v + 1] - rp[v] > HUB_RELAX;

@@ -204,7 +204,8 @@ static void build_schedule(const GraphView &g, uint64_t seed, const BinLimits &b
             x.v = hv[h];
             x.nb1 = (int32_t)((hd[h] + HUB_CHUNK - 1) / HUB_CHUNK);
             // hubs up to HUB_LAST are decided by their last aggregation item
-            x.nb2 = hd[h] <= HUB_LAST ? 0 : (int32_t)((slots + HUB_SCAN - 1) / HUB_SCAN);
+            // (the occupied list of a hub holds at most deg entries)
+            x.nb2 = hd[h] <= HUB_LAST ? 0 : (int32_t)((hd[h] + HUB_SCAN - 1) / HUB_SCAN);
             x.pad = 0;
             x.tab = tab;
             x.slots = slots;
@@ -226,7 +227,7 @@ static void build_schedule(const GraphView &g, uint64_t seed, const BinLimits &b
                 SliceDesc d{};
                 d.tab = tab;
                 d.s0 = (int64_t)j * HUB_SCAN;
-                d.s1 = std::min(slots, d.s0 + HUB_SCAN);
+                d.s1 = d.s0 + HUB_SCAN;
                 d.u = hv[h];
                 d.h = hr;
                 d.nb1 = x.nb1;
@@ -309,7 +310,8 @@ struct PhaseRun {
     DBuf<unsigned long long> nmv, ncand;
     DBuf<uint8_t> active;
     DBuf<unsigned long long> sched;   // decide-slice and class-finish counters
-    DBuf<int32_t> dz_u, dz_l, hub_acc;  // deferred hub labels, re-check hub list
+    DBuf<int32_t> dz_u, dz_l;         // deferred hub labels
+    DBuf<int32_t> cstamp;             // re-check community stamps
     DBuf<unsigned int> dz_n;
     // set by the engine after the launch
     double launch_ms = 0, wall_ms = 0;
@@ -349,19 +351,20 @@ static PhaseArgs phase_args(const GraphView &g, const Schedule &S, int32_t *zeta
     return a;
 }
 
-static void alloc_counters(PhaseRun &r, int32_t cap, int64_t nhubs, cudaStream_t s) {
+static void alloc_counters(PhaseRun &r, int32_t cap, int64_t nhubs, int64_t n, cudaStream_t s) {
     r.sched.alloc(2, s);
     r.sched.zero();
     r.a.sched = r.sched.p;
     r.dz_u.alloc(nhubs + 1, s);
     r.dz_l.alloc(nhubs + 1, s);
-    r.hub_acc.alloc(nhubs + 1, s);
+    r.cstamp.alloc(n, s);
+    r.cstamp.zero();
     r.dz_n.alloc(1, s);
     r.dz_n.zero();
     r.a.dz_u = r.dz_u.p;
     r.a.dz_l = r.dz_l.p;
     r.a.dz_n = r.dz_n.p;
-    r.a.hub_acc = r.hub_acc.p;
+    r.a.cstamp = r.cstamp.p;
     r.cap = cap;
     r.cnt.alloc((size_t)cap + 1, s);
     r.cnt.zero();
@@ -437,7 +440,7 @@ static std::unique_ptr<PhaseRun> prepare_move(const GraphView &g, const Schedule
         CD_LAUNCH_CHECK();
     }
     if (n) CD_CUDA(cudaMemcpyAsync(r->vol_b.p, r->vol_a.p, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    alloc_counters(*r, o.max_sweeps, S.nhubs, s);
+    alloc_counters(*r, o.max_sweeps, S.nhubs, n, s);
     PhaseArgs &a = r->a;
     a.vol_a = r->vol_a.p;
     a.vol_b = r->vol_b.p;
@@ -494,7 +497,7 @@ static std::unique_ptr<PhaseRun> prepare_plp(const GraphView &g, const Schedule 
     r->active.alloc(g.n, s);
     if (g.n) CD_CUDA(cudaMemsetAsync(r->active.p, 1, g.n, s));
     iota32(zeta, g.n, s);
-    alloc_counters(*r, o.max_iters + 1, S.nhubs, s);
+    alloc_counters(*r, o.max_iters + 1, S.nhubs, 0, s);
     r->a.active = r->active.p;
     r->a.seed = seed;
     r->a.theta = theta;

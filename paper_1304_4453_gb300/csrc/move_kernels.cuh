@@ -26,9 +26,10 @@
 //              table, and every slot it fills is appended to the hub's
 //              occupied-slot list.  For hubs of degree <= HUB_LAST the block
 //              that merges the last chunk decides from that list at once;
-//              larger hubs are decided by hub-decide slices that scan their
-//              tables once every chunk is merged (blocks take them after their
-//              own items), the last slice of each hub taking the decision.
+//              larger hubs are decided by hub-decide slices of that list
+//              (HUB_SCAN entries each) once every chunk is merged (blocks take
+//              them after their own items), the last slice of each hub taking
+//              the decision.
 #pragma once
 #include <type_traits>
 
@@ -41,9 +42,9 @@ constexpr int BLK_MAXDEG = 1024;
 constexpr int BLK_SLOTS = 2048;     // block role table (deg <= 1024)
 constexpr int HUB_CHUNK = 256;      // adjacency entries per hub-aggregation item
 constexpr int HUB_CHUNK_SLOTS = 512;  // shared table of one hub-aggregation item
-constexpr int HUB_SCAN = 1024;      // hub table slots per hub-decide item
+constexpr int HUB_SCAN = 1024;      // occupied-list entries per hub-decide slice
 constexpr int HUB_LAST = 2048;      // hubs up to this degree: decided by their last aggregation item
-constexpr int SMEM_BYTES = 24576;   // shared table union of every role
+constexpr int SMEM_BYTES = 32768;   // shared memory the roles may use (the phase kernels' dynamic shared memory)
 
 // Degree bins of the schedule: bin b holds degrees in (lim[b-1], lim[b]];
 // degrees above lim[3] are hubs.  The limits are launch-shape options (they
@@ -80,9 +81,9 @@ struct ChunkDesc {             // one aggregation item: a chunk of a hub's adjac
     int32_t nb1, nb2;          // the hub's aggregation items and decide slices
     int32_t relax, pad;        // 1: more than HUB_RELAX neighbours (may share the class with hub neighbours)
 };
-struct SliceDesc {             // one decide slice of a hub table
-    int64_t tab;               // the hub's global table
-    int64_t s0, s1;            // slots of the slice
+struct SliceDesc {             // one decide slice of a hub's occupied-slot list
+    int64_t tab;               // the hub's global table (and list)
+    int64_t s0, s1;            // list entries [s0, s1) of the slice, cut at the list length
     int32_t u, h;              // hub vertex, class-relative hub index
     int32_t nb1, nb2;
     int32_t p0, relax;         // first slice of the hub inside the class; more than HUB_RELAX neighbours
@@ -514,7 +515,7 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
 }
 
 // ---------------------------------------------------------------------------
-// Hub roles (deg > 1024).
+// Hub roles (degree above the block-role limit, bin_max[3] <= 1024).
 // ---------------------------------------------------------------------------
 
 // Takes the decision of hub u from its best candidate (one block; r, C and
@@ -631,11 +632,7 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
     int32_t *gk = c.hub_keys + hi.tab;
     VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
     const uint32_t gmask = (uint32_t)(hi.slots - 1);
-    if (hi.nb2 != 0) {
-        // decided later by slices that scan the whole table
-        for (int s = threadIdx.x; s < HUB_CHUNK_SLOTS; s += kBlock)
-            if (keys[s] >= 0) tab_insert<VT>(gk, gv, gmask, keys[s], vals[s], &c.cnt->overflow);
-    } else {
+    {
         // merge into the hub table; slots created here go to the occupied list
         int32_t fresh[PER];
         int nf = 0;

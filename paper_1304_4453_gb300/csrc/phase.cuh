@@ -17,6 +17,7 @@
 namespace cd {
 
 constexpr int PHASE_SMEM = 32768;          // dynamic shared memory per block
+static_assert(SMEM_BYTES <= PHASE_SMEM, "role tables exceed the phase kernels' shared memory");
 constexpr int RC_SMALL = 4096;             // candidates sorted in shared memory
 // Per-class schedule record (read by one thread per block at class start).
 struct ClassMeta {
@@ -45,7 +46,7 @@ struct PhaseArgs {
     unsigned int *hub_nocc;                // per hub
     int32_t *dz_u, *dz_l;                  // deferred hub label writes of the current class
     unsigned int *dz_n;                    //   and their count (0 between classes)
-    int32_t *hub_acc;                      // re-check scratch: hubs accepted in the current class
+    int32_t *cstamp;                       // re-check: per community, last class step a hub moved it (0: never)
     int32_t *hub_keys;
     void *hub_vals, *hub_wc;
     unsigned int *done1, *done2;
@@ -143,7 +144,9 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
     }
     int32_t *gk = c.hub_keys + hi.tab;
     VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
-    const int64_t s0 = hi.s0, s1 = hi.s1;
+    const int32_t *occ = c.hub_occ + hi.tab;
+    const int64_t nocc = (int64_t)__ldcg(c.hub_nocc + h);
+    const int64_t s0 = hi.s0, s1 = min(hi.s1, nocc);
     const int32_t C = c.zeta[u];
     VT *hwc = static_cast<VT *>(c.hub_wc) + h;
     if (threadIdx.x == 0) *s_cand = 0;
@@ -154,28 +157,26 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
     if constexpr (!PLP) {
         using T = typename GainT<BIG>::T;
         const int64_t vu = c.g.vol[u], twoW = 2 * c.g.W;
-        for (int64_t s = s0 + threadIdx.x; s < s1; s += kBlock) {
-            const int32_t key = gk[s];
-            if (key >= 0) {
-                ncand++;
-                const int64_t w = (int64_t)gv[s];
-                if (key != C) b.offer((T)twoW * (T)w - (T)vu * (T)c.volc[key], key, w);
-                else { *hwc = (VT)w; __threadfence(); }
-                gk[s] = -1;
-                gv[s] = 0;
-            }
+        for (int64_t i = s0 + threadIdx.x; i < s1; i += kBlock) {
+            const int32_t s = __ldcg(occ + i);
+            const int32_t key = __ldcg(gk + s);
+            ncand++;
+            const int64_t w = (int64_t)__ldcg(gv + s);
+            if (key != C) b.offer((T)twoW * (T)w - (T)vu * (T)c.volc[key], key, w);
+            else { *hwc = (VT)w; __threadfence(); }
+            gk[s] = -1;
+            gv[s] = 0;
         }
     } else {
-        for (int64_t s = s0 + threadIdx.x; s < s1; s += kBlock) {
-            const int32_t key = gk[s];
-            if (key >= 0) {
-                ncand++;
-                const int64_t w = (int64_t)gv[s];
-                b.offer(w, fmix32((uint32_t)key ^ c.tie_salt), key);
-                if (key == C) { *hwc = (VT)w; __threadfence(); }
-                gk[s] = -1;
-                gv[s] = 0;
-            }
+        for (int64_t i = s0 + threadIdx.x; i < s1; i += kBlock) {
+            const int32_t s = __ldcg(occ + i);
+            const int32_t key = __ldcg(gk + s);
+            ncand++;
+            const int64_t w = (int64_t)__ldcg(gv + s);
+            b.offer(w, fmix32((uint32_t)key ^ c.tie_salt), key);
+            if (key == C) { *hwc = (VT)w; __threadfence(); }
+            gk[s] = -1;
+            gv[s] = 0;
         }
     }
     ncand = __reduce_add_sync(0xffffffffu, ncand);
@@ -237,6 +238,7 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
     if (threadIdx.x == 0) {
         c.hub_done2[h] = 0;
         c.hub_done1[h] = 0;
+        c.hub_nocc[h] = 0;
         *hwc = 0;
     }
     hub_finish<BIG, PLP>(c, u, C, wC, b, s_last, hi.relax != 0);
@@ -292,23 +294,11 @@ struct RecheckArgs {
     uint64_t *tmp_a, *tmp_b;   // class-sized scratch for long candidate lists
     int ubits;                 // bits of the largest vertex id
     Counters *cnt;
-    const int64_t *rp;         // adjacency (sorted rows), for the hub rule
-    const int32_t *col;
-    int32_t *hub_acc;          // hubs accepted so far in this class
+    const int64_t *rp;         // row offsets (hub test)
+    int32_t *cstamp;           // cstamp[X] == step: a hub of this class moved into or out of X
+    int32_t step;              // id of this class step (> 0)
 };
 
-// True when sorted row of `a` contains b (binary search on the shorter row).
-__device__ __forceinline__ bool adjacent(const int64_t *rp, const int32_t *col, int32_t a, int32_t b) {
-    if (rp[a + 1] - rp[a] > rp[b + 1] - rp[b]) { const int32_t t = a; a = b; b = t; }
-    int64_t lo = rp[a], hi = rp[a + 1];
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        const int32_t x = col[mid];
-        if (x == b) return true;
-        if (x < b) lo = mid + 1; else hi = mid;
-    }
-    return false;
-}
 
 __device__ __forceinline__ void rc_radix_pass(const uint64_t *in, uint64_t *out, int64_t m, int shift,
                                               unsigned char *smem) {
@@ -393,7 +383,6 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
     }
     if (tid < 32) {
         unsigned long long moved = 0;
-        int nacc = 0;   // hubs accepted so far in this class (hub_acc[0, nacc))
         for (int64_t w0 = 0; w0 < m; w0 += 32) {
             const int64_t i = w0 + lane;
             const bool valid = i < m;
@@ -412,10 +401,9 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
                 int acc = 0;
                 if (lane == k) {
                     acc = plm_gain<BIG>(a.twoW, wD, wC, vu, volD, volC) > 0;
-                    // a hub next to a hub moved earlier in this class waits:
-                    // its omega(u, .) would be out of date
-                    for (int j = 0; acc && hub && j < nacc; j++)
-                        if (adjacent(a.rp, a.col, u, a.hub_acc[j])) acc = 0;
+                    // a hub whose omega(u, C) or omega(u, D) a hub moved
+                    // earlier in this class may have changed waits
+                    if (acc && hub && (__ldcg(a.cstamp + C) == a.step || __ldcg(a.cstamp + D) == a.step)) acc = 0;
                 }
                 acc = __shfl_sync(0xffffffffu, acc, k);
                 if (acc) {
@@ -428,8 +416,10 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
                         if (D == Ck) volD -= vk; else if (D == Dk) volD += vk;
                     }
                     if (__shfl_sync(0xffffffffu, (int)hub, k)) {
-                        if (lane == k) a.hub_acc[nacc] = u;
-                        nacc++;
+                        if (lane == k) {
+                            a.cstamp[C] = a.step;
+                            a.cstamp[D] = a.step;
+                        }
                         __syncwarp();
                     }
                 }
@@ -587,7 +577,7 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
                         const uint64_t r0 = a.stage_ns ? global_ns() : 0;
                         RecheckArgs ra{c.cand_u, c.cand_c, c.cand_d, c.cand_wd, c.cand_wc, c.ncand, a.zeta,
                                        a.g.vol, c.volw, 2 * a.g.W, a.tmp_a, a.tmp_b, a.ubits, c.cnt,
-                                       a.g.rp, a.g.col, a.hub_acc};
+                                       a.g.rp, a.cstamp, sw * a.ncol + k + 1};
                         recheck_block<BIG>(ra, sh.smem);
                         if (a.stage_ns && threadIdx.x == 0) atomicAdd(a.stage_ns + 2, global_ns() - r0);
                     }

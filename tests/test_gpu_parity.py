@@ -299,12 +299,13 @@ def test_sweep_cap_returns_notconv_with_valid_labels(O):
     assert np.array_equal(_np_labels(r.labels), o.labels)
 
 
-@pytest.mark.parametrize("nh,leaves,seed", [(5, 1100, 1), (4, 1030, 3), (12, 1500, 5)])
+@pytest.mark.parametrize("nh,leaves,seed", [(5, 4200, 1), (4, 4100, 3), (8, 4500, 5)])
 def test_adjacent_hubs_share_classes(O, nh, leaves, seed):
-    """Mutually adjacent hubs (more than 1024 neighbours) share colour classes:
+    """Mutually adjacent hubs (more than 4096 neighbours) share colour classes:
     their label writes are deferred to the end of the class and the re-check
-    passes over a hub next to a hub moved earlier in the class.  Everything
-    must still match the oracle exactly, for PLM, PLMR, PLP and EPP."""
+    passes over a hub whose communities a hub moved earlier in the class
+    touched.  Everything must still match the oracle exactly, for PLM, PLMR,
+    PLP and EPP."""
     from tests.test_oracle_pins import _hub_core_graph
     g = _hub_core_graph(nh=nh, leaves=leaves, seed=seed)
     G = gpu_graph(g)

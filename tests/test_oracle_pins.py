@@ -172,8 +172,8 @@ def test_colouring_equals_greedy_in_priority_order(oracle_mod, seed):
         assert col.tolist() == _greedy_in_priority_order(rp, c, seed)
 
 
-def _hub_core_graph(nh=5, leaves=1100, seed=1):
-    """nh mutually adjacent hubs (degree > 1024), each with `leaves` private
+def _hub_core_graph(nh=5, leaves=4200, seed=1):
+    """nh mutually adjacent hubs (degree > 4096), each with `leaves` private
     leaves grouped in 5-cliques, plus random leaf-leaf edges across hubs."""
     rng = np.random.default_rng(seed)
     n = nh + nh * leaves
@@ -193,14 +193,14 @@ def _hub_core_graph(nh=5, leaves=1100, seed=1):
 
 
 def test_colouring_ignores_only_hub_hub_edges(oracle_mod):
-    """Vertices with more than 1024 neighbours (hubs) do not constrain each
+    """Vertices with more than 4096 neighbours (hubs) do not constrain each
     other's colours; every other edge is properly coloured, and the result is
     sequential greedy colouring in priority order on the graph without its
     hub-hub edges."""
     g = _hub_core_graph()
     rp, c, w = csr(g)
     deg = np.diff(rp)
-    hub = deg > 1024
+    hub = deg > 4096
     assert hub.sum() == 5
     for seed in (1, 7):
         k, col = oracle_mod.color(rp, c, w, seed)
@@ -220,10 +220,11 @@ def test_colouring_ignores_only_hub_hub_edges(oracle_mod):
 
 
 def test_hub_core_late_sweeps_never_lower_modularity(oracle_mod):
-    """With adjacent hubs in one class, the re-check passes over a hub next to
-    a hub already moved in the class, so late sweeps still never lower the
-    exact modularity and the phase converges."""
-    g = _hub_core_graph(nh=4, leaves=1030, seed=3)
+    """With adjacent hubs in one class, the re-check passes over a hub whose
+    current or target community a hub moved earlier in the class left or
+    entered, so late sweeps still never lower the exact modularity and the
+    phase converges."""
+    g = _hub_core_graph(nh=4, leaves=4100, seed=3)
     rp, c, w = csr(g)
     ed = exact.edges_of(rp, c, w)
     full, st = oracle_mod.move_phase(rp, c, w, 2)
