@@ -283,7 +283,7 @@ def run_ours(a):
                  "team_quantum": best.team_quantum, "team_min": best.team_min, "bin_max": list(best.bin_max)}
         for o in (opts_plain, opts_prof):
             o.team_quantum, o.team_min = best.team_quantum, best.team_min
-            for i in range(4):
+            for i in range(5):
                 o.bin_max[i] = best.bin_max[i]
 
     def run(h, out, opts):

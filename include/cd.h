@@ -57,7 +57,7 @@ enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1 };
 
 /* Options.  cd_opts_default() fills: seed 1, max_sweeps 256, max_levels 64,
  * max_iters 1000, profile 0, team_quantum 262144, team_min 8,
- * bin_max {4, 16, 128, 1024}.
+ * bin_max {4, 16, 128, 1024, 1024} (the global-table block role is empty).
  *   seed        colouring priorities (Jones-Plassmann) and the PLP tie order
  *               derive from it; EPP base i uses seed+i.
  *   max_sweeps  cap on sweeps of one move phase (Algorithm 2 "repeat").
@@ -73,9 +73,11 @@ enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1 };
  *               change speed only, never results.
  *   bin_max     degree limits of the schedule's vertex roles: degree <=
  *               bin_max[0] -> 4 lanes, <= bin_max[1] -> 8 lanes, <= bin_max[2]
- *               -> a warp, <= bin_max[3] -> a block, above -> multi-block hub
- *               path.  Limits may not exceed 4, 16, 128, 1024 and must not
- *               decrease (0 keeps the default).  Speed only, never results.
+ *               -> a warp, <= bin_max[3] -> a block with a shared-memory
+ *               table, <= bin_max[4] -> a block with a table in global
+ *               memory, above -> multi-block hub path.  Limits may not exceed
+ *               4, 16, 128, 1024, 4096 and must not decrease (0 keeps the
+ *               default).  Speed only, never results.
  * cd_tune picks team_quantum, team_min and bin_max by measurement. */
 typedef struct {
     uint64_t seed;
@@ -86,7 +88,7 @@ typedef struct {
     int64_t team_quantum;
     int32_t team_min;
     int32_t reserved;   /* 0 */
-    int32_t bin_max[4];
+    int32_t bin_max[5];
 } cd_opts;
 
 /* Run statistics (all optional: pass NULL to skip). */

@@ -38,7 +38,7 @@ class cd_opts(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("team_quantum", ctypes.c_int64),
                 ("team_min", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("bin_max", ctypes.c_int32 * 4)]
+                ("bin_max", ctypes.c_int32 * 5)]
 
 
 class cd_stats(ctypes.Structure):

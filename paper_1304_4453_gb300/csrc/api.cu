@@ -69,7 +69,7 @@ void cd_opts_default(cd_opts *o) {
     o->team_quantum = int64_t(1) << 18;
     o->team_min = 8;
     o->reserved = 0;
-    for (int i = 0; i < 4; i++) o->bin_max[i] = BIN_CAP[i];
+    for (int i = 0; i < NLIM; i++) o->bin_max[i] = BIN_DEFAULT[i];
 }
 
 const char *cd_status_str(cd_status s) {

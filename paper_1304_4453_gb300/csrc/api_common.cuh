@@ -43,8 +43,8 @@ inline RunOpts to_run(const cd_opts *o) {
     r.profile = o->profile != 0;
     r.team_quantum = o->team_quantum;
     r.team_min = o->team_min;
-    for (int i = 0; i < 4; i++) {
-        const int32_t v = o->bin_max[i] ? o->bin_max[i] : BIN_CAP[i];
+    for (int i = 0; i < NLIM; i++) {
+        const int32_t v = o->bin_max[i] ? o->bin_max[i] : BIN_DEFAULT[i];
         if (v < 1 || v > BIN_CAP[i] || (i > 0 && v < r.bins.lim[i - 1]))
             raise(CD_EINVAL, "bin_max[%d] = %d outside [bin_max[%d], %d]", i, v, i - 1, BIN_CAP[i]);
         r.bins.lim[i] = v;

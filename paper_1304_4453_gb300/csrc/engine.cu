@@ -154,7 +154,7 @@ static void build_schedule(const GraphView &g, uint64_t seed, const BinLimits &b
     int64_t H = 0;
     for (int32_t k = 0; k < S.ncol; k++) {
         S.hub_start[k] = (int32_t)H;
-        H += S.off[(int64_t)k * NBINS + 5] - S.off[(int64_t)k * NBINS + 4];
+        H += S.off[(int64_t)k * NBINS + 6] - S.off[(int64_t)k * NBINS + 5];   // hub-path bucket
     }
     S.hub_start[S.ncol] = (int32_t)H;
     S.nhubs = H;
@@ -168,7 +168,7 @@ static void build_schedule(const GraphView &g, uint64_t seed, const BinLimits &b
     {
         Pinned pv(H * sizeof(int32_t)), pd(2 * H * sizeof(int64_t));
         for (int32_t k = 0; k < S.ncol; k++) {
-            const int64_t a = S.off[(int64_t)k * NBINS + 4], e = S.off[(int64_t)k * NBINS + 5];
+            const int64_t a = S.off[(int64_t)k * NBINS + 5], e = S.off[(int64_t)k * NBINS + 6];
             if (e > a)
                 CD_CUDA(cudaMemcpyAsync(pv.as<int32_t>() + S.hub_start[k], S.order.p + a, (e - a) * sizeof(int32_t),
                                         cudaMemcpyDeviceToHost, s));
@@ -1043,9 +1043,12 @@ void Engine::launch(std::vector<PhaseRun *> &runs) {
         for (auto &g : groups) {
             const void *kern = g[0]->plp ? plp_batch_kernel(g[0]->wk, g[0]->big) : move_batch_kernel(g[0]->wk, g[0]->big);
             const int G = persistent_grid(kern);
+            ensure_block_tables(G);
             auto is = std::make_unique<Issued>();
             is->plan = plan_launch(g, G);
             LaunchPlan &p = is->plan;
+            p.b.gt_keys = gt_keys_.p;
+            p.b.gt_vals = gt_vals_.p;
             std::vector<PhaseArgs> host(p.order.size());
             for (size_t i = 0; i < p.order.size(); i++) host[i] = p.order[i]->a;
             is->args.alloc(host.size(), s_);
@@ -1100,7 +1103,20 @@ void Engine::launch(std::vector<PhaseRun *> &runs) {
             r->fail_msg = e.msg;
         }
         cudaStreamSynchronize(s_);
+        gt_blocks_ = 0;   // a failed launch may have left entries behind: clear before the next one
     }
+}
+
+// Role-3b tables, GT_SLOTS per block of the largest grid: all keys -1 and
+// values 0, which every use restores.
+void Engine::ensure_block_tables(int blocks) {
+    if (blocks <= gt_blocks_) return;
+    const size_t slots = (size_t)blocks * GT_SLOTS;
+    gt_keys_.alloc(slots, s_);
+    gt_vals_.alloc(slots, s_);
+    CD_CUDA(cudaMemsetAsync(gt_keys_.p, 0xff, slots * sizeof(int32_t), s_));
+    gt_vals_.zero();
+    gt_blocks_ = blocks;
 }
 
 void run_jobs(std::vector<Job *> &jobs, cudaStream_t s, int workers) {

@@ -29,7 +29,7 @@ struct RunOpts {
     bool profile = false;
     int64_t team_quantum = int64_t(1) << 18;   // launch shape (speed only)
     int32_t team_min = 8;
-    BinLimits bins{{4, 16, 128, BLK_MAXDEG}};  // schedule degree bins (speed only)
+    BinLimits bins{{4, 16, 128, BLK_MAXDEG, BLK_MAXDEG}};  // schedule degree bins (speed only)
 };
 
 enum Algo { ALGO_PLP = 0, ALGO_PLM = 1, ALGO_EPP = 2 };
@@ -89,7 +89,11 @@ class Engine {
 
   private:
     void launch(std::vector<PhaseRun *> &runs);
+    void ensure_block_tables(int blocks);
     cudaStream_t s_;
+    DBuf<int32_t> gt_keys_;            // role-3b tables of the launches
+    DBuf<unsigned long long> gt_vals_;
+    int gt_blocks_ = 0;
     std::unique_ptr<WorkerPool> pool_;
     std::vector<Job *> active_;
 };

@@ -21,6 +21,9 @@
 //              slots per group, deg <= DMAX (4, 16, 128);
 //   role 3     one block per vertex, shared table of nextpow2(2 deg) slots,
 //              deg <= 1024;
+//   role 3b    one block per vertex, deg <= 4096, the same with a table in
+//              the block's own slice of global memory (GT_SLOTS slots, left
+//              empty after use, small enough to stay in L2);
 //   role 4     hub aggregation: a chunk of a hub's adjacency is merged in a
 //              shared table, then into the hub's global open-addressing
 //              table, and every slot it fills is appended to the hub's
@@ -37,8 +40,11 @@
 
 namespace cd {
 
-constexpr int NBINS = 5;
+constexpr int NBINS = 6;
 constexpr int BLK_MAXDEG = 1024;
+constexpr int GBLK_MAXDEG = 4096;   // role 3b
+constexpr int GT_SLOTS = 8192;      // role 3b table slots per block
+static_assert(GT_SLOTS >= 2 * GBLK_MAXDEG, "role 3b table must hold twice its largest degree");
 constexpr int BLK_SLOTS = 2048;     // block role table (deg <= 1024)
 constexpr int HUB_CHUNK = 256;      // adjacency entries per hub-aggregation item
 constexpr int HUB_CHUNK_SLOTS = 512;  // shared table of one hub-aggregation item
@@ -47,16 +53,21 @@ constexpr int HUB_LAST = 2048;      // hubs up to this degree: decided by their 
 constexpr int SMEM_BYTES = 32768;   // shared memory the roles may use (the phase kernels' dynamic shared memory)
 
 // Degree bins of the schedule: bin b holds degrees in (lim[b-1], lim[b]];
-// degrees above lim[3] are hubs.  The limits are launch-shape options (they
-// move vertices between roles, never change a result) and may not exceed
-// the roles' capacities 4, 16, 128 and BLK_MAXDEG.
+// degrees above lim[4] take the multi-block hub path.  The limits are
+// launch-shape options (they move vertices between roles, never change a
+// result) and may not exceed the roles' capacities.
+constexpr int NLIM = 5;
 struct BinLimits {
-    int32_t lim[4];
+    int32_t lim[NLIM];
 };
-constexpr int32_t BIN_CAP[4] = {4, 16, 128, BLK_MAXDEG};
+constexpr int32_t BIN_CAP[NLIM] = {4, 16, 128, BLK_MAXDEG, GBLK_MAXDEG};
+// Defaults: role 3b is empty (bin_max[4] == bin_max[3]).  On R-MAT its
+// single-block chain per vertex is longer than the chunked hub path's, and
+// the classes are latency-bound; cd_tune may still choose it.
+constexpr int32_t BIN_DEFAULT[NLIM] = {4, 16, 128, BLK_MAXDEG, BLK_MAXDEG};
 
 __host__ __device__ inline int degree_bin(int64_t d, const BinLimits &b) {
-    return d <= b.lim[0] ? 0 : d <= b.lim[1] ? 1 : d <= b.lim[2] ? 2 : d <= b.lim[3] ? 3 : 4;
+    return d <= b.lim[0] ? 0 : d <= b.lim[1] ? 1 : d <= b.lim[2] ? 2 : d <= b.lim[3] ? 3 : d <= b.lim[4] ? 4 : 5;
 }
 
 struct Counters {              // per sweep / iteration, device
@@ -96,6 +107,8 @@ struct SweepCtx {
     const int32_t *order;      // class vertices, bin by bin
     int64_t off[NBINS + 1];    // bin offsets into `order`
     int32_t bend[NBINS];       // exclusive end block of each role
+    int32_t *gt_keys;          // this block's role-3b table (all -1 between uses)
+    void *gt_vals;             //   values (all 0 between uses)
     Counters *cnt;
     // PLM
     const int64_t *volc;       // volumes at class start (read)
@@ -435,14 +448,16 @@ struct BestOf { using T = PlmBest<BIG>; };
 template <bool BIG>
 struct BestOf<true, BIG> { using T = PlpBest; };
 
-template <int WK, bool BIG, bool PLP>
+// GLOBAL: role 3b (table in the block's global slice: read through L2, and
+// the slots used are emptied again before the block moves on).
+template <int WK, bool BIG, bool PLP, bool GLOBAL>
 __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const int32_t *__restrict__ list,
                                            unsigned char *smem, typename BestOf<PLP, BIG>::T *s_best,
                                            unsigned *s_cand) {
     using VT = ValT<BIG>;
     static_assert(BLK_SLOTS * (4 + sizeof(VT)) <= SMEM_BYTES, "block table too large");
-    int32_t *keys = reinterpret_cast<int32_t *>(smem);
-    VT *vals = reinterpret_cast<VT *>(smem + BLK_SLOTS * 4);
+    int32_t *keys = GLOBAL ? c.gt_keys : reinterpret_cast<int32_t *>(smem);
+    VT *vals = GLOBAL ? static_cast<VT *>(c.gt_vals) : reinterpret_cast<VT *>(smem + BLK_SLOTS * 4);
     const int32_t u = list[rb];
     if constexpr (PLP) {
         if (!c.active[u]) return;   // uniform across the block
@@ -452,7 +467,8 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
     int slots = 64;
     while (slots < 2 * deg) slots <<= 1;
     const uint32_t mask = slots - 1;
-    for (int s = threadIdx.x; s < slots; s += kBlock) { keys[s] = -1; vals[s] = 0; }
+    if constexpr (!GLOBAL)
+        for (int s = threadIdx.x; s < slots; s += kBlock) { keys[s] = -1; vals[s] = 0; }
     if (threadIdx.x == 0) *s_cand = 0;
     __syncthreads();
     for (int k = threadIdx.x; k < deg; k += kBlock) {
@@ -461,18 +477,20 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
     }
     __syncthreads();
     const int32_t C = c.zeta[u];
-    const int64_t wC = (int64_t)tab_lookup<VT>(keys, vals, mask, C);
+    const int64_t wC = GLOBAL ? (int64_t)tab_lookup_cg<VT>(keys, vals, mask, C) : (int64_t)tab_lookup<VT>(keys, vals, mask, C);
+    if constexpr (GLOBAL) __syncthreads();   // every lookup is done before slots are emptied
     unsigned ncand = 0;
     if constexpr (!PLP) {
         const int64_t vu = c.g.vol[u], volC = c.volc[C], twoW = 2 * c.g.W;
         PlmBest<BIG> b;
         b.init();
         for (int s = threadIdx.x; s < slots; s += kBlock) {
-            const int32_t key = keys[s];
+            const int32_t key = GLOBAL ? __ldcg(keys + s) : keys[s];
             if (key >= 0) {
                 ncand++;
-                if (key != C)
-                    b.offer(plm_gain<BIG>(twoW, (int64_t)vals[s], wC, vu, c.volc[key], volC), key, (int64_t)vals[s]);
+                const int64_t w = GLOBAL ? (int64_t)__ldcg(vals + s) : (int64_t)vals[s];
+                if (key != C) b.offer(plm_gain<BIG>(twoW, w, wC, vu, c.volc[key], volC), key, w);
+                if constexpr (GLOBAL) { keys[s] = -1; vals[s] = 0; }
             }
         }
         ncand = __reduce_add_sync(0xffffffffu, ncand);
@@ -491,10 +509,12 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
         PlpBest b;
         b.init();
         for (int s = threadIdx.x; s < slots; s += kBlock) {
-            const int32_t key = keys[s];
+            const int32_t key = GLOBAL ? __ldcg(keys + s) : keys[s];
             if (key >= 0) {
                 ncand++;
-                b.offer((int64_t)vals[s], fmix32((uint32_t)key ^ c.tie_salt), key);
+                const int64_t w = GLOBAL ? (int64_t)__ldcg(vals + s) : (int64_t)vals[s];
+                b.offer(w, fmix32((uint32_t)key ^ c.tie_salt), key);
+                if constexpr (GLOBAL) { keys[s] = -1; vals[s] = 0; }
             }
         }
         ncand = __reduce_add_sync(0xffffffffu, ncand);

@@ -101,12 +101,13 @@ __device__ __forceinline__ int32_t class_ctx(const PhaseArgs &a, int32_t k, Swee
     c.part_id = a.part_id;
     c.part_tk = a.part_tk;
     const int64_t n0 = c.off[1] - c.off[0], n1 = c.off[2] - c.off[1], n2 = c.off[3] - c.off[2];
-    const int64_t n3 = c.off[4] - c.off[3];
+    const int64_t n3 = c.off[4] - c.off[3], n4 = c.off[5] - c.off[4];
     c.bend[0] = (int32_t)((n0 + kBlock / 4 - 1) / (kBlock / 4));
     c.bend[1] = c.bend[0] + (int32_t)((n1 + kBlock / 8 - 1) / (kBlock / 8));
     c.bend[2] = c.bend[1] + (int32_t)((n2 + kBlock / 32 - 1) / (kBlock / 32));
     c.bend[3] = c.bend[2] + (int32_t)n3;
-    c.bend[4] = c.bend[3] + m.nb1;
+    c.bend[4] = c.bend[3] + (int32_t)n4;
+    c.bend[5] = c.bend[4] + m.nb1;
     c.nrelax = m.nrelax;
     c.dz_u = a.dz_u;
     c.dz_l = a.dz_l;
@@ -120,8 +121,9 @@ __device__ __forceinline__ void run_item(const SweepCtx &c, int32_t b, unsigned 
     if (b < c.bend[0]) role_group<4, 4, WK, BIG, PLP>(c, b, c.order + c.off[0], c.off[1] - c.off[0], smem);
     else if (b < c.bend[1]) role_group<8, 16, WK, BIG, PLP>(c, b - c.bend[0], c.order + c.off[1], c.off[2] - c.off[1], smem);
     else if (b < c.bend[2]) role_group<32, 128, WK, BIG, PLP>(c, b - c.bend[1], c.order + c.off[2], c.off[3] - c.off[2], smem);
-    else if (b < c.bend[3]) role_block<WK, BIG, PLP>(c, b - c.bend[2], c.order + c.off[3], smem, s_best, s_cand);
-    else role_hub_aggregate<WK, BIG, PLP>(c, b - c.bend[3], smem, s_best, s_last);
+    else if (b < c.bend[3]) role_block<WK, BIG, PLP, false>(c, b - c.bend[2], c.order + c.off[3], smem, s_best, s_cand);
+    else if (b < c.bend[4]) role_block<WK, BIG, PLP, true>(c, b - c.bend[3], c.order + c.off[4], smem, s_best, s_cand);
+    else role_hub_aggregate<WK, BIG, PLP>(c, b - c.bend[4], smem, s_best, s_last);
 }
 
 // Hub decide: slice `item` of a hub table; the last slice of a hub decides.
@@ -497,7 +499,8 @@ __device__ __forceinline__ bool decide_pool(const Team &tm, const SweepCtx &c, i
 // no vertex wants to move.  Returns false when a barrier failed.
 // ---------------------------------------------------------------------------
 template <int WK, bool BIG>
-__device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockShared<PlmBest<BIG>> &sh) {
+__device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockShared<PlmBest<BIG>> &sh,
+                                int32_t *gt_keys, void *gt_vals) {
     SweepCtx &c = *sh.c;
     int64_t *vb[2] = {a.vol_a, a.vol_b};
     int64_t t = 0;
@@ -522,6 +525,8 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
                 *sh.nb2 = class_ctx(a, k, c);
                 c.g = a.g;
                 c.zeta = a.zeta;
+                c.gt_keys = gt_keys;
+                c.gt_vals = gt_vals;
                 c.cnt = a.cnt + sw;
                 c.late = late;
                 c.rp_n = nullptr;
@@ -559,7 +564,7 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
             const uint64_t t0 = timed ? global_ns() : 0;
             // a block walks several items; the barrier keeps one item's warps
             // out of the shared tables of the next
-            for (int32_t b = tm.rank; b < c.bend[4]; b += tm.size) {
+            for (int32_t b = tm.rank; b < c.bend[5]; b += tm.size) {
                 run_item<WK, BIG, false>(c, b, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
             }
@@ -610,7 +615,8 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
 // theta labels changed.  Returns false when a barrier failed.
 // ---------------------------------------------------------------------------
 template <int WK, bool BIG>
-__device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<PlpBest> &sh) {
+__device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<PlpBest> &sh, int32_t *gt_keys,
+                         void *gt_vals) {
     SweepCtx &c = *sh.c;
     int32_t it = 0;
     unsigned long long updated = (unsigned long long)a.g.n;
@@ -625,13 +631,15 @@ __device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<P
                 *sh.nb2 = class_ctx(a, k, c);
                 c.g = a.g;
                 c.zeta = a.zeta;
+                c.gt_keys = gt_keys;
+                c.gt_vals = gt_vals;
                 c.cnt = a.cnt + it;
                 c.active = a.active;
                 c.tie_salt = salt;
             }
             __syncthreads();
             const int32_t nb2 = *sh.nb2;
-            for (int32_t b = tm.rank; b < c.bend[4]; b += tm.size) {
+            for (int32_t b = tm.rank; b < c.bend[5]; b += tm.size) {
                 run_item<WK, BIG, true>(c, b, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
             }
@@ -670,6 +678,8 @@ struct Tier {
 
 struct BatchArgs {
     const PhaseArgs *graphs;   // device array, tier by tier
+    int32_t *gt_keys;          // role-3b tables: GT_SLOTS per block of the grid (all -1 between uses)
+    unsigned long long *gt_vals;   //   values (all 0 between uses)
     GridBarrier *bars;         // one per team
     unsigned int *queues;      // one per tier: next graph
     int32_t *team_graph;       // current graph of each team
@@ -726,7 +736,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_move_phase_batch(BatchArgs b) {
     Team tm;
     find_team(b, &tier, &team, &tm);
     while (next_graph(b, tier, team, tm, &s_gen, &s_ok, s_args) >= 0)
-        if (!move_phase_body<WK, BIG>(*reinterpret_cast<const PhaseArgs *>(s_args), tm, sh)) return;
+        if (!move_phase_body<WK, BIG>(*reinterpret_cast<const PhaseArgs *>(s_args), tm, sh,
+                                      b.gt_keys + (size_t)blockIdx.x * GT_SLOTS,
+                                      b.gt_vals + (size_t)blockIdx.x * GT_SLOTS)) return;
 }
 
 template <int WK, bool BIG>
@@ -736,7 +748,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_plp_batch(BatchArgs b) {
     Team tm;
     find_team(b, &tier, &team, &tm);
     while (next_graph(b, tier, team, tm, &s_gen, &s_ok, s_args) >= 0)
-        if (!plp_body<WK, BIG>(*reinterpret_cast<const PhaseArgs *>(s_args), tm, sh)) return;
+        if (!plp_body<WK, BIG>(*reinterpret_cast<const PhaseArgs *>(s_args), tm, sh,
+                               b.gt_keys + (size_t)blockIdx.x * GT_SLOTS,
+                               b.gt_vals + (size_t)blockIdx.x * GT_SLOTS)) return;
 }
 
 }  // namespace cd

@@ -55,8 +55,8 @@ extern "C" cd_status cd_tune(cd_graph *const *gs, int count, const cd_task *task
         cd_opts cur;
         cd_opts_default(&cur);
         if (base) cur = *base;
-        for (int i = 0; i < 4; i++)
-            if (cur.bin_max[i] == 0) cur.bin_max[i] = BIN_CAP[i];
+        for (int i = 0; i < NLIM; i++)
+            if (cur.bin_max[i] == 0) cur.bin_max[i] = BIN_DEFAULT[i];
         to_run(&cur);   // validates the base options
         (void)task_spec(v[0]->g.view, task, to_run(&cur), nullptr);   // validates the task
         cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -67,7 +67,7 @@ extern "C" cd_status cd_tune(cd_graph *const *gs, int count, const cd_task *task
         int trials = 1;
         // candidate values, one option at a time
         struct Axis {
-            int which;                      // 0 quantum, 1 team_min, 2..5 bin_max[0..3]
+            int which;                      // 0 quantum, 1 team_min, 2..6 bin_max[0..4]
             std::vector<int64_t> values;
         };
         std::vector<Axis> axes;
@@ -77,6 +77,7 @@ extern "C" cd_status cd_tune(cd_graph *const *gs, int count, const cd_task *task
                                 int64_t(1) << 22}});
             axes.push_back({1, {1, 2, 4, 8, 16, 32}});
         }
+        axes.push_back({6, {1024, 2048, 4096}});
         axes.push_back({5, {256, 512, 1024}});
         axes.push_back({4, {32, 64, 128}});
         axes.push_back({3, {8, 12, 16}});
@@ -96,7 +97,7 @@ extern "C" cd_status cd_tune(cd_graph *const *gs, int count, const cd_task *task
                     if (o.bin_max[b] == (int32_t)val) continue;
                     o.bin_max[b] = (int32_t)val;
                     bool ok = true;
-                    for (int i = 1; i < 4; i++) ok = ok && o.bin_max[i] >= o.bin_max[i - 1];
+                    for (int i = 1; i < NLIM; i++) ok = ok && o.bin_max[i] >= o.bin_max[i - 1];
                     if (!ok) continue;
                 }
                 const double ms = timed_run(v, task, o, s, workers);

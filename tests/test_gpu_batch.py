@@ -239,11 +239,13 @@ def test_server_destroy_with_pending_runs():
 # Degree-bin limits and the autotuner (speed-only options)
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("bins", [(4, 4, 4, 4), (1, 2, 3, 4), (2, 8, 32, 256), (4, 16, 128, 1024), (3, 12, 64, 512)])
+@pytest.mark.parametrize("bins", [(4, 4, 4, 4, 4), (1, 2, 3, 4, 5), (2, 8, 32, 256, 1024), (4, 16, 128, 1024, 4096),
+                                  (3, 12, 64, 512, 2048), (4, 16, 16, 16, 4096), (4, 16, 128, 1024, 1024)])
 def test_bin_limits_change_nothing(O, bins):
-    """Moving vertices between the lane-group, block and hub roles leaves
-    every result and counter unchanged (the (4,4,4,4) case sends every vertex
-    above degree 4 down the multi-block hub path)."""
+    """Moving vertices between the lane-group, block, global-table block and
+    hub roles leaves every result and counter unchanged (the (4,4,4,4,4) case
+    sends every vertex above degree 4 down the multi-block hub path, the last
+    one every vertex of degree 17..4096 to the global-table block role)."""
     for g in (GRAPHS[0], GRAPHS[5], GRAPHS[7], GRAPHS[8], GRAPHS[9]):
         G = cd.Graph.from_synth(g, device="cuda")
         for refine in (False, True):
@@ -257,7 +259,8 @@ def test_bin_limits_change_nothing(O, bins):
 
 def test_bin_limits_validated():
     G = cd.Graph.from_synth(GRAPHS[0], device="cuda")
-    for bad in [(5, 16, 128, 1024), (4, 3, 128, 1024), (4, 16, 129, 1024), (4, 16, 128, 2048), (-1, 16, 128, 1024)]:
+    for bad in [(5, 16, 128, 1024), (4, 3, 128, 1024), (4, 16, 129, 1024), (4, 16, 128, 2048),
+                (-1, 16, 128, 1024), (4, 16, 128, 1024, 8192), (4, 16, 128, 1024, 512)]:
         with pytest.raises(cd.CDError) as e:
             G.plm(bin_max=bad)
         assert e.value.status == cd.CD_EINVAL
@@ -272,4 +275,4 @@ def test_tuner_returns_a_shape_with_identical_results():
     for a, b in zip(cd.run_batch(Gs, cd.CD_ALGO_PLM, True, **kw), cd.run_batch(Gs, cd.CD_ALGO_PLM, True, seed=3)):
         _same(a, b)
     best1, _ = cd.cd_tune([Gs[1].h], cd.make_task(cd.CD_ALGO_PLP), None, max_trials=3)
-    assert list(best1.bin_max) != [0, 0, 0, 0]
+    assert 0 not in list(best1.bin_max)
