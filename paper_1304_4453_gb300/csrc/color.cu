@@ -129,6 +129,60 @@ __device__ __forceinline__ void color_warp_items(const int64_t *__restrict__ rp,
     }
 }
 
+// One thread's share of a frontier vertex's adjacency [beg, end), stride
+// `step`: higher-priority neighbours contribute their colour (below NB, into
+// the returned bits, or into the shared bitmap `sbm` when NB > 64), and
+// lower-priority neighbours are released (the last one pushes itself).  Four
+// entries are loaded per step before any is used, so a thread keeps several
+// loads in flight.
+template <int NB>
+__device__ __forceinline__ unsigned long long scan_neighbours(const int64_t *__restrict__ rp,
+                                                              const int32_t *__restrict__ col,
+                                                              const uint32_t *__restrict__ hash, int32_t *wait,
+                                                              int32_t *color, const Frontier &nf, int32_t v,
+                                                              uint32_t hv, bool vh, int64_t beg, int64_t end,
+                                                              int64_t first, int64_t step, uint32_t *sbm) {
+    constexpr int U = 4;
+    unsigned long long bits = 0;
+    for (int64_t e0 = beg + first; e0 < end; e0 += step * U) {
+        int32_t x[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t e = e0 + u * step;
+            ok[u] = e < end;
+            x[u] = ok[u] ? col[e] : 0;
+        }
+        if (vh) {
+#pragma unroll
+            for (int u = 0; u < U; u++) ok[u] = ok[u] && !relaxed_hub(rp, x[u]);
+        }
+        uint32_t hx[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) hx[u] = ok[u] ? hash[x[u]] : 0u;
+        bool hi[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) hi[u] = ok[u] && prio_gt(hx[u], x[u], hv, v);
+        int32_t cx[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) cx[u] = hi[u] ? color[x[u]] : -1;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (hi[u]) {
+                const uint32_t c = (uint32_t)cx[u];
+                if (NB == 64) {
+                    if (c < 64) bits |= 1ull << c;
+                } else if (c < (uint32_t)NB) {
+                    atomicOr(&sbm[c >> 5], 1u << (c & 31));
+                }
+            } else if (ok[u] && atomicSub(&wait[x[u]], 1) == 1) {
+                push_ready(x[u], rp, nf);
+            }
+        }
+    }
+    return bits;
+}
+
 // One block per frontier vertex (COLOR_WARP_DEG < degree <= COLOR_BIG_DEG).
 __device__ __forceinline__ void color_block_items(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                                   const uint32_t *__restrict__ hash, const int32_t *list,
@@ -141,17 +195,9 @@ __device__ __forceinline__ void color_block_items(const int64_t *__restrict__ rp
         const bool vh = end - beg > HUB_RELAX;
         if (threadIdx.x == 0) sbits = 0;
         __syncthreads();
-        unsigned long long bits = 0;
-        for (int64_t e = beg + threadIdx.x; e < end; e += kBlock) {
-            const int32_t x = col[e];
-            if (vh && relaxed_hub(rp, x)) continue;
-            if (prio_gt(hash[x], x, hv, v)) {
-                const uint32_t c = (uint32_t)color[x];
-                if (c < 64) bits |= 1ull << c;
-            } else if (atomicSub(&wait[x], 1) == 1) {
-                push_ready(x, rp, nf);
-            }
-        }
+        const unsigned long long bits0 = scan_neighbours<64>(rp, col, hash, wait, color, nf, v, hv, vh, beg, end,
+                                                              threadIdx.x, kBlock, nullptr);
+        unsigned long long bits = bits0;
         for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
         if ((threadIdx.x & 31) == 0) atomicOr(&sbits, bits);
         __syncthreads();
@@ -214,16 +260,8 @@ __device__ __forceinline__ void color_hub_items(const int64_t *__restrict__ rp, 
             for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock) sbm[w] = 0;
             __syncthreads();
             const int64_t cb = beg + j * COLOR_CHUNK, ce = min(end, cb + COLOR_CHUNK);
-            for (int64_t e = cb + threadIdx.x; e < ce; e += kBlock) {
-                const int32_t x = col[e];
-                if (relaxed_hub(rp, x)) continue;   // degree > 4096: v is a hub
-                if (prio_gt(hash[x], x, hv, v)) {
-                    const uint32_t c = (uint32_t)color[x];
-                    if (c < COLOR_BITS) atomicOr(&sbm[c >> 5], 1u << (c & 31));
-                } else if (atomicSub(&wait[x], 1) == 1) {
-                    push_ready(x, rp, nf);
-                }
-            }
+            // degree > 4096: v is a hub
+            scan_neighbours<COLOR_BITS>(rp, col, hash, wait, color, nf, v, hv, true, cb, ce, threadIdx.x, kBlock, sbm);
             __syncthreads();
             for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock)
                 if (sbm[w]) atomicOr(&bm[w], sbm[w]);
