@@ -362,14 +362,21 @@ __device__ __forceinline__ void role_group(const SweepCtx &c, int64_t rb, const 
         beg = c.g.rp[u];
         deg = (int)(c.g.rp[u + 1] - beg);
     }
+    // neighbour ids, then their labels, then the inserts: every load of a
+    // lane is in flight before the first one is used
+    constexpr int PER = DMAX / G;
+    int32_t nb[PER];
 #pragma unroll
-    for (int k = gl; k < DMAX; k += G) {
-        if (valid && k < deg) {
-            const int32_t v = c.g.col[beg + k];
-            const VT w = (VT)edge_weight<WK>(c.g.w, beg + k);
-            tab_insert<VT>(keys, vals, SLOTS - 1, c.zeta[v], w, &c.cnt->overflow);
-        }
+    for (int j = 0; j < PER; j++) {
+        const int k = gl + j * G;
+        nb[j] = (valid && k < deg) ? c.g.col[beg + k] : -1;
     }
+#pragma unroll
+    for (int j = 0; j < PER; j++) nb[j] = nb[j] >= 0 ? c.zeta[nb[j]] : -1;
+#pragma unroll
+    for (int j = 0; j < PER; j++)
+        if (nb[j] >= 0)
+            tab_insert<VT>(keys, vals, SLOTS - 1, nb[j], (VT)edge_weight<WK>(c.g.w, beg + gl + j * G), &c.cnt->overflow);
     __syncwarp();
     const int32_t C = valid ? c.zeta[u] : 0;
     const int64_t wC = valid ? (int64_t)tab_lookup<VT>(keys, vals, SLOTS - 1, C) : 0;
@@ -380,15 +387,24 @@ __device__ __forceinline__ void role_group(const SweepCtx &c, int64_t rb, const 
         const int64_t twoW = 2 * c.g.W;
         PlmBest<BIG> b;
         b.init();
+        // keys, then the volumes of the candidates, then the gains
+        constexpr int SPL = SLOTS / G;
+        int32_t ky[SPL];
+        int64_t vk[SPL];
 #pragma unroll
-        for (int s = gl; s < SLOTS; s += G) {
-            const int32_t key = keys[s];
-            if (valid && key >= 0) {
-                ncand++;
-                if (key != C)
-                    b.offer(plm_gain<BIG>(twoW, (int64_t)vals[s], wC, vu, c.volc[key], volC), key, (int64_t)vals[s]);
-            }
+        for (int j = 0; j < SPL; j++) {
+            const int32_t key = valid ? keys[gl + j * G] : -1;
+            ky[j] = key;
+            ncand += key >= 0;
         }
+#pragma unroll
+        for (int j = 0; j < SPL; j++) vk[j] = (ky[j] >= 0 && ky[j] != C) ? c.volc[ky[j]] : 0;
+#pragma unroll
+        for (int j = 0; j < SPL; j++)
+            if (ky[j] >= 0 && ky[j] != C) {
+                const int64_t w = (int64_t)vals[gl + j * G];
+                b.offer(plm_gain<BIG>(twoW, w, wC, vu, vk[j], volC), ky[j], w);
+            }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) b.merge(b.shfl_xor(gmask, o));
         const bool want = gl == 0 && valid && b.id >= 0 && b.g > 0;
@@ -471,9 +487,18 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
         for (int s = threadIdx.x; s < slots; s += kBlock) { keys[s] = -1; vals[s] = 0; }
     if (threadIdx.x == 0) *s_cand = 0;
     __syncthreads();
-    for (int k = threadIdx.x; k < deg; k += kBlock) {
-        const int32_t v = c.g.col[beg + k];
-        tab_insert<VT>(keys, vals, mask, c.zeta[v], (VT)edge_weight<WK>(c.g.w, beg + k), &c.cnt->overflow);
+    // four entries per thread and step: ids, then labels, then inserts
+    for (int k0 = threadIdx.x; k0 < deg; k0 += 4 * kBlock) {
+        int32_t nb[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) nb[j] = k0 + j * kBlock < deg ? c.g.col[beg + k0 + j * kBlock] : -1;
+#pragma unroll
+        for (int j = 0; j < 4; j++) nb[j] = nb[j] >= 0 ? c.zeta[nb[j]] : -1;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (nb[j] >= 0)
+                tab_insert<VT>(keys, vals, mask, nb[j], (VT)edge_weight<WK>(c.g.w, beg + k0 + j * kBlock),
+                               &c.cnt->overflow);
     }
     __syncthreads();
     const int32_t C = c.zeta[u];
@@ -484,13 +509,26 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
         const int64_t vu = c.g.vol[u], volC = c.volc[C], twoW = 2 * c.g.W;
         PlmBest<BIG> b;
         b.init();
-        for (int s = threadIdx.x; s < slots; s += kBlock) {
-            const int32_t key = GLOBAL ? __ldcg(keys + s) : keys[s];
-            if (key >= 0) {
-                ncand++;
-                const int64_t w = GLOBAL ? (int64_t)__ldcg(vals + s) : (int64_t)vals[s];
-                if (key != C) b.offer(plm_gain<BIG>(twoW, w, wC, vu, c.volc[key], volC), key, w);
-                if constexpr (GLOBAL) { keys[s] = -1; vals[s] = 0; }
+        // four slots per thread and step: keys, then candidate volumes, then gains
+        for (int s0 = threadIdx.x; s0 < slots; s0 += 4 * kBlock) {
+            int32_t ky[4];
+            int64_t vk[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int s = s0 + j * kBlock;
+                ky[j] = s < slots ? (GLOBAL ? __ldcg(keys + s) : keys[s]) : -1;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) vk[j] = (ky[j] >= 0 && ky[j] != C) ? c.volc[ky[j]] : 0;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int s = s0 + j * kBlock;
+                if (ky[j] >= 0) {
+                    ncand++;
+                    const int64_t w = GLOBAL ? (int64_t)__ldcg(vals + s) : (int64_t)vals[s];
+                    if (ky[j] != C) b.offer(plm_gain<BIG>(twoW, w, wC, vu, vk[j], volC), ky[j], w);
+                    if constexpr (GLOBAL) { keys[s] = -1; vals[s] = 0; }
+                }
             }
         }
         ncand = __reduce_add_sync(0xffffffffu, ncand);

@@ -159,15 +159,29 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
     if constexpr (!PLP) {
         using T = typename GainT<BIG>::T;
         const int64_t vu = c.g.vol[u], twoW = 2 * c.g.W;
-        for (int64_t i = s0 + threadIdx.x; i < s1; i += kBlock) {
-            const int32_t s = __ldcg(occ + i);
-            const int32_t key = __ldcg(gk + s);
-            ncand++;
-            const int64_t w = (int64_t)__ldcg(gv + s);
-            if (key != C) b.offer((T)twoW * (T)w - (T)vu * (T)c.volc[key], key, w);
-            else { *hwc = (VT)w; __threadfence(); }
-            gk[s] = -1;
-            gv[s] = 0;
+        // four occupied slots per thread and step: slot numbers, then keys and
+        // weights, then candidate volumes, then gains
+        for (int64_t i0 = s0 + threadIdx.x; i0 < s1; i0 += 4 * kBlock) {
+            int32_t sl[4], ky[4];
+            int64_t wv[4], vk[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) sl[j] = i0 + j * kBlock < s1 ? __ldcg(occ + i0 + j * kBlock) : -1;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                ky[j] = sl[j] >= 0 ? __ldcg(gk + sl[j]) : -1;
+                wv[j] = sl[j] >= 0 ? (int64_t)__ldcg(gv + sl[j]) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) vk[j] = (sl[j] >= 0 && ky[j] != C) ? c.volc[ky[j]] : 0;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (sl[j] < 0) continue;
+                ncand++;
+                if (ky[j] != C) b.offer((T)twoW * (T)wv[j] - (T)vu * (T)vk[j], ky[j], wv[j]);
+                else { *hwc = (VT)wv[j]; __threadfence(); }
+                gk[sl[j]] = -1;
+                gv[sl[j]] = 0;
+            }
         }
     } else {
         for (int64_t i = s0 + threadIdx.x; i < s1; i += kBlock) {
