@@ -293,11 +293,11 @@ __device__ __forceinline__ bool wait_hub_ready(const SweepCtx &c, int32_t item, 
 // Sequential re-check of one class's wanted moves, by one block.  The
 // candidates are sorted by vertex id (bitonic sort in shared memory, or a
 // block-wide LSD radix sort in global scratch for long lists); then warp 0
-// walks them in windows of 32: lane k recomputes its gain with the volumes
-// of its source and target as updated by every move accepted before it, and
-// every later lane of the window adjusts its copies of the volumes it shares
-// with an accepted move.  Accepted moves update zeta and the volumes before
-// the next window loads its volumes.
+// walks them in windows of 32, accepting in each round the lowest lane whose
+// gain, on the volumes as updated by every move accepted before it, is
+// positive; the later lanes of the window adjust their copies of the volumes
+// they share with an accepted move.  Accepted moves update zeta and the
+// volumes before the next window loads its volumes.
 // ---------------------------------------------------------------------------
 struct RecheckArgs {
     const int32_t *cu, *cc, *cd;
@@ -326,6 +326,7 @@ __device__ __forceinline__ void rc_radix_pass(const uint64_t *in, uint64_t *out,
     if (tid < 256) hist[tid] = 0;
     for (int j = tid; j < NW * 256; j += kBlock) wcnt[j] = 0;
     __syncthreads();
+#pragma unroll 4
     for (int64_t i = tid; i < m; i += kBlock) atomicAdd(&hist[(uint32_t)(in[i] >> shift) & 255u], 1u);
     __syncthreads();
     if (tid == 0) {
@@ -333,10 +334,13 @@ __device__ __forceinline__ void rc_radix_pass(const uint64_t *in, uint64_t *out,
         for (int d = 0; d < 256; d++) { base[d] = run; run += hist[d]; }
     }
     __syncthreads();
+    // the next round's key is loaded before this round's barriers
+    uint64_t knext = tid < m ? in[tid] : 0;
     for (int64_t r = 0; r < m; r += kBlock) {
         const int64_t i = r + tid;
         const bool valid = i < m;
-        const uint64_t k = valid ? in[i] : 0;
+        const uint64_t k = knext;
+        if (i + kBlock < m) knext = in[i + kBlock];
         const uint32_t d = valid ? ((uint32_t)(k >> shift) & 255u) : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
@@ -411,33 +415,38 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
             const int64_t wD = valid ? __ldcg(a.cwd + ci) : 0, wC = valid ? __ldcg(a.cwc + ci) : 0;
             int64_t volC = valid ? __ldcg(a.volc + C) : 0;
             int64_t volD = valid ? __ldcg(a.volc + D) : 0;
+            // a hub whose omega(u, C) or omega(u, D) a hub moved earlier in
+            // this class may have changed waits for the next sweep
+            bool blocked = hub && (__ldcg(a.cstamp + C) == a.step || __ldcg(a.cstamp + D) == a.step);
             bool mine = false;
-            const int cnt = (m - w0) < 32 ? (int)(m - w0) : 32;
-            for (int k = 0; k < cnt; k++) {
-                int acc = 0;
+            // Every undecided lane evaluates its gain with the volumes as
+            // updated by the moves accepted so far.  The lowest accepting lane
+            // is accepted: every lane below it was evaluated on exactly the
+            // state the sequential order gives it and declined, so it is done
+            // too.  Lanes above it fold the accepted move into their volumes
+            // and evaluate again.  A window thus costs one round per accepted
+            // move (plus one), not one per candidate.
+            unsigned pending = __ballot_sync(0xffffffffu, valid);
+            while (pending) {
+                const bool acc = ((pending >> lane) & 1u) && !blocked &&
+                                 plm_gain<BIG>(a.twoW, wD, wC, vu, volD, volC) > 0;
+                const unsigned am = __ballot_sync(0xffffffffu, acc);
+                if (am == 0) break;
+                const int k = __ffs(am) - 1;
+                pending &= ~(0xffffffffu >> (31 - k));   // lanes 0..k are decided
+                const int32_t Ck = __shfl_sync(0xffffffffu, C, k), Dk = __shfl_sync(0xffffffffu, D, k);
+                const int64_t vk = __shfl_sync(0xffffffffu, vu, k);
+                const bool hk = __shfl_sync(0xffffffffu, (int)hub, k) != 0;
                 if (lane == k) {
-                    acc = plm_gain<BIG>(a.twoW, wD, wC, vu, volD, volC) > 0;
-                    // a hub whose omega(u, C) or omega(u, D) a hub moved
-                    // earlier in this class may have changed waits
-                    if (acc && hub && (__ldcg(a.cstamp + C) == a.step || __ldcg(a.cstamp + D) == a.step)) acc = 0;
-                }
-                acc = __shfl_sync(0xffffffffu, acc, k);
-                if (acc) {
-                    const int32_t Ck = __shfl_sync(0xffffffffu, C, k), Dk = __shfl_sync(0xffffffffu, D, k);
-                    const int64_t vk = __shfl_sync(0xffffffffu, vu, k);
-                    if (lane == k) {
-                        mine = true;
-                    } else if (lane > k) {
-                        if (C == Ck) volC -= vk; else if (C == Dk) volC += vk;
-                        if (D == Ck) volD -= vk; else if (D == Dk) volD += vk;
+                    mine = true;
+                    if (hub) {
+                        a.cstamp[C] = a.step;
+                        a.cstamp[D] = a.step;
                     }
-                    if (__shfl_sync(0xffffffffu, (int)hub, k)) {
-                        if (lane == k) {
-                            a.cstamp[C] = a.step;
-                            a.cstamp[D] = a.step;
-                        }
-                        __syncwarp();
-                    }
+                } else if (lane > k) {
+                    if (C == Ck) volC -= vk; else if (C == Dk) volC += vk;
+                    if (D == Ck) volD -= vk; else if (D == Dk) volD += vk;
+                    if (hk && hub && (C == Ck || C == Dk || D == Ck || D == Dk)) blocked = true;
                 }
             }
             if (valid && mine) {
