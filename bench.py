@@ -392,7 +392,7 @@ def run_ours(a):
         "plm": {"levels": st["levels"], "colors0": st["colors0"], "sweeps": st["sweeps"],
                 "communities": st["ncomm"], "ms_color": st["ms_color"], "ms_move": st["ms_move"],
                 "ms_coarsen": st["ms_coarsen"], "ms_total": st["ms_total"], "converged": st["converged"],
-                "move_kernel_stage_ms": {"items": st["stage_items_ms"], "hub_decide": st["stage_hub_ms"],
+                "move_kernel_stage_ms": {"class_steps": st["stage_items_ms"], "recheck_sort": st["stage_sort_ms"],
                                          "recheck": st["stage_recheck_ms"]}},
         "plp": {"edges_per_s": g.m / plp_s, "modularity": plp_mod, "iters": plp_st["iters"],
                 "communities": plp_st["ncomm"]},

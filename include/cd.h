@@ -108,9 +108,9 @@ typedef struct {
     int64_t k_launches;      /* move-phase / PLP kernel launches timed */
     double k_ms;             /* their summed device time */
     double k_bytes;          /* their algorithmic bytes (from the schedule counters) */
-    double stage_items_ms;   /* PLM move kernel: decide items of each class */
-    double stage_hub_ms;     /*   hub decisions */
-    double stage_recheck_ms; /*   sequential re-check of late sweeps */
+    double stage_items_ms;   /* PLM move kernel: whole class steps (profile mode) */
+    double stage_sort_ms;    /*   re-check: sorting the wanted moves by id */
+    double stage_recheck_ms; /*   re-check of late sweeps, sort included */
 } cd_stats;
 
 void cd_opts_default(cd_opts *o);

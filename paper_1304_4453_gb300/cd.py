@@ -51,7 +51,7 @@ class cd_stats(ctypes.Structure):
                 ("ms_coarsen", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("k_launches", ctypes.c_int64), ("k_ms", ctypes.c_double),
                 ("k_bytes", ctypes.c_double), ("stage_items_ms", ctypes.c_double),
-                ("stage_hub_ms", ctypes.c_double), ("stage_recheck_ms", ctypes.c_double)]
+                ("stage_sort_ms", ctypes.c_double), ("stage_recheck_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -72,7 +72,7 @@ inline void to_stats(const RunStats &r, cd_stats *st) {
     st->k_ms = r.k_ms;
     st->k_bytes = r.k_bytes;
     st->stage_items_ms = r.stage_ms[0];
-    st->stage_hub_ms = r.stage_ms[1];
+    st->stage_sort_ms = r.stage_ms[1];
     st->stage_recheck_ms = r.stage_ms[2];
 }
 

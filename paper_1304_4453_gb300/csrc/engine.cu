@@ -307,6 +307,9 @@ struct PhaseRun {
     DBuf<int32_t> mv_u, mv_c, cd_;
     DBuf<int64_t> vol_a, vol_b, cwd, cwc;
     DBuf<uint64_t> tmp_a, tmp_b;
+    DBuf<int32_t> rc_u;               // re-check records in id order
+    DBuf<uint64_t> rc_cd, rc_vu;
+    DBuf<int64_t> rc_dw;
     DBuf<unsigned long long> nmv, ncand;
     DBuf<uint8_t> active;
     DBuf<unsigned long long> sched;   // decide-slice and class-finish counters
@@ -429,6 +432,10 @@ static std::unique_ptr<PhaseRun> prepare_move(const GraphView &g, const Schedule
     r->vol_b.alloc(n, s);
     r->tmp_a.alloc(n, s);
     r->tmp_b.alloc(n, s);
+    r->rc_u.alloc(n, s);
+    r->rc_cd.alloc(n, s);
+    r->rc_vu.alloc(n, s);
+    r->rc_dw.alloc(n, s);
     r->nmv.alloc(2 * ncol + 1, s);
     r->nmv.zero();
     r->ncand.alloc(ncol + 1, s);
@@ -453,6 +460,10 @@ static std::unique_ptr<PhaseRun> prepare_move(const GraphView &g, const Schedule
     a.ncand = r->ncand.p;
     a.tmp_a = r->tmp_a.p;
     a.tmp_b = r->tmp_b.p;
+    a.rc_u = r->rc_u.p;
+    a.rc_cd = r->rc_cd.p;
+    a.rc_vu = r->rc_vu.p;
+    a.rc_dw = r->rc_dw.p;
     int ubits = 1;
     while (((int64_t)1 << ubits) < n) ubits++;
     a.ubits = ubits;

@@ -20,7 +20,7 @@ struct RunStats {
     double ms_color = 0, ms_move = 0, ms_coarsen = 0, ms_total = 0;
     int64_t k_launches = 0;
     double k_ms = 0, k_bytes = 0;
-    double stage_ms[3] = {0, 0, 0};   // move kernel: items, hub decide, re-check (profile mode)
+    double stage_ms[3] = {0, 0, 0};   // move kernel (profile mode): class steps, re-check sort, re-check
 };
 
 struct RunOpts {

@@ -63,6 +63,9 @@ struct PhaseArgs {
     unsigned long long *ncand;             // [ncol]
     uint64_t *tmp_a, *tmp_b;
     int32_t ubits;
+    int32_t *rc_u;
+    uint64_t *rc_cd, *rc_vu;
+    int64_t *rc_dw;
     int32_t max_sweeps, recheck_from;
     // PLP
     uint8_t *active;
@@ -309,10 +312,14 @@ struct RecheckArgs {
     int64_t twoW;
     uint64_t *tmp_a, *tmp_b;   // class-sized scratch for long candidate lists
     int ubits;                 // bits of the largest vertex id
+    int32_t *rc_u;             // class-sized: the candidates' records in id order
+    uint64_t *rc_cd, *rc_vu;   //   (C | D << 32), vol(u) | hub << 63
+    int64_t *rc_dw;            //   omega(u, D) - omega(u, C)
     Counters *cnt;
     const int64_t *rp;         // row offsets (hub test)
     int32_t *cstamp;           // cstamp[X] == step: a hub of this class moved into or out of X
     int32_t step;              // id of this class step (> 0)
+    unsigned long long *stage_ns;   // profile mode: [1] += sort time; else nullptr
 };
 
 
@@ -366,6 +373,7 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
     const int64_t m = (int64_t)__ldcg(a.ncand);
     if (m == 0) return;
     const int tid = threadIdx.x, lane = tid & 31;
+    const uint64_t t_sort = a.stage_ns && tid == 0 ? global_ns() : 0;
     const uint64_t *keys;
     if (m <= RC_SMALL) {
         uint64_t *sk = reinterpret_cast<uint64_t *>(smem);
@@ -401,18 +409,42 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
         __syncthreads();
         keys = src;
     }
+    if (a.stage_ns && tid == 0) atomicAdd(a.stage_ns + 1, global_ns() - t_sort);
+    // the whole block gathers the candidates' records in id order, so that
+    // the walk below reads them contiguously
+#pragma unroll 4
+    for (int64_t i = tid; i < m; i += kBlock) {
+        const uint32_t ci = (uint32_t)(keys[i] & 0xffffffffull);
+        const int32_t u = __ldcg(a.cu + ci);
+        const uint32_t C = (uint32_t)__ldcg(a.cc + ci), D = (uint32_t)__ldcg(a.cd + ci);
+        const bool hub = a.rp[u + 1] - a.rp[u] > HUB_RELAX;
+        a.rc_u[i] = u;
+        a.rc_cd[i] = ((uint64_t)D << 32) | C;
+        a.rc_vu[i] = (uint64_t)a.vol[u] | ((uint64_t)hub << 63);
+        a.rc_dw[i] = __ldcg(a.cwd + ci) - __ldcg(a.cwc + ci);
+    }
+    __syncthreads();
     if (tid < 32) {
         unsigned long long moved = 0;
+        // records are read one window ahead; they never change, only the
+        // volumes and stamps do, and those are read after the previous
+        // window's moves are committed
+        uint64_t n_cd = lane < m ? __ldcg(a.rc_cd + lane) : 0, n_vu = lane < m ? __ldcg(a.rc_vu + lane) : 0;
+        int64_t n_dw = lane < m ? __ldcg(a.rc_dw + lane) : 0;
+        int32_t n_u = lane < m ? __ldcg(a.rc_u + lane) : 0;
         for (int64_t w0 = 0; w0 < m; w0 += 32) {
-            const int64_t i = w0 + lane;
-            const bool valid = i < m;
-            const uint32_t ci = valid ? (uint32_t)(keys[i] & 0xffffffffull) : 0u;
-            const int32_t u = valid ? __ldcg(a.cu + ci) : 0;
-            const int32_t C = valid ? __ldcg(a.cc + ci) : -1;
-            const int32_t D = valid ? __ldcg(a.cd + ci) : -2;
-            const int64_t vu = valid ? a.vol[u] : 0;
-            const bool hub = valid && a.rp[u + 1] - a.rp[u] > HUB_RELAX;
-            const int64_t wD = valid ? __ldcg(a.cwd + ci) : 0, wC = valid ? __ldcg(a.cwc + ci) : 0;
+            const bool valid = w0 + lane < m;
+            const int32_t C = valid ? (int32_t)(uint32_t)n_cd : -1, D = valid ? (int32_t)(n_cd >> 32) : -2;
+            const int64_t vu = (int64_t)(n_vu & ~(1ull << 63)), dw = n_dw;
+            const bool hub = valid && (n_vu >> 63);
+            const int32_t u = n_u;
+            const int64_t j = w0 + 32 + lane;
+            if (j < m) {
+                n_cd = __ldcg(a.rc_cd + j);
+                n_vu = __ldcg(a.rc_vu + j);
+                n_dw = __ldcg(a.rc_dw + j);
+                n_u = __ldcg(a.rc_u + j);
+            }
             int64_t volC = valid ? __ldcg(a.volc + C) : 0;
             int64_t volD = valid ? __ldcg(a.volc + D) : 0;
             // a hub whose omega(u, C) or omega(u, D) a hub moved earlier in
@@ -429,7 +461,7 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
             unsigned pending = __ballot_sync(0xffffffffu, valid);
             while (pending) {
                 const bool acc = ((pending >> lane) & 1u) && !blocked &&
-                                 plm_gain<BIG>(a.twoW, wD, wC, vu, volD, volC) > 0;
+                                 plm_gain<BIG>(a.twoW, dw, 0, vu, volD, volC) > 0;
                 const unsigned am = __ballot_sync(0xffffffffu, acc);
                 if (am == 0) break;
                 const int k = __ffs(am) - 1;
@@ -586,9 +618,11 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
             const bool timed = a.stage_ns && tm.rank == 0 && threadIdx.x == 0;
             const uint64_t t0 = timed ? global_ns() : 0;
             // a block walks several items; the barrier keeps one item's warps
-            // out of the shared tables of the next
+            // out of the shared tables of the next.  Items are taken from the
+            // end: hub chunks first, so that the hubs' decide slices find
+            // their tables complete, then blocks, then the lane groups.
             for (int32_t b = tm.rank; b < c.bend[5]; b += tm.size) {
-                run_item<WK, BIG, false>(c, b, sh.smem, sh.best, sh.cand, sh.last);
+                run_item<WK, BIG, false>(c, c.bend[5] - 1 - b, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
             }
             if (nb2 > 0) {
@@ -604,8 +638,9 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
                     } else if (__ldcg(c.ncand) != 0) {
                         const uint64_t r0 = a.stage_ns ? global_ns() : 0;
                         RecheckArgs ra{c.cand_u, c.cand_c, c.cand_d, c.cand_wd, c.cand_wc, c.ncand, a.zeta,
-                                       a.g.vol, c.volw, 2 * a.g.W, a.tmp_a, a.tmp_b, a.ubits, c.cnt,
-                                       a.g.rp, a.cstamp, sw * a.ncol + k + 1};
+                                       a.g.vol, c.volw, 2 * a.g.W, a.tmp_a, a.tmp_b, a.ubits,
+                                       a.rc_u, a.rc_cd, a.rc_vu, a.rc_dw, c.cnt,
+                                       a.g.rp, a.cstamp, sw * a.ncol + k + 1, a.stage_ns};
                         recheck_block<BIG>(ra, sh.smem);
                         if (a.stage_ns && threadIdx.x == 0) atomicAdd(a.stage_ns + 2, global_ns() - r0);
                     }
@@ -663,7 +698,7 @@ __device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<P
             __syncthreads();
             const int32_t nb2 = *sh.nb2;
             for (int32_t b = tm.rank; b < c.bend[5]; b += tm.size) {
-                run_item<WK, BIG, true>(c, b, sh.smem, sh.best, sh.cand, sh.last);
+                run_item<WK, BIG, true>(c, c.bend[5] - 1 - b, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
             }
             if (nb2 > 0) {

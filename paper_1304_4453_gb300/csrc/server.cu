@@ -37,7 +37,7 @@ struct Entry {
 // level, coarse levels no larger than the input, and the coarsening sort.
 size_t estimate_bytes(const JobSpec &sp) {
     const double n = (double)sp.g.n, nnz = (double)sp.g.nnz;
-    double b = (1 << 20) + 200.0 * n + 32.0 * nnz;
+    double b = (1 << 20) + 230.0 * n + 32.0 * nnz;
     if (sp.algo == ALGO_PLP) b = (1 << 20) + 120.0 * n + 8.0 * nnz;
     if (sp.algo == ALGO_EPP) b += sp.ensemble * 100.0 * n + 48.0 * n;
     return (size_t)b;
