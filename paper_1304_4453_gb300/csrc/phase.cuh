@@ -375,15 +375,50 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
     const int tid = threadIdx.x, lane = tid & 31;
     const uint64_t t_sort = a.stage_ns && tid == 0 ? global_ns() : 0;
     const uint64_t *keys;
-    if (m <= RC_SMALL) {
+    if (m <= 32) {
+        // one warp: bitonic network over the lanes, no block barriers
+        uint64_t *sk = reinterpret_cast<uint64_t *>(smem);
+        if (tid < 32) {
+            uint64_t x = lane < m ? (((uint64_t)(uint32_t)__ldcg(a.cu + lane) << 32) | (uint32_t)lane) : ~0ull;
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const uint64_t y = __shfl_xor_sync(0xffffffffu, x, j);
+                    const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+                    x = keep_min ? (x < y ? x : y) : (x < y ? y : x);
+                }
+            sk[lane] = x;
+        }
+        __syncthreads();
+        keys = sk;
+    } else if (m <= RC_SMALL) {
         uint64_t *sk = reinterpret_cast<uint64_t *>(smem);
         int P = 1;
         while (P < m) P <<= 1;
         for (int i = tid; i < P; i += kBlock)
             sk[i] = i < m ? (((uint64_t)(uint32_t)__ldcg(a.cu + i) << 32) | (uint32_t)i) : ~0ull;
         __syncthreads();
-        for (int k = 2; k <= P; k <<= 1)
-            for (int j = k >> 1; j > 0; j >>= 1) {
+        // bitonic network: stages whose partner is in the same warp (j < 32)
+        // run on registers with shuffles, the others through shared memory
+        const int wbase = tid & ~31;
+        auto warp_stages = [&](int k_lo, int k_hi, int j_top) {
+            for (int i0 = wbase; i0 < P; i0 += kBlock) {   // whole warps: P is a multiple of 64
+                const int i = i0 + lane;
+                uint64_t x = sk[i];
+                for (int k = k_lo; k <= k_hi; k <<= 1)
+                    for (int j = min(k >> 1, j_top); j > 0; j >>= 1) {
+                        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, j);
+                        const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+                        x = keep_min ? (x < y ? x : y) : (x < y ? y : x);
+                    }
+                sk[i] = x;
+            }
+            __syncthreads();
+        };
+        warp_stages(2, 32, 16);
+        for (int k = 64; k <= P; k <<= 1) {
+            for (int j = k >> 1; j >= 32; j >>= 1) {
                 for (int i = tid; i < P; i += kBlock) {
                     const int ixj = i ^ j;
                     if (ixj > i) {
@@ -394,6 +429,8 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
                 }
                 __syncthreads();
             }
+            warp_stages(k, k, 16);
+        }
         keys = sk;
     } else {
         for (int64_t i = tid; i < m; i += kBlock)
