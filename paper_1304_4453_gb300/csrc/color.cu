@@ -15,9 +15,10 @@
 // that reach 0 form the next frontier.  Every adjacency entry is read once to
 // count and once when its row's vertex is coloured (plus a rescan per extra
 // window of 64 colours).  Frontier vertices of degree <= 64 are handled by one
-// warp each, up to 4096 by one block each, and the adjacency of larger ones
-// is cut into chunks spread over all blocks (color_hub_items): a round lasts
-// as long as its slowest vertex.  All rounds run inside one persistent
+// warp each, up to 1024 by one block each, and the adjacency of larger ones
+// is cut into chunks of 1024 entries spread over all blocks
+// (color_chunk_items): a round lasts as long as its slowest vertex, so no
+// thread walks more than a few entries of one vertex.  All rounds run inside one persistent
 // cooperative kernel, separated by a grid barrier; the frontiers rotate over
 // three buffers so that the buffer a round pushes into was cleared a round
 // earlier, and the kernel stops at the first round whose frontier is empty.
@@ -28,24 +29,35 @@
 namespace cd {
 
 constexpr int COLOR_WARP_DEG = 64;     // frontier vertices up to this degree: one warp each
-constexpr int COLOR_BIG_DEG = 4096;    // up to this degree: one block each; above: chunked
-static_assert(COLOR_WARP_DEG <= HUB_RELAX && COLOR_BIG_DEG >= HUB_RELAX,
-              "warp-tier vertices are never hubs; chunked-tier vertices always are");
+constexpr int COLOR_BIG_DEG = 1024;    // up to this degree: one block each; above: chunked
+constexpr int COLOR_CHUNK = 1024;      // adjacency entries per chunk item
+static_assert(COLOR_WARP_DEG <= COLOR_BIG_DEG && COLOR_BIG_DEG <= HUB_RELAX,
+              "warp- and block-tier vertices are never hubs");
 
 __device__ __forceinline__ bool prio_gt(uint32_t hx, int32_t x, uint32_t hv, int32_t v) {
     return hx > hv || (hx == hv && x > v);
 }
 
-// Next-round frontier: three lists by degree (warp / block / chunked).
+// Next-round frontier: vertex lists of the warp and block tiers, and the
+// chunk items (vertex | chunk << 32) of the larger vertices.
 struct Frontier {
-    int32_t *list[3];
-    unsigned long long *count[3];
+    int32_t *list[2];
+    unsigned long long *items;
+    unsigned long long *count[3];   // warp, block, chunk items
 };
+
+__device__ __forceinline__ int64_t colour_chunks(int64_t deg) { return (deg + COLOR_CHUNK - 1) / COLOR_CHUNK; }
 
 __device__ __forceinline__ void push_ready(int32_t x, const int64_t *rp, const Frontier &f) {
     const int64_t d = rp[x + 1] - rp[x];
-    const int t = d <= COLOR_WARP_DEG ? 0 : d <= COLOR_BIG_DEG ? 1 : 2;
-    f.list[t][atomicAdd(f.count[t], 1ull)] = x;
+    if (d <= COLOR_BIG_DEG) {
+        const int t = d <= COLOR_WARP_DEG ? 0 : 1;
+        f.list[t][atomicAdd(f.count[t], 1ull)] = x;
+    } else {
+        const int64_t nch = colour_chunks(d);
+        const unsigned long long b = atomicAdd(f.count[2], (unsigned long long)nch);
+        for (int64_t j = 0; j < nch; j++) f.items[b + j] = (unsigned long long)(uint32_t)x | ((unsigned long long)j << 32);
+    }
 }
 
 // wait[v] and the first frontier; one warp per vertex.
@@ -222,13 +234,13 @@ __device__ __forceinline__ void color_block_items(const int64_t *__restrict__ rp
     }
 }
 
-// Frontier hubs (degree > COLOR_BIG_DEG): each hub's adjacency is cut into
-// chunks of COLOR_CHUNK entries, and the (hub, chunk) items of the round are
-// spread over all blocks.  A chunk ORs the colours (< COLOR_BITS) of its
-// higher-priority neighbours into the hub's bitmap and releases its
-// lower-priority neighbours; the last chunk of a hub takes the first free
-// colour (scanning the adjacency for windows beyond COLOR_BITS if needed).
-constexpr int COLOR_CHUNK = 2048;
+// Frontier vertices above COLOR_BIG_DEG: each one's adjacency is cut into
+// chunks of COLOR_CHUNK entries, queued as (vertex, chunk) items when the
+// vertex was released, and the items of the round are spread over all
+// blocks.  A chunk ORs the colours (< COLOR_BITS) of its higher-priority
+// neighbours into the vertex's bitmap and releases its lower-priority
+// neighbours; the last chunk of a vertex takes the first free colour
+// (scanning the adjacency for windows beyond COLOR_BITS if needed).
 constexpr int COLOR_BITS = 4096;
 constexpr int COLOR_WORDS = COLOR_BITS / 32;
 
@@ -237,73 +249,68 @@ struct HubShared {
     int last;
 };
 
-__device__ __forceinline__ void color_hub_items(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                                const uint32_t *__restrict__ hash, const int32_t *list,
-                                                int64_t count, const int32_t *hub_slot, uint32_t *bitmaps,
-                                                unsigned int *chunks_done, int32_t *wait, int32_t *color,
-                                                const Frontier &nf, unsigned long long *done, HubShared &hs,
-                                                unsigned long long &sbits) {
+__device__ __forceinline__ void color_chunk_items(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                                  const uint32_t *__restrict__ hash, const unsigned long long *items,
+                                                  int64_t count, const int32_t *hub_slot, uint32_t *bitmaps,
+                                                  unsigned int *chunks_done, int32_t *wait, int32_t *color,
+                                                  const Frontier &nf, unsigned long long *done, HubShared &hs,
+                                                  unsigned long long &sbits) {
     uint32_t *sbm = hs.sbm;
     int &s_last = hs.last;
-    int64_t item0 = 0;
-    for (int64_t i = 0; i < count; i++) {
-        const int32_t v = list[i];
+    for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+        const unsigned long long item = items[it];
+        const int32_t v = (int32_t)(item & 0xffffffffull);
+        const int64_t j = (int64_t)(item >> 32);
         const int64_t beg = rp[v], end = rp[v + 1];
-        const int64_t nch = (end - beg + COLOR_CHUNK - 1) / COLOR_CHUNK;
+        const int64_t nch = colour_chunks(end - beg);
+        const bool vh = end - beg > HUB_RELAX;
         const uint32_t hv = hash[v];
         const int32_t slot = hub_slot[v];
         uint32_t *bm = bitmaps + (size_t)slot * COLOR_WORDS;
-        // items item0 .. item0 + nch - 1 belong to this hub
-        int64_t first = item0 + ((blockIdx.x - item0 % gridDim.x) + gridDim.x) % gridDim.x;
-        for (int64_t it = first; it < item0 + nch; it += gridDim.x) {
-            const int64_t j = it - item0;
-            for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock) sbm[w] = 0;
-            __syncthreads();
-            const int64_t cb = beg + j * COLOR_CHUNK, ce = min(end, cb + COLOR_CHUNK);
-            // degree > 4096: v is a hub
-            scan_neighbours<COLOR_BITS>(rp, col, hash, wait, color, nf, v, hv, true, cb, ce, threadIdx.x, kBlock, sbm);
-            __syncthreads();
-            for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock)
-                if (sbm[w]) atomicOr(&bm[w], sbm[w]);
+        for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock) sbm[w] = 0;
+        __syncthreads();
+        const int64_t cb = beg + j * COLOR_CHUNK, ce = min(end, cb + COLOR_CHUNK);
+        scan_neighbours<COLOR_BITS>(rp, col, hash, wait, color, nf, v, hv, vh, cb, ce, threadIdx.x, kBlock, sbm);
+        __syncthreads();
+        for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock)
+            if (sbm[w]) atomicOr(&bm[w], sbm[w]);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(&chunks_done[slot], 1u) == (unsigned)(nch - 1);
+        __syncthreads();
+        if (s_last) {
             __threadfence();
+            // first zero bit of the bitmap
+            if (threadIdx.x == 0) sbits = ~0ull;
             __syncthreads();
-            if (threadIdx.x == 0) s_last = atomicAdd(&chunks_done[slot], 1u) == (unsigned)(nch - 1);
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                // first zero bit of the bitmap
-                if (threadIdx.x == 0) sbits = ~0ull;
-                __syncthreads();
-                for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock) {
-                    const uint32_t word = __ldcg(bm + w);
-                    if (word != 0xffffffffu) atomicMin(&sbits, (unsigned long long)(w * 32 + __ffs(~word) - 1));
-                }
-                __syncthreads();
-                uint32_t c = (uint32_t)sbits;
-                if (sbits == ~0ull) {
-                    // every colour below COLOR_BITS is taken: scan windows of 64 above it
-                    uint32_t base = COLOR_BITS;
-                    while (true) {
-                        __syncthreads();
-                        if (threadIdx.x == 0) sbits = 0;
-                        __syncthreads();
-                        unsigned long long b = window_bits(rp, col, hash, color, v, hv, threadIdx.x, kBlock, base, true);
-                        for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
-                        if ((threadIdx.x & 31) == 0) atomicOr(&sbits, b);
-                        __syncthreads();
-                        const unsigned long long bits = sbits;
-                        if (bits != ~0ull) { c = base + __ffsll((long long)~bits) - 1; break; }
-                        base += 64;
-                    }
-                }
-                if (threadIdx.x == 0) {
-                    color[v] = (int32_t)c;
-                    atomicAdd(done, 1ull);
-                }
+            for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock) {
+                const uint32_t word = __ldcg(bm + w);
+                if (word != 0xffffffffu) atomicMin(&sbits, (unsigned long long)(w * 32 + __ffs(~word) - 1));
             }
             __syncthreads();
+            uint32_t c = (uint32_t)sbits;
+            if (sbits == ~0ull) {
+                // every colour below COLOR_BITS is taken: scan windows of 64 above it
+                uint32_t base = COLOR_BITS;
+                while (true) {
+                    __syncthreads();
+                    if (threadIdx.x == 0) sbits = 0;
+                    __syncthreads();
+                    unsigned long long b = window_bits(rp, col, hash, color, v, hv, threadIdx.x, kBlock, base, vh);
+                    for (int o = 16; o > 0; o >>= 1) b |= __shfl_xor_sync(0xffffffffu, b, o);
+                    if ((threadIdx.x & 31) == 0) atomicOr(&sbits, b);
+                    __syncthreads();
+                    const unsigned long long bits = sbits;
+                    if (bits != ~0ull) { c = base + __ffsll((long long)~bits) - 1; break; }
+                    base += 64;
+                }
+            }
+            if (threadIdx.x == 0) {
+                color[v] = (int32_t)c;
+                atomicAdd(done, 1ull);
+            }
         }
-        item0 += nch;
+        __syncthreads();
     }
 }
 
@@ -326,7 +333,9 @@ struct ColorArgs {
     const uint32_t *hash;
     int64_t n;
     int32_t *wait, *color;
-    int32_t *lists;                // [3 sides][3 tiers][n]
+    int32_t *lists;                // [3 sides][2 tiers][n]
+    unsigned long long *items;     // [3 sides][icap] chunk items
+    int64_t icap;
     unsigned long long *counts;    // [3 sides][3 tiers]
     unsigned long long *done;
     const int32_t *hub_slot;
@@ -339,10 +348,9 @@ struct ColorArgs {
 
 __device__ __forceinline__ Frontier frontier_side(const ColorArgs &a, int side) {
     Frontier f;
-    for (int t = 0; t < 3; t++) {
-        f.list[t] = a.lists + (size_t)(3 * side + t) * a.n;
-        f.count[t] = a.counts + 3 * side + t;
-    }
+    for (int t = 0; t < 2; t++) f.list[t] = a.lists + (size_t)(2 * side + t) * a.n;
+    f.items = a.items + (size_t)side * a.icap;
+    for (int t = 0; t < 3; t++) f.count[t] = a.counts + 3 * side + t;
     return f;
 }
 
@@ -369,8 +377,8 @@ __global__ void __launch_bounds__(kBlock) k_color_persistent(ColorArgs a) {
             color_block_items(a.rp, a.col, a.hash, fc.list[1], (int64_t)s_cnt[1], a.wait, a.color, fn, a.done,
                               sbits);
         if (s_cnt[2])
-            color_hub_items(a.rp, a.col, a.hash, fc.list[2], (int64_t)s_cnt[2], a.hub_slot, a.bitmaps,
-                            a.chunks_done, a.wait, a.color, fn, a.done, hs, sbits);
+            color_chunk_items(a.rp, a.col, a.hash, fc.items, (int64_t)s_cnt[2], a.hub_slot, a.bitmaps,
+                              a.chunks_done, a.wait, a.color, fn, a.done, hs, sbits);
         if (!team_sync(tm, &s_gen, &s_ok)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.rounds = r;
@@ -381,15 +389,18 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     const uint32_t sw = seed_word(seed);
     DBuf<uint32_t> hash(g.n, s);
     DBuf<int32_t> wait(g.n, s);
-    DBuf<int32_t> lists(9 * g.n, s);          // three sides of three tiers
+    // every chunked vertex has more than COLOR_BIG_DEG entries; a frontier holds
+    // at most all of their chunks
+    const int64_t max_hubs = g.nnz / (COLOR_BIG_DEG + 1) + 1;
+    const int64_t icap = g.nnz / COLOR_CHUNK + max_hubs;
+    DBuf<int32_t> lists(6 * g.n, s);          // three sides of two vertex tiers
+    DBuf<unsigned long long> items(3 * icap, s);
     DBuf<unsigned long long> cnt(10, s);      // [side * 3 + tier], [9] coloured
     DBuf<GridBarrier> bar(1, s);
     DBuf<int64_t> rounds(1, s);
     cnt.zero();
     bar.zero();
     rounds.zero();
-    // every chunked hub has more than COLOR_BIG_DEG entries
-    const int64_t max_hubs = g.nnz / (COLOR_BIG_DEG + 1) + 1;
     DBuf<int32_t> hub_slot(g.n, s);
     DBuf<uint32_t> bitmaps((size_t)max_hubs * COLOR_WORDS, s);
     DBuf<unsigned int> chunks_done(max_hubs, s), nhubs(1, s);
@@ -404,6 +415,8 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     a.wait = wait.p;
     a.color = color;
     a.lists = lists.p;
+    a.items = items.p;
+    a.icap = icap;
     a.counts = cnt.p;
     a.done = cnt.p + 9;
     a.hub_slot = hub_slot.p;
@@ -413,10 +426,9 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     a.max_rounds = g.n + 64;   // every round colours at least one vertex
     a.rounds = rounds.p;
     Frontier f0;
-    for (int t = 0; t < 3; t++) {
-        f0.list[t] = lists.p + (size_t)t * g.n;
-        f0.count[t] = cnt.p + t;
-    }
+    for (int t = 0; t < 2; t++) f0.list[t] = lists.p + (size_t)t * g.n;
+    f0.items = items.p;
+    for (int t = 0; t < 3; t++) f0.count[t] = cnt.p + t;
     { k_color_init<<<grid_for(g.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(g.rp, g.col, g.n, sw, hash.p, wait.p, color,
                                                                           f0, hub_slot.p, nhubs.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
