@@ -60,6 +60,42 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+class Ranks:
+    """The processes of one run, one per GPU (torchrun sets RANK / WORLD_SIZE /
+    MASTER_*).  Every rank solves its own replica of the workload: there is no
+    exchange on the data path, so the only collectives are the barriers around
+    the timed region and the reductions of the timing.  With one process every
+    call is local."""
+
+    def __init__(self, world, device=None, backend="nccl"):
+        self.world = world
+        self.device = device
+        if world > 1:
+            import torch.distributed as dist
+            if backend == "nccl":
+                dist.init_process_group(backend, device_id=device)
+            else:
+                dist.init_process_group(backend)
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def rate(self, units, seconds):
+        """Whole-job rate: the units every rank processed over the slowest
+        rank's time.  Returns (rate, slowest seconds)."""
+        if self.world == 1:
+            return units / seconds, seconds
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([seconds], dtype=torch.float64, device=self.device)
+        u = torch.tensor([float(units)], dtype=torch.float64, device=self.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        return float(u) / float(t), float(t)
+
+
 CHUNGLU_N = 16_000_000
 EPP_SCALE, EPP_B = 24, 8
 
@@ -260,9 +296,7 @@ def run_ours(a):
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    ranks = Ranks(world, dev)
     build.build()
     cd.lib()
 
@@ -295,14 +329,9 @@ def run_ours(a):
         mod, st, status = run(G.h, labels, opts_plain)
     torch.cuda.synchronize()
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
-    barrier()
+    ranks.barrier()
     torch.cuda.synchronize()
     l0 = cd.cd_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -318,17 +347,12 @@ def run_ours(a):
         stats.append(st)
     ev1.record(stream)
     torch.cuda.synchronize()
-    barrier()
+    ranks.barrier()
     launches = cd.cd_launch_count() - l0
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / a.steps
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t)
-    value = g.m * world / (ms_max / 1000.0)
+    value, s_max = ranks.rate(g.m, ms / 1000.0)
+    ms_max = 1000.0 * s_max
 
     if a.profile_run:
         if rank == 0:
@@ -354,7 +378,7 @@ def run_ours(a):
         if i > 0:
             e2e_t.append(time.perf_counter() - t)
     e2e_ok = bool(torch.equal(lab_h, labels.cpu()))
-    e2e_value = g.m * world / statistics.median(e2e_t)
+    e2e_value, _ = ranks.rate(g.m, statistics.median(e2e_t))
 
     # one PLP run on the same graph (context, outside the timed region)
     torch.cuda.synchronize()
@@ -440,6 +464,7 @@ def run_batch_workload(a):
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    ranks = Ranks(world, dev)
     build.build()
     cd.lib()
     t0 = time.perf_counter()
@@ -474,6 +499,8 @@ def run_batch_workload(a):
     plain_pass()   # warm-up of the one-call-per-graph path
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
+    ranks.barrier()
+    torch.cuda.synchronize()
     l0 = cd.cd_launch_count()
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -482,15 +509,17 @@ def run_batch_workload(a):
         mods, sts, status = cd.cd_run_batch(handles, task, outs_batch, opts)
     ev1.record(stream)
     torch.cuda.synchronize()
+    ranks.barrier()
     launches = cd.cd_launch_count() - l0
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / a.steps
+    value, s_max = ranks.rate(len(Gs), ms / 1000.0)
+    edges_rate, _ = ranks.rate(m_tot, ms / 1000.0)
     t = time.perf_counter()
     plain_pass()
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t
     same = all(torch.equal(x, y) for x, y in zip(outs_plain, outs_batch))
-    value = len(Gs) / (ms / 1000.0)
     # end to end: host CSR in pinned memory -> handles -> batched run -> labels to host, every step
     host = []
     for G in Gs:
@@ -505,21 +534,22 @@ def run_batch_workload(a):
         cd.cd_graph_destroy(h)
     e2e_s = time.perf_counter() - t
     e2e_same = all(torch.equal(lh, ob.cpu()) for lh, ob in zip(lab_h, outs_batch))
+    e2e_value, _ = ranks.rate(len(Gs), e2e_s)
     h2d = sum(8 * (G.n + 1) + 4 * 2 * G.m for G in Gs)
     if rank != 0:
         return
     line = {
         "metric": BATCH_METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": a.steps,
-        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": a.warmup, "ms_per_step": 1000.0 * s_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": batch_config(len(Gs), n_tot, m_tot),
         "plain": {"graphs_per_s": len(Gs) / plain_s, "s": plain_s,
                   "how": "one cd_plm call per graph, in order, same handles and options"},
         "speedup_vs_plain": (len(Gs) / (ms / 1000.0)) / (len(Gs) / plain_s),
-        "edges_per_s": m_tot / (ms / 1000.0),
+        "edges_per_s": edges_rate,
         "labels_identical_to_plain": same,
         "mean_modularity": sum(mods) / len(mods),
-        "e2e": {"value": len(Gs) / e2e_s, "unit": "graphs/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": e2e_value, "unit": "graphs/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 4 * n_tot, "labels_match_device_run": e2e_same},
         "gpu_launches": launches / a.steps,
         "tuned": tuned,
@@ -580,6 +610,7 @@ def run_serve_workload(a):
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    ranks = Ranks(world, dev)
     build.build()
     cd.lib()
     t0 = time.perf_counter()
@@ -621,6 +652,8 @@ def run_serve_workload(a):
     # continuous-batching server
     S = cd.Server(max_slots=a.serve_slots, max_queue=max(a.serve_requests, 1))
     sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    ranks.barrier()
     l0 = cd.cd_launch_count()
     tickets = []
     base = time.perf_counter()
@@ -643,13 +676,15 @@ def run_serve_workload(a):
     launches = cd.cd_launch_count() - l0
     clocks = sampler.stop()
     S.close()
+    ranks.barrier()
+    nreq = len(arrivals)
+    value, span_max = ranks.rate(nreq, srv_span)
     if rank != 0:
         return
-    nreq = len(arrivals)
     m_req = sum(pool[p].m for p in picks)
     line = {
-        "metric": SERVE_METRIC, "value": nreq / srv_span, "unit": "graphs/s", "n_gpus": world,
-        "steps": 1, "warmup": 1, "ms_per_step": 1000.0 * srv_span, "higher_is_better": True,
+        "metric": SERVE_METRIC, "value": value, "unit": "graphs/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": 1000.0 * span_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"serve{nreq}_poisson{a.serve_rate:g}",
                    "requests": f"first {nreq} requests of a Poisson stream (rate {a.serve_rate:g}/s, seed 7), "
@@ -663,7 +698,7 @@ def run_serve_workload(a):
         "plain_fifo": {"graphs_per_s": nreq / plain_span, "p50_ms": 1000 * pct(lat_plain, 0.5),
                        "p99_ms": 1000 * pct(lat_plain, 0.99)},
         "labels_identical_to_plain": same,
-        "e2e": {"value": nreq / srv_span, "unit": "graphs/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0,
                 "note": "requests reference resident graphs; labels stay on the device"},
         "gpu_launches": launches, "generation_s": gen_s, "clocks": clocks,
