@@ -62,8 +62,8 @@ __device__ __forceinline__ void push_ready(int32_t x, const int64_t *rp, const F
 
 // wait[v] and the first frontier; one warp per vertex.
 __global__ void k_color_init(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, int64_t n, uint32_t s,
-                             uint32_t *hash, int32_t *wait, int32_t *color, Frontier nf, int32_t *hub_slot,
-                             unsigned int *nhubs) {
+                             uint32_t *hash, int32_t *wait, int32_t *color, Frontier nf, int32_t *chunk_slot,
+                             unsigned int *nchunked) {
     const int lane = threadIdx.x & 31;
     int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -82,7 +82,7 @@ __global__ void k_color_init(const int64_t *__restrict__ rp, const int32_t *__re
             hash[v] = hv;
             wait[v] = cnt;
             color[v] = -1;
-            if (end - beg > COLOR_BIG_DEG) hub_slot[v] = (int32_t)atomicAdd(nhubs, 1u);
+            if (end - beg > COLOR_BIG_DEG) chunk_slot[v] = (int32_t)atomicAdd(nchunked, 1u);
             if (cnt == 0) push_ready((int32_t)v, rp, nf);
         }
     }
@@ -244,16 +244,16 @@ __device__ __forceinline__ void color_block_items(const int64_t *__restrict__ rp
 constexpr int COLOR_BITS = 4096;
 constexpr int COLOR_WORDS = COLOR_BITS / 32;
 
-struct HubShared {
+struct ChunkShared {
     uint32_t sbm[COLOR_WORDS];
     int last;
 };
 
 __device__ __forceinline__ void color_chunk_items(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                                   const uint32_t *__restrict__ hash, const unsigned long long *items,
-                                                  int64_t count, const int32_t *hub_slot, uint32_t *bitmaps,
+                                                  int64_t count, const int32_t *chunk_slot, uint32_t *bitmaps,
                                                   unsigned int *chunks_done, int32_t *wait, int32_t *color,
-                                                  const Frontier &nf, unsigned long long *done, HubShared &hs,
+                                                  const Frontier &nf, unsigned long long *done, ChunkShared &hs,
                                                   unsigned long long &sbits) {
     uint32_t *sbm = hs.sbm;
     int &s_last = hs.last;
@@ -265,7 +265,7 @@ __device__ __forceinline__ void color_chunk_items(const int64_t *__restrict__ rp
         const int64_t nch = colour_chunks(end - beg);
         const bool vh = end - beg > HUB_RELAX;
         const uint32_t hv = hash[v];
-        const int32_t slot = hub_slot[v];
+        const int32_t slot = chunk_slot[v];
         uint32_t *bm = bitmaps + (size_t)slot * COLOR_WORDS;
         for (int w = threadIdx.x; w < COLOR_WORDS; w += kBlock) sbm[w] = 0;
         __syncthreads();
@@ -338,7 +338,7 @@ struct ColorArgs {
     int64_t icap;
     unsigned long long *counts;    // [3 sides][3 tiers]
     unsigned long long *done;
-    const int32_t *hub_slot;
+    const int32_t *chunk_slot;
     uint32_t *bitmaps;
     unsigned int *chunks_done;
     GridBarrier *bar;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kBlock) k_color_persistent(ColorArgs a) {
     __shared__ int s_ok;
     __shared__ unsigned long long s_cnt[3];
     __shared__ unsigned long long sbits;
-    __shared__ HubShared hs;
+    __shared__ ChunkShared hs;
     const Team tm{(int32_t)blockIdx.x, (int32_t)gridDim.x, a.bar};
     if (threadIdx.x == 0) s_gen = 0;
     __syncthreads();
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kBlock) k_color_persistent(ColorArgs a) {
             color_block_items(a.rp, a.col, a.hash, fc.list[1], (int64_t)s_cnt[1], a.wait, a.color, fn, a.done,
                               sbits);
         if (s_cnt[2])
-            color_chunk_items(a.rp, a.col, a.hash, fc.items, (int64_t)s_cnt[2], a.hub_slot, a.bitmaps,
+            color_chunk_items(a.rp, a.col, a.hash, fc.items, (int64_t)s_cnt[2], a.chunk_slot, a.bitmaps,
                               a.chunks_done, a.wait, a.color, fn, a.done, hs, sbits);
         if (!team_sync(tm, &s_gen, &s_ok)) return;
     }
@@ -391,8 +391,8 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     DBuf<int32_t> wait(g.n, s);
     // every chunked vertex has more than COLOR_BIG_DEG entries; a frontier holds
     // at most all of their chunks
-    const int64_t max_hubs = g.nnz / (COLOR_BIG_DEG + 1) + 1;
-    const int64_t icap = g.nnz / COLOR_CHUNK + max_hubs;
+    const int64_t max_chunked = g.nnz / (COLOR_BIG_DEG + 1) + 1;
+    const int64_t icap = g.nnz / COLOR_CHUNK + max_chunked;
     DBuf<int32_t> lists(6 * g.n, s);          // three sides of two vertex tiers
     DBuf<unsigned long long> items(3 * icap, s);
     DBuf<unsigned long long> cnt(10, s);      // [side * 3 + tier], [9] coloured
@@ -401,12 +401,12 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     cnt.zero();
     bar.zero();
     rounds.zero();
-    DBuf<int32_t> hub_slot(g.n, s);
-    DBuf<uint32_t> bitmaps((size_t)max_hubs * COLOR_WORDS, s);
-    DBuf<unsigned int> chunks_done(max_hubs, s), nhubs(1, s);
+    DBuf<int32_t> chunk_slot(g.n, s);
+    DBuf<uint32_t> bitmaps((size_t)max_chunked * COLOR_WORDS, s);
+    DBuf<unsigned int> chunks_done(max_chunked, s), nchunked(1, s);
     bitmaps.zero();
     chunks_done.zero();
-    nhubs.zero();
+    nchunked.zero();
     ColorArgs a{};
     a.rp = g.rp;
     a.col = g.col;
@@ -419,7 +419,7 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     a.icap = icap;
     a.counts = cnt.p;
     a.done = cnt.p + 9;
-    a.hub_slot = hub_slot.p;
+    a.chunk_slot = chunk_slot.p;
     a.bitmaps = bitmaps.p;
     a.chunks_done = chunks_done.p;
     a.bar = bar.p;
@@ -430,7 +430,7 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     f0.items = items.p;
     for (int t = 0; t < 3; t++) f0.count[t] = cnt.p + t;
     { k_color_init<<<grid_for(g.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(g.rp, g.col, g.n, sw, hash.p, wait.p, color,
-                                                                          f0, hub_slot.p, nhubs.p); ::cd::note_launch(); }
+                                                                          f0, chunk_slot.p, nchunked.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
     // grid: every block resident (the barrier needs it); small graphs take
     // fewer blocks so that concurrent colourings of a batch fit side by side
