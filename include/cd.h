@@ -298,6 +298,18 @@ uint64_t cd_launch_count(void);
  * (k <= 0 disables).  Used to check that failures leak nothing. */
 void cd_debug_fail_alloc(int k);
 
+/* Testing hook: the batch engine's launch planner (cd_run_batch, Section
+ * III-C's nested parallelism as one launch) on bare phase sizes, on the host
+ * only (no device work, no GPU needed).  work[i] (count >= 1 entries) is the
+ * adjacency entries plus vertices of run i; team_quantum and team_min are the
+ * cd_opts fields of that name; grid_max is the number of resident blocks.
+ * Writes the grid used (<= grid_max), the number of tiers (<= 16), six int32
+ * per tier into tiers[16 * 6] (first block, blocks, team size, index of the
+ * first team, first run in `order`, number of runs), and in order[count] the
+ * runs in tier order.  Errors: CD_EINVAL. */
+cd_status cd_debug_plan_launch(const int64_t *work, int count, int64_t team_quantum, int32_t team_min, int grid_max,
+                               int32_t *grid, int32_t *ntiers, int32_t *tiers, int32_t *order);
+
 #ifdef __cplusplus
 }
 #endif

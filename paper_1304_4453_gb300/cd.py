@@ -74,7 +74,7 @@ SYMBOLS = ["cd_opts_default", "cd_status_str", "cd_last_error", "cd_graph_create
            "cd_epp", "cd_color", "cd_coarsen", "cd_graph_export", "cd_debug_fail_alloc",
            "cd_launch_count", "cd_modularity_static", "cd_run_batch", "cd_plm_batch",
            "cd_server_create", "cd_server_submit", "cd_server_poll", "cd_server_info",
-           "cd_server_destroy", "cd_tune"]
+           "cd_server_destroy", "cd_tune", "cd_debug_plan_launch"]
 
 
 def library_path() -> str:
@@ -106,6 +106,7 @@ def lib():
             L.cd_graph_export.argtypes = [P, P, P, P, c_int, P]
             L.cd_debug_fail_alloc.argtypes = [c_int]
             L.cd_debug_fail_alloc.restype = None
+            L.cd_debug_plan_launch.argtypes = [P, c_int, i64, ctypes.c_int32, c_int, P, P, P, P]
             L.cd_modularity_static.argtypes = [i64, P, P, P, P, P, P]
             L.cd_run_batch.argtypes = [P, c_int, P, P, P, c_int, P, P, P]
             L.cd_plm_batch.argtypes = [P, c_int, c_int, P, P, c_int, P, P]
@@ -269,6 +270,22 @@ def cd_graph_export(h):
 
 def cd_debug_fail_alloc(k: int):
     lib().cd_debug_fail_alloc(int(k))
+
+
+def cd_debug_plan_launch(work, team_quantum: int, team_min: int, grid_max: int):
+    """The batch engine's launch planner on bare phase sizes (host only).
+    Returns (grid, tiers, order): tiers as dicts of begin, blocks, team_size,
+    team0, first, count; order lists the runs in tier order."""
+    w = np.ascontiguousarray(np.asarray(work, dtype=np.int64))
+    grid = ctypes.c_int32()
+    nt = ctypes.c_int32()
+    tiers = np.zeros(16 * 6, np.int32)
+    order = np.zeros(len(w), np.int32)
+    _check(lib().cd_debug_plan_launch(w.ctypes.data, len(w), int(team_quantum), int(team_min), int(grid_max),
+                                      ctypes.byref(grid), ctypes.byref(nt), tiers.ctypes.data, order.ctypes.data),
+           False)
+    keys = ("begin", "blocks", "team_size", "team0", "first", "count")
+    return grid.value, [dict(zip(keys, tiers[6 * i:6 * i + 6].tolist())) for i in range(nt.value)], order.tolist()
 
 
 def cd_modularity_static(row_ptr, col, w, labels, stream=None) -> float:

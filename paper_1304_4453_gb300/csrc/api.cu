@@ -278,6 +278,25 @@ cd_status cd_graph_export(const cd_graph *g, int64_t *row_ptr, int32_t *col, int
 
 void cd_debug_fail_alloc(int k) { set_alloc_failure(k); }
 
+cd_status cd_debug_plan_launch(const int64_t *work, int count, int64_t team_quantum, int32_t team_min, int grid_max,
+                               int32_t *grid, int32_t *ntiers, int32_t *tiers, int32_t *order) {
+    if (!work || !grid || !ntiers || !tiers || !order) return CD_EINVAL;
+    return guarded([&]() {
+        if (count < 1 || team_quantum < 1 || team_min < 1 || grid_max < 1)
+            raise(CD_EINVAL, "count, team_quantum, team_min and grid_max must be >= 1");
+        const PlanView v = plan_for_sizes(std::vector<int64_t>(work, work + count), team_quantum, team_min, grid_max);
+        *grid = v.grid;
+        *ntiers = (int32_t)v.tiers.size();
+        for (size_t i = 0; i < v.tiers.size(); i++) {
+            const PlanTier &t = v.tiers[i];
+            const int32_t row[6] = {t.begin, t.blocks, t.team_size, t.team0, t.first, t.count};
+            for (int k = 0; k < 6; k++) tiers[6 * i + k] = row[k];
+        }
+        for (int i = 0; i < count; i++) order[i] = v.order[i];
+        return CD_OK;
+    });
+}
+
 uint64_t cd_launch_count(void) { return launch_count(); }
 
 }  // extern "C"

@@ -1026,6 +1026,32 @@ static LaunchPlan plan_launch(std::vector<PhaseRun *> runs, int G) {
     return p;
 }
 
+// The planner on bare phase sizes (host only; no device work): one run per
+// entry of `work`, every run with the same launch shape.
+PlanView plan_for_sizes(const std::vector<int64_t> &work, int64_t quantum, int32_t team_min, int grid_max) {
+    std::vector<std::unique_ptr<PhaseRun>> own;
+    std::vector<PhaseRun *> runs;
+    for (int64_t wk : work) {
+        own.push_back(std::make_unique<PhaseRun>());
+        own.back()->work = wk;
+        own.back()->quantum = quantum;
+        own.back()->team_min = team_min;
+        runs.push_back(own.back().get());
+    }
+    const LaunchPlan lp = plan_launch(runs, grid_max);
+    PlanView v;
+    v.grid = lp.grid;
+    v.nteams = lp.nteams;
+    for (int i = 0; i < lp.b.ntiers; i++) {
+        const Tier &t = lp.b.tiers[i];
+        v.tiers.push_back(PlanTier{t.begin, t.blocks, t.team_size, t.team0, t.first, t.count});
+    }
+    for (const PhaseRun *r : lp.order)
+        for (size_t k = 0; k < runs.size(); k++)
+            if (runs[k] == r) v.order.push_back((int32_t)k);
+    return v;
+}
+
 void Engine::launch(std::vector<PhaseRun *> &runs) {
     const auto t = Clock::now();
     // group by kernel instantiation, keeping the order of first appearance

@@ -102,6 +102,21 @@ class Engine {
 // job has stopped.
 void run_jobs(std::vector<Job *> &jobs, cudaStream_t s, int workers);
 
+// The batch engine's launch planner on bare phase sizes (host only): tiers
+// of teams over a grid of at most `grid_max` blocks, and the order in which
+// the runs are placed into the tiers.
+struct PlanTier {
+    int32_t begin, blocks;      // block range [begin, begin + blocks)
+    int32_t team_size, team0;   // blocks per team; index of the tier's first team
+    int32_t first, count;       // runs [first, first + count) of `order`
+};
+struct PlanView {
+    int32_t grid = 0, nteams = 0;
+    std::vector<PlanTier> tiers;
+    std::vector<int32_t> order;
+};
+PlanView plan_for_sizes(const std::vector<int64_t> &work, int64_t quantum, int32_t team_min, int grid_max);
+
 // Single-graph drivers (one job on the caller's thread).  Labels are written
 // to `labels` (device, g.n entries), compacted.
 void run_plm(const GraphView &g, bool refine, const RunOpts &o, int32_t *labels, RunStats &st, cudaStream_t s);
