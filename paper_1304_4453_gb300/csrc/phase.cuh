@@ -294,13 +294,15 @@ __device__ __forceinline__ bool wait_hub_ready(const SweepCtx &c, int32_t item, 
 
 // ---------------------------------------------------------------------------
 // Sequential re-check of one class's wanted moves, by one block.  The
-// candidates are sorted by vertex id (bitonic sort in shared memory, or a
-// block-wide LSD radix sort in global scratch for long lists); then warp 0
-// walks them in windows of 32, accepting in each round the lowest lane whose
-// gain, on the volumes as updated by every move accepted before it, is
-// positive; the later lanes of the window adjust their copies of the volumes
-// they share with an accepted move.  Accepted moves update zeta and the
-// volumes before the next window loads its volumes.
+// candidates are sorted by vertex id (one warp's shuffle network up to 32,
+// a bitonic network in shared memory up to RC_SMALL, else a block-wide LSD
+// radix sort in global scratch), and the whole block gathers their records
+// in that order.  Warp 0 then walks them in windows of 32, accepting in each
+// round the lowest lane whose gain, on the volumes as updated by every move
+// accepted before it, is positive; the later lanes of the window adjust
+// their copies of the volumes they share with an accepted move.  Accepted
+// moves update zeta and the volumes before the next window loads its
+// volumes; the records themselves never change and are read a window ahead.
 // ---------------------------------------------------------------------------
 struct RecheckArgs {
     const int32_t *cu, *cc, *cd;
