@@ -14,7 +14,8 @@
 // the class reads the volumes as they stood when it began (buffer volc) and
 // adds its moves, plus a replay of the previous class's moves, to the other
 // buffer (volw), which then holds the volumes after this class.  Late sweeps
-// record wanted moves as candidates; k_recheck applies them in vertex order.
+// record wanted moves as candidates; the block that finishes the class
+// re-checks them in vertex order (recheck_block in phase.cuh).
 //
 // Work items of a class (the persistent kernels in phase.cuh walk them):
 //   role 0..2  G lanes per vertex (G = 4, 8, 32), shared table of 2*DMAX
@@ -23,7 +24,8 @@
 //              deg <= 1024;
 //   role 3b    one block per vertex, deg <= 4096, the same with a table in
 //              the block's own slice of global memory (GT_SLOTS slots, left
-//              empty after use, small enough to stay in L2);
+//              empty after use, small enough to stay in L2); opt-in through
+//              bin_max[4] > 1024 (the default routes those vertices to role 4);
 //   role 4     hub aggregation: a chunk of a hub's adjacency is merged in a
 //              shared table, then into the hub's global open-addressing
 //              table, and every slot it fills is appended to the hub's
@@ -33,6 +35,9 @@
 //              (HUB_SCAN entries each) once every chunk is merged (blocks take
 //              them after their own items), the last slice of each hub taking
 //              the decision.
+// Blocks take the items hub chunks first, then block items, then lane
+// groups; every role issues several neighbour, label and volume loads per
+// thread before it uses any of them.
 #pragma once
 #include <type_traits>
 
