@@ -34,8 +34,8 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // A team: `size` consecutive blocks of the grid that work on one graph and
-// synchronise through their own barrier.  The single-graph kernels use the
-// whole grid as one team.
+// synchronise through their own barrier.  The colouring kernel, and a batched
+// launch that holds a single graph, use the whole grid as one team.
 struct Team {
     int32_t rank, size;
     GridBarrier *bar;
