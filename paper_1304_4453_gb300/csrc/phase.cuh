@@ -1,11 +1,12 @@
 // Persistent kernels: one cooperative launch runs whole PLM move phases
 // (every sweep, every colour class) or whole PLP runs (every iteration) of
 // one or many graphs.  A team of blocks works on one graph at a time: colour
-// classes follow each other in order, separated by team barriers; inside a
-// class, the team's blocks take work items (group / block / hub roles, then
-// hub-decide slices) in a strided loop.  Late PLM sweeps end each class with
-// the sequential re-check, done by the team's first block between two
-// barriers.
+// classes follow each other in order, one team barrier after each; inside a
+// class, the team's blocks take the work items in a strided loop (hub
+// chunks, block items, lane groups), then the hub-decide slices.  The block
+// that finishes the class last (a finish counter) writes the hubs' deferred
+// labels in early PLM sweeps and runs the sequential re-check in late ones,
+// before the class's barrier.
 //
 // The team barrier is a generation counter; a block that waits longer than
 // BARRIER_TIMEOUT_NS sets an error flag and the team's blocks leave the
