@@ -1,4 +1,5 @@
-// Runtime support: error reporting, the device memory pool, pinned staging.
+// Runtime support: error reporting, the device memory pool, pinned staging,
+// and the residency budget of concurrent persistent kernels.
 #include <atomic>
 #include <condition_variable>
 #include <mutex>
