@@ -43,6 +43,10 @@
  *   - EPP base run i colours with seed+i; the combination is the exact
  *     core-community partition of Eq. (2) (pairwise key compaction), not a
  *     hash.
+ *   - The resolution gamma of Section III-B scales the volume term of the
+ *     move gain; it is a rational p/q (default 1/1, modularity) so that the
+ *     gain stays an exact integer, and the reported quality stays the
+ *     standard modularity.
  *   - Caps: 256 sweeps per move phase, 64 levels, 1000 PLP iterations.
  *   - Modularity of an edgeless graph is 0.
  */
@@ -67,6 +71,8 @@ typedef struct {
     int64_t *loop;  /* [n] self-loop weight omega(u, u) */
     int64_t *vol;   /* [n] vol(u) */
     int64_t W;      /* omega(E): every edge once, self-loops once */
+    int64_t res_num, res_den;   /* resolution gamma = res_num / res_den of the
+                                 * move gain (Sec. III-B); 1/1: modularity */
 } OG;
 
 static void og_free(OG *g)
@@ -94,6 +100,7 @@ static int og_from_input(OG *g, int64_t n, const int64_t *row_ptr,
 {
     memset(g, 0, sizeof(*g));
     g->n = n;
+    g->res_num = g->res_den = 1;
     g->rp = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     g->loop = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     g->vol = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
@@ -304,11 +311,16 @@ static void clear_weights(Scratch *s, int64_t nt)
 
 /* Gain of moving u from C = z[u] to D != C, multiplied by 2W^2 > 0
  * (Section III-B, Delta mod):
- *   g = 2W (omega(u,D) - omega(u,C\u)) - vol(u) (vol(D) - vol(C\u)).     */
-static i128 gain(int64_t W, int64_t w_uD, int64_t w_uC, int64_t vol_u,
+ *   g = 2W (omega(u,D) - omega(u,C\u)) - vol(u) (vol(D) - vol(C\u)).
+ * With a resolution gamma = p/q (Section III-B: gamma scales the volume
+ * term; 0 yields one community per connected component, 1 is modularity,
+ * 2W yields singletons) the gain is multiplied by 2W^2 q instead:
+ *   g = 2W q (omega(u,D) - omega(u,C\u)) - p vol(u) (vol(D) - vol(C\u)). */
+static i128 gain(const OG *g, int64_t w_uD, int64_t w_uC, int64_t vol_u,
                  int64_t vol_D, int64_t vol_C)
 {
-    return (i128)(2 * W) * (w_uD - w_uC) - (i128)vol_u * (vol_D - (vol_C - vol_u));
+    return (i128)g->res_den * (2 * g->W) * (w_uD - w_uC)
+         - (i128)g->res_num * vol_u * (vol_D - (vol_C - vol_u));
 }
 
 /* Best target community for u, or z[u] if no candidate has positive gain. */
@@ -331,7 +343,7 @@ static int32_t decide_move(const OG *g, const int32_t *z, const int64_t *volc,
     for (int64_t i = 0; i < nt; i++) {
         int32_t D = s->touched[i];
         if (D == C) continue;
-        i128 gD = gain(g->W, s->acc[D], w_uC, g->vol[u], volc[D], volc[C]);
+        i128 gD = gain(g, s->acc[D], w_uC, g->vol[u], volc[D], volc[C]);
         if (!have || gD > bestg || (gD == bestg && D < best)) { best = D; bestg = gD; have = 1; }
     }
     st[ST_ENTRIES] += g->rp[u + 1] - g->rp[u];
@@ -421,7 +433,7 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
                      * next sweep */
                     const int uh = is_hub(g, u);
                     if (uh && (stamp[C] == step || stamp[D] == step)) continue;
-                    if (gain(g->W, wprop[u], wcur[u], g->vol[u], volc[D], volc[C]) <= 0) continue;
+                    if (gain(g, wprop[u], wcur[u], g->vol[u], volc[D], volc[C]) <= 0) continue;
                     volc[C] -= g->vol[u];
                     volc[D] += g->vol[u];
                     z[u] = D;
@@ -466,6 +478,8 @@ static void coarsen(const OG *g, const int32_t *z, OG *cg, int32_t *pi)
 
     memset(cg, 0, sizeof(*cg));
     cg->n = nc;
+    cg->res_num = g->res_num;   /* every level optimises the same objective */
+    cg->res_den = g->res_den;
     cg->rp = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
     cg->loop = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
     cg->vol = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
@@ -684,10 +698,13 @@ int or_modularity(int64_t n, const int64_t *rp, const int32_t *col, const int64_
 
 /* gain numerator g (x 2W^2) of moving u from labels[u] to community D */
 int or_gain(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
-            const int32_t *labels, int32_t u, int32_t D, int64_t *g_out)
+            const int32_t *labels, int32_t u, int32_t D, int64_t res_num, int64_t res_den, int64_t *g_out)
 {
     OG g;
+    if (res_num < 0 || res_den < 1) return -2;
     if (og_from_input(&g, n, rp, col, w)) return -1;
+    g.res_num = res_num;
+    g.res_den = res_den;
     int64_t *volc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     for (int64_t x = 0; x < n; x++) volc[labels[x]] += g.vol[x];
     int64_t wD = 0, wC = 0;
@@ -695,7 +712,7 @@ int or_gain(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
         if (labels[g.adj[e]] == D) wD += g.wt[e];
         if (labels[g.adj[e]] == labels[u]) wC += g.wt[e];
     }
-    put128(gain(g.W, wD, wC, g.vol[u], volc[D], volc[labels[u]]), g_out);
+    put128(gain(&g, wD, wC, g.vol[u], volc[D], volc[labels[u]]), g_out);
     free(volc);
     og_free(&g);
     return 0;
@@ -731,10 +748,13 @@ int or_move_phase(int64_t n, const int64_t *rp, const int32_t *col, const int64_
 
 int or_plm(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
            int refine, uint64_t seed, int32_t max_sweeps, int32_t max_levels, int rev,
-           int32_t *labels, double *mod, int64_t *stats)
+           int64_t res_num, int64_t res_den, int32_t *labels, double *mod, int64_t *stats)
 {
     OG g;
+    if (res_num < 0 || res_den < 1) return -2;
     if (og_from_input(&g, n, rp, col, w)) return -1;
+    g.res_num = res_num;
+    g.res_den = res_den;
     int64_t st[ST_N] = {0};
     st[ST_CONVERGED] = 1;
     Opts o = { seed, max_sweeps, max_levels, rev };
@@ -861,7 +881,7 @@ int64_t or_positive_moves(int64_t n, const int64_t *rp, const int32_t *col, cons
         for (int64_t i = 0; i < nt; i++) {
             int32_t D = s.touched[i];
             if (D == C) continue;
-            i128 gD = gain(g.W, s.acc[D], s.acc[C], g.vol[u], volc[D], volc[C]);
+            i128 gD = gain(&g, s.acc[D], s.acc[C], g.vol[u], volc[D], volc[C]);
             if (gD > 0) { cnt++; if (gD > mx) mx = gD; break; }
         }
         clear_weights(&s, nt);

@@ -53,11 +53,11 @@ def lib():
             P = ctypes.c_void_p
             i64, i32, dbl, u64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64
             L.or_modularity.argtypes = [i64, P, P, P, P, P, P]
-            L.or_gain.argtypes = [i64, P, P, P, P, i32, i32, P]
+            L.or_gain.argtypes = [i64, P, P, P, P, i32, i32, i64, i64, P]
             L.or_color.argtypes = [i64, P, P, P, u64, P]
             L.or_color.restype = i32
             L.or_move_phase.argtypes = [i64, P, P, P, u64, i32, ctypes.c_int, P, P]
-            L.or_plm.argtypes = [i64, P, P, P, ctypes.c_int, u64, i32, i32, ctypes.c_int, P, P, P]
+            L.or_plm.argtypes = [i64, P, P, P, ctypes.c_int, u64, i32, i32, ctypes.c_int, i64, i64, P, P, P]
             L.or_plp.argtypes = [i64, P, P, P, u64, dbl, i32, ctypes.c_int, ctypes.c_int, P, P, P]
             L.or_combine.argtypes = [i64, ctypes.c_int, P, P]
             L.or_combine.restype = i64
@@ -124,12 +124,16 @@ def modularity(row_ptr, col, w, labels):
     return out.value, _i128(nd[0], nd[1]), _i128(nd[2], nd[3])
 
 
-def gain(row_ptr, col, w, labels, u, D):
-    """Exact gain numerator g = 2W^2 * Delta mod(u, labels[u] -> D)."""
+def gain(row_ptr, col, w, labels, u, D, resolution=(1, 1)):
+    """Exact gain numerator g = 2W^2 q * Delta Q_gamma(u, labels[u] -> D) for
+    the resolution gamma = p/q given as resolution = (p, q); (1, 1) is
+    modularity, where g = 2W^2 * Delta mod."""
     g = _CSR(row_ptr, col, w)
     z = _np(labels, np.int32)
     out = np.zeros(2, np.int64)
-    lib().or_gain(*g.args(), _ptr(z), int(u), int(D), _ptr(out))
+    p, q = resolution
+    if lib().or_gain(*g.args(), _ptr(z), int(u), int(D), int(p), int(q), _ptr(out)) == -2:
+        raise ValueError("resolution must be p >= 0, q >= 1")
     return _i128(out[0], out[1])
 
 
@@ -149,13 +153,20 @@ def move_phase(row_ptr, col, w, seed, labels=None, max_sweeps=MAX_SWEEPS, rev=Fa
 
 
 def plm(row_ptr, col, w, refine=False, seed=1, max_sweeps=MAX_SWEEPS,
-        max_levels=MAX_LEVELS, rev=False) -> Result:
+        max_levels=MAX_LEVELS, rev=False, resolution=(1, 1)) -> Result:
+    """PLM / PLMR.  resolution = (p, q): the moves maximise the objective with
+    gamma = p/q scaling the volume term (Sec. III-B); the returned modularity
+    is always the standard one (gamma = 1)."""
     g = _CSR(row_ptr, col, w)
     z = np.zeros(max(g.n, 1), np.int32)
     mod = ctypes.c_double()
     st = np.zeros(len(STATS), np.int64)
-    if lib().or_plm(*g.args(), int(refine), seed, max_sweeps, max_levels, int(rev),
-                    _ptr(z), ctypes.byref(mod), _ptr(st)):
+    p, q = resolution
+    rc = lib().or_plm(*g.args(), int(refine), seed, max_sweeps, max_levels, int(rev), int(p), int(q),
+                      _ptr(z), ctypes.byref(mod), _ptr(st))
+    if rc == -2:
+        raise ValueError("resolution must be p >= 0, q >= 1")
+    if rc:
         raise MemoryError
     return Result(z[:g.n], mod.value, _stats(st))
 

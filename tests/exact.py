@@ -21,8 +21,10 @@ def edges_of(row_ptr, col, w):
     return out
 
 
-def modularity_fraction(n, edges, labels):
-    """mod(zeta, G) = sum_C omega(C)/omega(E) - vol(C)^2 / (4 omega(E)^2).
+def modularity_fraction(n, edges, labels, gamma=Fraction(1)):
+    """mod(zeta, G) = sum_C omega(C)/omega(E) - gamma vol(C)^2 / (4 omega(E)^2);
+    gamma = 1 is modularity (Eq. 1), other values the resolution-scaled
+    objective that the gamma parameter of Section III-B optimises.
 
     vol(u): sum of incident non-loop edge weights plus twice the loop weight.
     omega(C): weight of edges with both ends in C, a loop counted once."""
@@ -44,7 +46,7 @@ def modularity_fraction(n, edges, labels):
         ms = set(members)
         inner = sum(wt for (u, v), wt in edges.items() if u in ms and v in ms)
         vc = sum(vol[u] for u in members)
-        q += Fraction(inner, W) - Fraction(vc * vc, 4 * W * W)
+        q += Fraction(inner, W) - gamma * Fraction(vc * vc, 4 * W * W)
     return q
 
 
