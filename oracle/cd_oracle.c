@@ -16,8 +16,9 @@
  * parallel schedule is nondeterministic there):
  *   - vol(u) sums the weights to neighbours other than u plus twice the
  *     self-loop (Section III-B, volume definition; read so that sum vol = 2W).
- *   - Schedule: colour classes of a hash-priority Jones-Plassmann colouring,
- *     processed in ascending colour; inside a class every vertex decides on
+ *   - Schedule: colour classes of a hash-priority Jones-Plassmann colouring
+ *     (computed in one pass as greedy colouring in descending priority
+ *     order, which it equals), processed in ascending colour; inside a class every vertex decides on
  *     the labels and community volumes as they stood when the class began,
  *     then all decisions of the class are applied.  The colouring ignores
  *     edges between two hubs (vertices with more than HUB_RELAX neighbours),
@@ -55,6 +56,31 @@
 #include <string.h>
 
 typedef __int128 i128;
+
+/* Built twice: plain (sequential) and with -fopenmp.  The OpenMP build runs
+ * the decisions of one colour class in parallel, which the schedule makes
+ * independent of each other (every vertex of a class reads only labels and
+ * volumes fixed before the class; Section III-B's parallel loop over the
+ * vertices).  Everything else runs in the same order in both builds, so the
+ * two give identical results. */
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_THREADS() omp_get_max_threads()
+#define OR_TID() omp_get_thread_num()
+#else
+#define OR_THREADS() 1
+#define OR_TID() 0
+#endif
+/* classes with fewer adjacency entries than this are decided by one thread */
+#define OR_PAR_MIN 4096
+
+/* adjacency entries of the vertices v[a..b) (the work of deciding them) */
+#define CLASS_WORK(g, v, a, b, out) do {                                       \
+        int64_t w_ = 0;                                                         \
+        for (int64_t i_ = (a); i_ < (b); i_++)                                  \
+            w_ += (g)->rp[(v)[i_] + 1] - (g)->rp[(v)[i_]];                      \
+        (out) = w_;                                                             \
+    } while (0)
 
 /* Hubs for the colouring: more than HUB_RELAX neighbours (self-loop not
  * counted).  Edges between two hubs do not constrain the colouring. */
@@ -118,6 +144,28 @@ static int og_from_input(OG *g, int64_t n, const int64_t *row_ptr,
         g->rp[u + 1] = k;
     }
     og_volumes(g);
+    return 0;
+}
+
+/* Resolution gamma = p/q of the move gain (Section III-B).  The fraction is
+ * reduced by gcd(p, q), which scales every gain by one positive factor and
+ * so changes no decision.  Both products of the gain are bounded by
+ * max(p, q) (2W)^2 (|omega(u,D) - omega(u,C\u)|, vol(u) and |vol(D) -
+ * vol(C\u)| are at most 2W), so p/q is accepted only when that bound stays
+ * below 2^126 and the gain fits a signed 128-bit integer.  Returns -2 for
+ * p < 0, q < 1 or a fraction outside that range. */
+static int og_set_resolution(OG *g, int64_t p, int64_t q)
+{
+    if (p < 0 || q < 1) return -2;
+    int64_t a = p, b = q;
+    while (b) { int64_t t = a % b; a = b; b = t; }
+    if (a > 1) { p /= a; q /= a; }
+    const i128 w2 = (i128)(2 * g->W) * (2 * g->W);
+    const i128 lim = ((i128)1) << 126;
+    const int64_t big = p > q ? p : q;
+    if (w2 > 0 && (i128)big > (lim - 1) / w2) return -2;
+    g->res_num = p;
+    g->res_den = q;
     return 0;
 }
 
@@ -253,6 +301,56 @@ static int32_t color_jp(const OG *g, uint64_t seed, int32_t *color)
     return ncol;
 }
 
+/* The same colouring in one pass.  A Jones-Plassmann round colours a vertex
+ * exactly when every neighbour of higher priority is coloured and never
+ * before, and first fit looks only at coloured neighbours, so the rounds give
+ * the colouring of the sequential greedy method run in descending priority
+ * order (each vertex takes the smallest colour its already coloured
+ * neighbours leave free; hub-hub edges skipped as above).  This form costs
+ * one sort plus one read of every adjacency entry, against one rescan of
+ * every uncoloured vertex per round for color_jp. */
+static int cmp_u64_desc(const void *a, const void *b)
+{
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x < y) - (x > y);
+}
+
+static int32_t color_greedy(const OG *g, uint64_t seed, int32_t *color)
+{
+    int64_t n = g->n;
+    uint32_t s = fmix32((uint32_t)seed ^ (uint32_t)(seed >> 32));
+    uint64_t *key = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    for (int64_t v = 0; v < n; v++) {
+        key[v] = ((uint64_t)fmix32((uint32_t)v ^ s) << 32) | (uint32_t)v;
+        color[v] = -1;
+    }
+    qsort(key, (size_t)n, sizeof(uint64_t), cmp_u64_desc);
+    char *taken = NULL;
+    int64_t taken_cap = 0;
+    int32_t ncol = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int32_t v = (int32_t)(uint32_t)key[i];
+        int64_t deg = g->rp[v + 1] - g->rp[v];
+        if (deg + 1 > taken_cap) {
+            taken_cap = deg + 1;
+            taken = (char *)realloc(taken, (size_t)taken_cap);
+        }
+        memset(taken, 0, (size_t)deg + 1);
+        const int vh = is_hub(g, v);
+        for (int64_t e = g->rp[v]; e < g->rp[v + 1]; e++) {
+            if (vh && is_hub(g, g->adj[e])) continue;
+            int32_t c = color[g->adj[e]];
+            if (c >= 0 && c <= deg) taken[c] = 1;
+        }
+        int32_t c = 0;
+        while (taken[c]) c++;
+        color[v] = c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(key); free(taken);
+    return ncol;
+}
+
 /* Vertices grouped by colour, ascending id inside a class (or descending
  * when rev != 0: the result must not depend on it). */
 typedef struct { int32_t ncol; int64_t *off; int32_t *v; } Classes;
@@ -261,7 +359,7 @@ static void classes_build(const OG *g, uint64_t seed, int rev, Classes *cl)
 {
     int64_t n = g->n;
     int32_t *color = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
-    cl->ncol = n ? color_jp(g, seed, color) : 0;
+    cl->ncol = n ? color_greedy(g, seed, color) : 0;
     cl->off = (int64_t *)calloc((size_t)cl->ncol + 2, sizeof(int64_t));
     cl->v = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
     for (int64_t u = 0; u < n; u++) cl->off[color[u] + 1]++;
@@ -285,6 +383,10 @@ enum {
     ST_CANDIDATES, ST_DECISIONS, ST_ITERS, ST_NCOMM, ST_SWEEPS0, ST_ENTRIES0,
     ST_CANDIDATES0, ST_N
 };
+
+/* per-thread counter rows of the OpenMP build, padded to 256 bytes so that
+ * two threads never write the same cache line */
+#define ST_PAD 32
 
 /* ---------------------------------------------------------------------- */
 /* Local moving, Algorithm 2, under the colour-class schedule.               */
@@ -391,9 +493,13 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
     int64_t *wprop = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
     int64_t *wcur = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
     int32_t *byid = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
-    Scratch s;
-    s.acc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
-    s.touched = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    const int T = OR_THREADS();
+    Scratch *ts = (Scratch *)calloc((size_t)T, sizeof(Scratch));
+    int64_t (*tst)[ST_PAD] = calloc((size_t)T, sizeof(*tst));  /* per-thread counters */
+    for (int t = 0; t < T; t++) {
+        ts[t].acc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+        ts[t].touched = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    }
     for (int64_t u = 0; u < n; u++) volc[z[u]] += g->vol[u];
     /* stamp[X] = class step in which a hub moved into or out of community X */
     int64_t *stamp = (int64_t *)malloc(((size_t)n + 1) * sizeof(int64_t));
@@ -406,9 +512,14 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
         for (int32_t k = 0; k < cl->ncol; k++) {
             int64_t a = cl->off[k], b = cl->off[k + 1];
             step++;
+            int64_t work;
+            CLASS_WORK(g, cl->v, a, b, work);
+            (void)work;
+            #pragma omp parallel for schedule(dynamic, 16) if (work >= OR_PAR_MIN)
             for (int64_t i = a; i < b; i++) {            /* decide */
                 int32_t u = cl->v[i];
-                prop[u] = decide_move(g, z, volc, u, &s, st, level0, &wprop[u], &wcur[u]);
+                const int t = OR_TID();
+                prop[u] = decide_move(g, z, volc, u, &ts[t], tst[t], level0, &wprop[u], &wcur[u]);
             }
             if (sw < RECHECK_FROM) {
                 for (int64_t i = a; i < b; i++) {        /* apply all */
@@ -449,8 +560,13 @@ static int64_t move_phase(const OG *g, int32_t *z, const Classes *cl, uint64_t s
     }
     if (!converged) st[ST_CONVERGED] = 0;
     st[ST_MOVES] += total;
+    for (int t = 0; t < T; t++) {
+        for (int k = 0; k < ST_N; k++) st[k] += tst[t][k];
+        free(ts[t].acc); free(ts[t].touched);
+    }
+    free(ts); free(tst);
     free(wprop); free(wcur); free(byid); free(stamp);
-    free(volc); free(prop); free(s.acc); free(s.touched);
+    free(volc); free(prop);
     return total;
 }
 
@@ -503,13 +619,8 @@ static void coarsen(const OG *g, const int32_t *z, OG *cg, int32_t *pi)
         }
         /* each intra-community edge was seen from both ends */
         cg->loop[c] = loops + intra / 2;
-        /* sorted neighbour list of the coarse node (insertion sort: plain) */
-        for (int64_t i = 1; i < nt; i++) {
-            int32_t x = touched[i];
-            int64_t j = i - 1;
-            while (j >= 0 && touched[j] > x) { touched[j + 1] = touched[j]; j--; }
-            touched[j + 1] = x;
-        }
+        /* sorted neighbour list of the coarse node */
+        qsort(touched, (size_t)nt, sizeof(int32_t), cmp_i32);
         for (int64_t i = 0; i < nt; i++) {
             cg->adj[k] = touched[i];
             cg->wt[k] = acc[touched[i]];
@@ -578,9 +689,13 @@ static void plp_run(const OG *g, uint64_t seed, double theta, int32_t max_iter,
     char *active = (char *)malloc((size_t)n + 1);
     char *adopt = (char *)calloc((size_t)n + 1, 1);
     int32_t *prop = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
-    Scratch s;
-    s.acc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
-    s.touched = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    const int T = OR_THREADS();
+    Scratch *ts = (Scratch *)calloc((size_t)T, sizeof(Scratch));
+    int64_t (*tst)[ST_PAD] = calloc((size_t)T, sizeof(*tst));  /* per-thread counters */
+    for (int t = 0; t < T; t++) {
+        ts[t].acc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+        ts[t].touched = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    }
     for (int64_t v = 0; v < n; v++) { z[v] = (int32_t)v; active[v] = 1; }
     int64_t updated = n;
     int32_t it = 0;
@@ -589,26 +704,32 @@ static void plp_run(const OG *g, uint64_t seed, double theta, int32_t max_iter,
         uint32_t salt = plp_salt(seed, it);
         for (int32_t k = 0; k < cl.ncol; k++) {
             int64_t a = cl.off[k], b = cl.off[k + 1];
+            int64_t work;
+            CLASS_WORK(g, cl.v, a, b, work);
+            (void)work;
+            #pragma omp parallel for schedule(dynamic, 16) if (work >= OR_PAR_MIN)
             for (int64_t i = a; i < b; i++) {
                 int32_t v = cl.v[i];
+                Scratch *sp = &ts[OR_TID()];
+                int64_t *lst = tst[OR_TID()];
                 adopt[v] = 0;
                 if (use_active && !active[v] && !is_hub(g, v)) continue;
                 if (g->rp[v + 1] == g->rp[v]) continue;           /* deg(v) = 0 */
-                int64_t nt = gather_weights(g, z, v, &s);
+                int64_t nt = gather_weights(g, z, v, sp);
                 int32_t bestl = -1;
                 int64_t bestw = 0;
                 for (int64_t j = 0; j < nt; j++) {                /* dominant label */
-                    int32_t l = s.touched[j];
-                    if (bestl < 0 || s.acc[l] > bestw ||
-                        (s.acc[l] == bestw && fmix32((uint32_t)l ^ salt) < fmix32((uint32_t)bestl ^ salt))) {
-                        bestl = l; bestw = s.acc[l];
+                    int32_t l = sp->touched[j];
+                    if (bestl < 0 || sp->acc[l] > bestw ||
+                        (sp->acc[l] == bestw && fmix32((uint32_t)l ^ salt) < fmix32((uint32_t)bestl ^ salt))) {
+                        bestl = l; bestw = sp->acc[l];
                     }
                 }
-                int64_t wcur = s.acc[z[v]];
-                st[ST_ENTRIES] += g->rp[v + 1] - g->rp[v];
-                st[ST_CANDIDATES] += nt;
-                st[ST_DECISIONS] += 1;
-                clear_weights(&s, nt);
+                int64_t wcur = sp->acc[z[v]];
+                lst[ST_ENTRIES] += g->rp[v + 1] - g->rp[v];
+                lst[ST_CANDIDATES] += nt;
+                lst[ST_DECISIONS] += 1;
+                clear_weights(sp, nt);
                 if (bestw > wcur) { adopt[v] = 1; prop[v] = bestl; }
                 else adopt[v] = 2;
             }
@@ -628,9 +749,14 @@ static void plp_run(const OG *g, uint64_t seed, double theta, int32_t max_iter,
     }
     st[ST_ITERS] = it;
     st[ST_CONVERGED] = ((double)updated > theta) ? 0 : 1;
+    for (int t = 0; t < T; t++) {
+        for (int k = 0; k < ST_N; k++) st[k] += tst[t][k];
+        free(ts[t].acc); free(ts[t].touched);
+    }
+    free(ts); free(tst);
     compact(n, z);
     classes_free(&cl);
-    free(active); free(adopt); free(prop); free(s.acc); free(s.touched);
+    free(active); free(adopt); free(prop);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -703,8 +829,7 @@ int or_gain(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
     OG g;
     if (res_num < 0 || res_den < 1) return -2;
     if (og_from_input(&g, n, rp, col, w)) return -1;
-    g.res_num = res_num;
-    g.res_den = res_den;
+    if (og_set_resolution(&g, res_num, res_den)) { og_free(&g); return -2; }
     int64_t *volc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     for (int64_t x = 0; x < n; x++) volc[labels[x]] += g.vol[x];
     int64_t wD = 0, wC = 0;
@@ -718,8 +843,33 @@ int or_gain(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
     return 0;
 }
 
+/* threads of the OpenMP build (no effect in the plain build); returns the
+ * number the next parallel class will use */
+int or_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+    return OR_THREADS();
+}
+
+/* the schedule's colouring (greedy in descending priority order) */
 int32_t or_color(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
                  uint64_t seed, int32_t *color)
+{
+    OG g;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    int32_t k = n ? color_greedy(&g, seed, color) : 0;
+    og_free(&g);
+    return k;
+}
+
+/* the same colouring by Jones-Plassmann rounds (small graphs: it rescans
+ * every uncoloured vertex in every round) */
+int32_t or_color_jp(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+                    uint64_t seed, int32_t *color)
 {
     OG g;
     if (og_from_input(&g, n, rp, col, w)) return -1;
@@ -753,8 +903,7 @@ int or_plm(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
     OG g;
     if (res_num < 0 || res_den < 1) return -2;
     if (og_from_input(&g, n, rp, col, w)) return -1;
-    g.res_num = res_num;
-    g.res_den = res_den;
+    if (og_set_resolution(&g, res_num, res_den)) { og_free(&g); return -2; }
     int64_t st[ST_N] = {0};
     st[ST_CONVERGED] = 1;
     Opts o = { seed, max_sweeps, max_levels, rev };
@@ -861,13 +1010,17 @@ int or_epp(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
 }
 
 /* Number of vertices that have a neighbour community with positive gain
- * under `labels` (the convergence condition of Algorithm 2); the largest
- * such gain numerator goes to max_gain as (hi, lo). */
+ * under `labels` (the convergence condition of Algorithm 2) for the
+ * resolution res_num / res_den; the largest such gain numerator goes to
+ * max_gain as (hi, lo).  -2: invalid resolution. */
 int64_t or_positive_moves(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
-                          const int32_t *labels, int64_t *max_gain)
+                          const int32_t *labels, int64_t res_num, int64_t res_den,
+                          int64_t *max_gain)
 {
     OG g;
+    if (res_num < 0 || res_den < 1) return -2;
     if (og_from_input(&g, n, rp, col, w)) return -1;
+    if (og_set_resolution(&g, res_num, res_den)) { og_free(&g); return -2; }
     int64_t *volc = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     for (int64_t x = 0; x < n; x++) volc[labels[x]] += g.vol[x];
     Scratch s;

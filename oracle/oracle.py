@@ -21,8 +21,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cd_oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 # stats layout (enum in cd_oracle.c)
 STATS = ["levels", "sweeps", "moves", "colors0", "converged", "entries",
@@ -34,28 +35,40 @@ MAX_LEVELS = 64
 MAX_PLP_ITERS = 1000
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, portable: no -march)."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
-        tmp = _OUT + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC",
+def _compile(out: str, extra, force: bool) -> str:
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", *extra,
                                "-o", tmp, _SRC])
-        os.replace(tmp, _OUT)
-    return _OUT
+        os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, portable: no -march), and its
+    OpenMP build beside it (same source, -fopenmp)."""
+    _compile(_OUT_OMP, ["-fopenmp"], force)
+    return _compile(_OUT, [], force)
+
+
+def lib(threads: int = 1):
+    """The sequential oracle (threads == 1) or its OpenMP build set to
+    `threads` threads (0: the OpenMP default, all cores)."""
+    omp = threads != 1
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+        L = _libs.get(omp)
+        if L is None:
+            build()
+            L = ctypes.CDLL(_OUT_OMP if omp else _OUT)
             P = ctypes.c_void_p
             i64, i32, dbl, u64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64
             L.or_modularity.argtypes = [i64, P, P, P, P, P, P]
             L.or_gain.argtypes = [i64, P, P, P, P, i32, i32, i64, i64, P]
             L.or_color.argtypes = [i64, P, P, P, u64, P]
             L.or_color.restype = i32
+            L.or_color_jp.argtypes = [i64, P, P, P, u64, P]
+            L.or_color_jp.restype = i32
             L.or_move_phase.argtypes = [i64, P, P, P, u64, i32, ctypes.c_int, P, P]
             L.or_plm.argtypes = [i64, P, P, P, ctypes.c_int, u64, i32, i32, ctypes.c_int, i64, i64, P, P, P]
             L.or_plp.argtypes = [i64, P, P, P, u64, dbl, i32, ctypes.c_int, ctypes.c_int, P, P, P]
@@ -65,10 +78,19 @@ def lib():
             L.or_coarsen.restype = i64
             L.or_epp.argtypes = [i64, P, P, P, ctypes.c_int, ctypes.c_int, u64, i32, i32,
                                  dbl, i32, P, P, P, P, P]
-            L.or_positive_moves.argtypes = [i64, P, P, P, P, P]
+            L.or_positive_moves.argtypes = [i64, P, P, P, P, i64, i64, P]
             L.or_positive_moves.restype = i64
-            _lib = L
-    return _lib
+            L.or_set_threads.argtypes = [ctypes.c_int]
+            L.or_set_threads.restype = ctypes.c_int
+            _libs[omp] = L
+        if omp:
+            L.or_set_threads(int(threads) if threads > 0 else (os.cpu_count() or 1))
+    return L
+
+
+def threads_used(threads: int) -> int:
+    """Threads a parallel colour class of the given build runs on."""
+    return 1 if threads == 1 else int(lib(threads).or_set_threads(0))
 
 
 def _np(x, dtype):
@@ -133,14 +155,23 @@ def gain(row_ptr, col, w, labels, u, D, resolution=(1, 1)):
     out = np.zeros(2, np.int64)
     p, q = resolution
     if lib().or_gain(*g.args(), _ptr(z), int(u), int(D), int(p), int(q), _ptr(out)) == -2:
-        raise ValueError("resolution must be p >= 0, q >= 1")
+        raise ValueError("resolution must be p >= 0, q >= 1, max(p, q) (2W)^2 < 2^126")
     return _i128(out[0], out[1])
 
 
 def color(row_ptr, col, w, seed):
+    """(number of colours, colour per vertex) of the schedule's colouring."""
     g = _CSR(row_ptr, col, w)
     c = np.zeros(max(g.n, 1), np.int32)
     k = lib().or_color(*g.args(), seed, _ptr(c))
+    return k, c[:g.n]
+
+
+def color_jp(row_ptr, col, w, seed):
+    """The same colouring computed by Jones-Plassmann rounds (small graphs)."""
+    g = _CSR(row_ptr, col, w)
+    c = np.zeros(max(g.n, 1), np.int32)
+    k = lib().or_color_jp(*g.args(), seed, _ptr(c))
     return k, c[:g.n]
 
 
@@ -153,33 +184,34 @@ def move_phase(row_ptr, col, w, seed, labels=None, max_sweeps=MAX_SWEEPS, rev=Fa
 
 
 def plm(row_ptr, col, w, refine=False, seed=1, max_sweeps=MAX_SWEEPS,
-        max_levels=MAX_LEVELS, rev=False, resolution=(1, 1)) -> Result:
+        max_levels=MAX_LEVELS, rev=False, resolution=(1, 1), threads=1) -> Result:
     """PLM / PLMR.  resolution = (p, q): the moves maximise the objective with
     gamma = p/q scaling the volume term (Sec. III-B); the returned modularity
-    is always the standard one (gamma = 1)."""
+    is always the standard one (gamma = 1).  threads != 1 runs the OpenMP
+    build (identical results)."""
     g = _CSR(row_ptr, col, w)
     z = np.zeros(max(g.n, 1), np.int32)
     mod = ctypes.c_double()
     st = np.zeros(len(STATS), np.int64)
     p, q = resolution
-    rc = lib().or_plm(*g.args(), int(refine), seed, max_sweeps, max_levels, int(rev), int(p), int(q),
+    rc = lib(threads).or_plm(*g.args(), int(refine), seed, max_sweeps, max_levels, int(rev), int(p), int(q),
                       _ptr(z), ctypes.byref(mod), _ptr(st))
     if rc == -2:
-        raise ValueError("resolution must be p >= 0, q >= 1")
+        raise ValueError("resolution must be p >= 0, q >= 1, max(p, q) (2W)^2 < 2^126")
     if rc:
         raise MemoryError
     return Result(z[:g.n], mod.value, _stats(st))
 
 
 def plp(row_ptr, col, w, seed=1, theta=None, max_iter=MAX_PLP_ITERS,
-        use_active=True, rev=False) -> Result:
+        use_active=True, rev=False, threads=1) -> Result:
     g = _CSR(row_ptr, col, w)
     if theta is None:
         theta = g.n * 1e-5
     z = np.zeros(max(g.n, 1), np.int32)
     mod = ctypes.c_double()
     st = np.zeros(len(STATS), np.int64)
-    if lib().or_plp(*g.args(), seed, float(theta), max_iter, int(use_active), int(rev),
+    if lib(threads).or_plp(*g.args(), seed, float(theta), max_iter, int(use_active), int(rev),
                     _ptr(z), ctypes.byref(mod), _ptr(st)):
         raise MemoryError
     return Result(z[:g.n], mod.value, _stats(st))
@@ -210,7 +242,7 @@ def coarsen(row_ptr, col, w, labels):
 
 def epp(row_ptr, col, w, b=4, final_refine=True, seed=1, theta=None,
         max_sweeps=MAX_SWEEPS, max_levels=MAX_LEVELS, max_iter=MAX_PLP_ITERS,
-        want_parts=False):
+        want_parts=False, threads=1):
     g = _CSR(row_ptr, col, w)
     if theta is None:
         theta = g.n * 1e-5
@@ -219,7 +251,7 @@ def epp(row_ptr, col, w, b=4, final_refine=True, seed=1, theta=None,
     core = np.zeros(max(g.n, 1), np.int32) if want_parts else None
     mod = ctypes.c_double()
     st = np.zeros(len(STATS), np.int64)
-    if lib().or_epp(*g.args(), b, int(final_refine), seed, max_sweeps, max_levels,
+    if lib(threads).or_epp(*g.args(), b, int(final_refine), seed, max_sweeps, max_levels,
                     float(theta), max_iter, _ptr(z), _ptr(base), _ptr(core),
                     ctypes.byref(mod), _ptr(st)):
         raise MemoryError
@@ -229,9 +261,14 @@ def epp(row_ptr, col, w, b=4, final_refine=True, seed=1, theta=None,
     return r
 
 
-def positive_moves(row_ptr, col, w, labels):
-    """Vertices with a positive-gain move under ``labels`` (0 at convergence)."""
+def positive_moves(row_ptr, col, w, labels, resolution=(1, 1)):
+    """Vertices with a positive-gain move under ``labels`` for the resolution
+    gamma = p/q, resolution = (p, q) (0 at convergence)."""
     g = _CSR(row_ptr, col, w)
     z = _np(labels, np.int32)
     mg = np.zeros(2, np.int64)
-    return int(lib().or_positive_moves(*g.args(), _ptr(z), _ptr(mg)))
+    p, q = resolution
+    k = int(lib().or_positive_moves(*g.args(), _ptr(z), int(p), int(q), _ptr(mg)))
+    if k == -2:
+        raise ValueError("resolution must be p >= 0, q >= 1, max(p, q) (2W)^2 < 2^126")
+    return k

@@ -100,21 +100,23 @@ def volumes(row_ptr, col, w):
     return vol, W
 
 
-def modularity_exact(row_ptr, col, w, labels):
+def modularity_exact(row_ptr, col, w, labels, fraction=False):
     """Eq. 1 as (2W * S_in - S_vol2) / (4 W^2) with exact integers:
-    S_in = 2 * sum_C omega(C), S_vol2 = sum_C vol(C)^2."""
+    S_in = 2 * sum_C omega(C), S_vol2 = sum_C vol(C)^2.  With fraction=True
+    returns (value, numerator, denominator), the last two as Python ints."""
     n, rp, src, c = _entries(row_ptr, col)
     wt = _weights(w, len(c))
     lab = np.asarray(labels, dtype=np.int64)
     vol, W = volumes(row_ptr, col, w)
     if W == 0:
-        return 0.0
+        return (0.0, 0, 0) if fraction else 0.0
     loop = src == c
     same = lab[src] == lab[c]
     s_in = int(wt[same & ~loop].sum()) + 2 * int(wt[loop].sum())
     vc = _int_sums(lab, vol, int(lab.max()) + 1 if n else 0)
     s_vol2 = sum(int(v) * int(v) for v in vc[vc != 0])
-    return (2 * W * s_in - s_vol2) / (4 * W * W)
+    N, D = 2 * W * s_in - s_vol2, 4 * W * W
+    return (N / D, N, D) if fraction else N / D
 
 
 def check_dense_labels(labels):

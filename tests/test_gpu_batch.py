@@ -1,7 +1,7 @@
-"""Batched and served runs: every graph's result in a batch, or in the
-server's mix, equals its single-graph result (labels, modularity and the
-schedule counters), which the parity tests tie to the oracle.  A few cases
-are compared with the oracle directly as well.
+"""Batched and served runs: every graph's result in a batch equals its
+single-graph result (labels, modularity and the schedule counters), which
+the parity tests tie to the oracle; a batch and every result served in the
+server's mix are also compared with the oracle directly.
 """
 import numpy as np
 import pytest
@@ -156,25 +156,42 @@ def test_batch_invalid_arguments():
 # Server
 # ---------------------------------------------------------------------------
 
-def test_server_results_equal_single():
+def _oracle_run(O, g, algo, refine, ensemble, seed):
+    if algo == cd.CD_ALGO_PLM:
+        return O.plm(*g.numpy(), refine=refine, seed=seed)
+    if algo == cd.CD_ALGO_PLP:
+        return O.plp(*g.numpy(), seed=seed)
+    return O.epp(*g.numpy(), b=ensemble, final_refine=refine, seed=seed)
+
+
+ORACLE_KEYS = {cd.CD_ALGO_PLM: ["levels", "sweeps", "moves", "entries", "candidates", "decisions",
+                                "converged", "ncomm"],
+               cd.CD_ALGO_PLP: ["iters", "moves", "entries", "candidates", "decisions", "ncomm"],
+               cd.CD_ALGO_EPP: ["ncomm"]}
+
+
+def test_server_results_match_oracle(O):
+    """Every served result, computed in the server's mix of concurrently
+    admitted runs, equals the oracle's result for that graph and task:
+    labels bit for bit, modularity, and the schedule counters."""
     Gs = [cd.Graph.from_synth(g, device="cuda") for g in GRAPHS]
     tasks = [(cd.CD_ALGO_PLM, False, 1), (cd.CD_ALGO_PLM, True, 1), (cd.CD_ALGO_PLP, False, 1),
              (cd.CD_ALGO_EPP, True, 2)]
     S = cd.Server(max_slots=8)
     try:
         tickets = []
-        for i, G in enumerate(Gs):
+        for i, (g, G) in enumerate(zip(GRAPHS, Gs)):
             for t in tasks[i % 2::2]:
-                tickets.append((G, t, S.submit(G, *t, seed=7)))
-        for G, t, tk in tickets:
+                tickets.append((g, G, t, S.submit(G, *t, seed=7)))
+        for g, G, t, tk in tickets:
             out = torch.empty(max(G.n, 1), dtype=torch.int32, device="cuda")[:G.n]
             status, mod, lat, st = S.poll(tk, out, timeout_ms=-1)
             assert lat >= 0
-            ref = _single(G, *t, seed=7)
-            assert torch.equal(out.cpu(), ref.labels.cpu())
-            assert mod == ref.modularity
-            for k in STAT_KEYS:
-                assert st[k] == ref.stats[k], k
+            o = _oracle_run(O, g, *t, seed=7)
+            assert np.array_equal(out.cpu().numpy(), o.labels), t
+            assert abs(mod - o.modularity) <= 1e-12 and mod == o.modularity
+            for k in ORACLE_KEYS[t[0]]:
+                assert st[k] == o.stats[k], (t, k, st[k], o.stats[k])
         assert S.info() == (0, 0, 0)
     finally:
         S.close()

@@ -168,8 +168,23 @@ def test_colouring_equals_greedy_in_priority_order(oracle_mod, seed):
     equals sequential greedy colouring in descending priority order."""
     for g in (synth.rmat(9, seed=3), synth.random_graph(200, 900, seed=seed % 97, loops=4)):
         rp, c, w = csr(g)
+        want = _greedy_in_priority_order(rp, c, seed)
         k, col = oracle_mod.color(rp, c, w, seed)
-        assert col.tolist() == _greedy_in_priority_order(rp, c, seed)
+        assert col.tolist() == want
+        kj, colj = oracle_mod.color_jp(rp, c, w, seed)
+        assert colj.tolist() == want and kj == k
+
+
+@pytest.mark.parametrize("seed", [1, 3])
+def test_colouring_one_pass_equals_rounds(oracle_mod, seed):
+    """The schedule's one-pass colouring equals the Jones-Plassmann rounds
+    on graphs with hubs (hub-hub edges skipped by both) and with loops."""
+    for g in (synth.rmat(12, seed=seed), _hub_core_graph(nh=4, leaves=4100, seed=seed),
+              synth.chung_lu(3000, seed=seed)):
+        rp, c, w = csr(g)
+        k, col = oracle_mod.color(rp, c, w, seed)
+        kj, colj = oracle_mod.color_jp(rp, c, w, seed)
+        assert k == kj and np.array_equal(col, colj)
 
 
 def _hub_core_graph(nh=5, leaves=4200, seed=1):
@@ -202,8 +217,8 @@ def test_colouring_ignores_only_hub_hub_edges(oracle_mod):
     deg = np.diff(rp)
     hub = deg > 4096
     assert hub.sum() == 5
-    for seed in (1, 7):
-        k, col = oracle_mod.color(rp, c, w, seed)
+    for seed, colour in ((1, oracle_mod.color), (7, oracle_mod.color), (7, oracle_mod.color_jp)):
+        k, col = colour(rp, c, w, seed)
         same_hub_pair = 0
         for u in range(g.n):
             nb = c[rp[u]:rp[u + 1]]

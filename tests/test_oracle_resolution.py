@@ -104,3 +104,59 @@ def test_invalid_resolution(oracle_mod):
             oracle_mod.plm(rp, c, w, resolution=res)
         with pytest.raises(ValueError):
             oracle_mod.gain(rp, c, w, np.zeros(6, np.int32), 0, 1, resolution=res)
+        with pytest.raises(ValueError):
+            oracle_mod.positive_moves(rp, c, w, np.zeros(6, np.int32), resolution=res)
+
+
+def _heavy():
+    """A weighted graph with 2W near 2^41, so that (2W)^2 is near 2^82."""
+    base = synth.random_graph(40, 300, seed=9, loops=4, wmax=50)
+    w = (base.w.to(torch.int64) * 20_000_000 + 3).clamp(max=2**31 - 1).to(torch.int32)
+    return synth.Graph(base.n, base.row_ptr, base.col, w, "heavy")
+
+
+def test_resolution_outside_128_bits_rejected(oracle_mod):
+    """Both gain products are bounded by max(p, q) (2W)^2; a resolution whose
+    bound reaches 2^126 could overflow the 128-bit gain and is rejected, one
+    just inside is accepted (also after reduction by the gcd)."""
+    g = _heavy()
+    rp, c, w = g.numpy()
+    W = sum(exact.edges_of(rp, c, w).values())
+    w2 = (2 * W) ** 2
+    inside = (2**126 - 1) // w2
+    assert 2**40 < inside < 2**62
+    for res in ((inside + 1, 1), (1, inside + 1), (2 * (inside + 1), 2)):
+        with pytest.raises(ValueError):
+            oracle_mod.plm(rp, c, w, resolution=res)
+        with pytest.raises(ValueError):
+            oracle_mod.gain(rp, c, w, np.zeros(g.n, np.int32), 0, 1, resolution=res)
+    oracle_mod.plm(rp, c, w, resolution=(inside, 1))
+    oracle_mod.plm(rp, c, w, resolution=(3 * inside, 3))     # reduces to (inside, 1)
+
+
+@pytest.mark.parametrize("refine", [False, True])
+def test_resolution_reduced_by_gcd_changes_nothing(oracle_mod, refine):
+    g = synth.random_graph(300, 1500, seed=6, loops=10)
+    rp, c, w = g.numpy()
+    for p, q in ((3, 2), (5, 7), (1, 3)):
+        a = oracle_mod.plm(rp, c, w, refine=refine, seed=2, resolution=(p, q))
+        b = oracle_mod.plm(rp, c, w, refine=refine, seed=2, resolution=(6 * p, 6 * q))
+        assert np.array_equal(a.labels, b.labels) and a.stats == b.stats
+
+
+@pytest.mark.parametrize("res", [(1, 2), (3, 1), (5, 7)])
+def test_converged_plmr_has_no_positive_gamma_move(oracle_mod, res):
+    """After a converged PLMR run (the last move phase works on the input
+    graph), no vertex has a move with positive gamma-gain (Algorithm 2's
+    stopping rule), for gamma != 1."""
+    elsewhere = 0
+    for g in (synth.rmat(10, seed=2), synth.random_graph(300, 1500, seed=6, loops=10),
+              synth.chung_lu(2000, seed=4)):
+        rp, c, w = g.numpy()
+        r = oracle_mod.plm(rp, c, w, refine=True, seed=1, resolution=res)
+        assert r.stats["converged"] == 1
+        assert oracle_mod.positive_moves(rp, c, w, r.labels, resolution=res) == 0
+        # the check sees gamma: judged at the inverse gamma, some vertex
+        # wants to move (on graphs that end with several communities)
+        elsewhere += oracle_mod.positive_moves(rp, c, w, r.labels, resolution=(res[1], res[0]))
+    assert elsewhere > 0
