@@ -275,9 +275,11 @@ cd_status cd_graph_export(const cd_graph *g, int64_t *row_ptr, int32_t *col, int
  * (an allocation can synchronise the device), or hooks run where allocation
  * is not permitted.
  *   n, row_ptr, col, w   the graph in the input conventions above (device
- *                        pointers; w may be NULL for unit weights); n must
+ *                        pointers; w may be NULL for unit weights, col may
+ *                        be NULL when the graph has no entries); n must
  *                        not exceed 1,048,576
- *   labels               device int32[n], each in [0, n)
+ *   labels               device int32[n], each in [0, n) (may be NULL when
+ *                        n = 0); an edgeless graph has modularity 0
  *   stream               cudaStream_t to run on (NULL: legacy default)
  *   mod                  host double receiving the result
  * Scratch is one fixed device array in the library (8.4 MB, held on every GPU

@@ -73,7 +73,8 @@ __global__ void k_static_rows(int64_t n, const int64_t *rp, const int32_t *col, 
     for (int64_t u = warp; u < n; u += nwarps) {
         const int64_t beg = rp[u], end = rp[u + 1];
         const int32_t cu = z[u];
-        if (beg < 0 || end < beg || end > nnz || cu < 0 || cu >= n) { bad = 1; continue; }
+        // col may be null only when no row has entries (an edgeless graph)
+        if (beg < 0 || end < beg || end > nnz || cu < 0 || cu >= n || (!col && end > beg)) { bad = 1; continue; }
         unsigned long long vol = 0, loop = 0, inner = 0;
         for (int64_t e = beg + lane; e < end; e += 32) {
             const int32_t v = col[e];
@@ -156,7 +157,7 @@ extern "C" cd_status cd_modularity_static(int64_t n, const int64_t *row_ptr, con
         if (n < 0 || n > STATIC_MAX_VERTICES)
             cd::raise(CD_EINVAL, "n = %lld is outside [0, %lld], the size of the static scratch", (long long)n,
                       (long long)STATIC_MAX_VERTICES);
-        if (!row_ptr || (n > 0 && (!labels || !col))) cd::raise(CD_EINVAL, "row_ptr, col and labels are required");
+        if (!row_ptr || (n > 0 && !labels)) cd::raise(CD_EINVAL, "row_ptr and labels are required");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         unsigned long long *scr = scratch_address();
         const unsigned gv = cd::grid_for(n, cd::kBlock, 152 * 16);

@@ -56,3 +56,22 @@ def test_static_scratch_rejects_out_of_range_labels():
     with pytest.raises(cd.CDError) as e:
         cd.cd_modularity_static(g.row_ptr, g.col, g.w, bad)
     assert e.value.status == cd.CD_EINVAL
+
+
+@pytest.mark.parametrize("case", ["empty", "isolated", "loops_only"])
+def test_static_scratch_degenerate_graphs(case):
+    """n = 0, vertices without edges (2W = 0: modularity 0), and self-loops
+    only: the same result and status as cd_modularity."""
+    g = {"empty": lambda: synth.from_edge_list(0, []),
+         "isolated": lambda: synth.from_edge_list(6, []),
+         "loops_only": lambda: synth.from_edge_list(4, [], self_loops={0: 3, 2: 1})}[case]()
+    gd = g.to("cuda")
+    G = cd.Graph(gd.row_ptr, gd.col, gd.w)
+    for labels in (torch.arange(g.n, dtype=torch.int32, device="cuda"),
+                   torch.zeros(g.n, dtype=torch.int32, device="cuda")):
+        q_static = cd.cd_modularity_static(gd.row_ptr, gd.col, gd.w, labels)
+        q_ref = G.modularity(labels)
+        assert q_static == q_ref
+        if case != "loops_only":
+            assert q_static == 0.0
+
