@@ -64,7 +64,8 @@ enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1 };
  *   max_levels  cap on the coarsening hierarchy depth (Algorithm 3).
  *   max_iters   cap on PLP iterations (Algorithm 1 "while").
  *   profile     1: time every persistent launch with CUDA events and report
- *               it in cd_stats (adds host synchronisation).
+ *               it in cd_stats (adds host synchronisation).  2: also trace
+ *               every class step of the move phases (cd_debug_class_trace).
  *   team_quantum, team_min  launch shape of shared launches (EPP bases,
  *               batches, the server): a graph whose work (adjacency entries
  *               + vertices) is w gets teams of at least
@@ -311,6 +312,17 @@ void cd_debug_fail_alloc(int k);
  * runs in tier order.  Errors: CD_EINVAL. */
 cd_status cd_debug_plan_launch(const int64_t *work, int count, int64_t team_quantum, int32_t team_min, int grid_max,
                                int32_t *grid, int32_t *ntiers, int32_t *tiers, int32_t *order);
+
+/* Diagnostic: the class trace of the move phases (Algorithm 2 under the
+ * colour-class schedule) run with opts.profile = 2 since the last call.  One
+ * row of nine int64 per class step, in completion order: phase number, sweep,
+ * colour class, its vertices, its adjacency entries, its hub aggregation
+ * chunks, its hub decide slices, its hubs above 4096 neighbours, and the wall
+ * time in ns on the team's first block from the previous class's barrier to
+ * this class's barrier.  With out == NULL only *count (rows) is set; then
+ * out[9 * count] receives the rows (cap = rows the buffer holds) and the
+ * trace is cleared.  Errors: CD_EINVAL. */
+cd_status cd_debug_class_trace(int64_t *out, int64_t cap, int64_t *count);
 
 #ifdef __cplusplus
 }

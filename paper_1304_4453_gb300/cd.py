@@ -74,7 +74,7 @@ SYMBOLS = ["cd_opts_default", "cd_status_str", "cd_last_error", "cd_graph_create
            "cd_epp", "cd_color", "cd_coarsen", "cd_graph_export", "cd_debug_fail_alloc",
            "cd_launch_count", "cd_modularity_static", "cd_run_batch", "cd_plm_batch",
            "cd_server_create", "cd_server_submit", "cd_server_poll", "cd_server_info",
-           "cd_server_destroy", "cd_tune", "cd_debug_plan_launch"]
+           "cd_server_destroy", "cd_tune", "cd_debug_plan_launch", "cd_debug_class_trace"]
 
 
 def library_path() -> str:
@@ -107,6 +107,7 @@ def lib():
             L.cd_debug_fail_alloc.argtypes = [c_int]
             L.cd_debug_fail_alloc.restype = None
             L.cd_debug_plan_launch.argtypes = [P, c_int, i64, ctypes.c_int32, c_int, P, P, P, P]
+            L.cd_debug_class_trace.argtypes = [P, i64, P]
             L.cd_modularity_static.argtypes = [i64, P, P, P, P, P, P]
             L.cd_run_batch.argtypes = [P, c_int, P, P, P, c_int, P, P, P]
             L.cd_plm_batch.argtypes = [P, c_int, c_int, P, P, c_int, P, P]
@@ -270,6 +271,19 @@ def cd_graph_export(h):
 
 def cd_debug_fail_alloc(k: int):
     lib().cd_debug_fail_alloc(int(k))
+
+
+TRACE_FIELDS = ("phase", "sweep", "cls", "vertices", "entries", "hub_chunks", "hub_slices", "big_hubs", "ns")
+
+
+def cd_debug_class_trace() -> np.ndarray:
+    """Rows (one per class step, fields TRACE_FIELDS) of the move phases run
+    with profile=2 since the last call; the library's trace is cleared."""
+    cnt = ctypes.c_int64()
+    _check(lib().cd_debug_class_trace(None, 0, ctypes.byref(cnt)), False)
+    out = np.zeros((max(cnt.value, 1), len(TRACE_FIELDS)), np.int64)
+    _check(lib().cd_debug_class_trace(out.ctypes.data, cnt.value, ctypes.byref(cnt)), False)
+    return out[:cnt.value]
 
 
 def cd_debug_plan_launch(work, team_quantum: int, team_min: int, grid_max: int):

@@ -297,6 +297,21 @@ cd_status cd_debug_plan_launch(const int64_t *work, int count, int64_t team_quan
     });
 }
 
+cd_status cd_debug_class_trace(int64_t *out, int64_t cap, int64_t *count) {
+    if (!count) return CD_EINVAL;
+    return guarded([&]() {
+        static std::vector<int64_t> pending;
+        if (pending.empty()) pending = take_class_trace();
+        const int64_t rows = (int64_t)pending.size() / TRACE_FIELDS;
+        *count = rows;
+        if (!out) return CD_OK;
+        if (cap < rows) raise(CD_EINVAL, "class trace holds %lld rows, buffer %lld", (long long)rows, (long long)cap);
+        std::copy(pending.begin(), pending.end(), out);
+        pending.clear();
+        return CD_OK;
+    });
+}
+
 uint64_t cd_launch_count(void) { return launch_count(); }
 
 }  // extern "C"

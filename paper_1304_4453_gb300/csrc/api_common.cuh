@@ -41,6 +41,7 @@ inline RunOpts to_run(const cd_opts *o) {
     r.max_levels = o->max_levels;
     r.max_iters = o->max_iters;
     r.profile = o->profile != 0;
+    r.trace = o->profile >= 2;
     r.team_quantum = o->team_quantum;
     r.team_min = o->team_min;
     for (int i = 0; i < NLIM; i++) {

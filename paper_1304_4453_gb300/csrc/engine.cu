@@ -316,6 +316,9 @@ struct PhaseRun {
     DBuf<int32_t> dz_u, dz_l;         // deferred hub labels
     DBuf<int32_t> cstamp;             // re-check community stamps
     DBuf<unsigned int> dz_n;
+    // class trace (RunOpts::trace): timestamps and the per-class sizes
+    DBuf<unsigned long long> cls_ns;
+    std::vector<int64_t> cls_info;    // per class: vertices, entries, hub chunks, hub slices, relaxed hubs
     // set by the engine after the launch
     double launch_ms = 0, wall_ms = 0;
     cd_status fail = CD_OK;
@@ -404,6 +407,67 @@ static int32_t read_counters(PhaseRun &r, int32_t *conv, std::vector<Counters> &
     return runs;
 }
 
+// ---------------------------------------------------------------------------
+// Class trace (profile level 2): per class step of a move phase, its wall time
+// on block 0 from the previous class's barrier to its own, beside the class's
+// size.  Diagnostic only; host copies of the schedule are made here.
+// ---------------------------------------------------------------------------
+static std::mutex g_trace_mu;
+static std::vector<int64_t> g_trace;
+static int64_t g_trace_phase = 0;
+
+static void prepare_trace(PhaseRun &r, const GraphView &g, const Schedule &S, cudaStream_t s) {
+    const int64_t ncol = S.ncol;
+    r.cls_ns.alloc((size_t)r.cap * ncol + 1, s);
+    r.cls_ns.zero();
+    r.a.class_ns = r.cls_ns.p;
+    const int64_t listed = S.off[(size_t)ncol * NBINS];
+    std::vector<int32_t> order((size_t)listed);
+    std::vector<int64_t> rp((size_t)g.n + 1);
+    if (listed) CD_CUDA(cudaMemcpyAsync(order.data(), S.order.p, listed * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaMemcpyAsync(rp.data(), g.rp, ((size_t)g.n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaStreamSynchronize(s));
+    r.cls_info.assign((size_t)ncol * 5, 0);
+    for (int64_t k = 0; k < ncol; k++) {
+        const int64_t a = S.off[(size_t)k * NBINS], b = S.off[(size_t)(k + 1) * NBINS];
+        int64_t e = 0;
+        for (int64_t i = a; i < b; i++) e += rp[order[i] + 1] - rp[order[i]];
+        int64_t *ci = &r.cls_info[(size_t)k * 5];
+        ci[0] = b - a;
+        ci[1] = e;
+        ci[2] = S.nb1[k];
+        ci[3] = S.nb2[k];
+        ci[4] = S.nrelax[k];
+    }
+}
+
+static void record_trace(PhaseRun &r, int32_t runs, cudaStream_t s) {
+    const int64_t ncol = r.a.ncol;
+    std::vector<unsigned long long> t((size_t)runs * ncol + 1);
+    CD_CUDA(cudaMemcpyAsync(t.data(), r.cls_ns.p, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaStreamSynchronize(s));
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    const int64_t ph = g_trace_phase++;
+    unsigned long long prev = t[0];
+    for (int64_t sw = 0; sw < runs; sw++)
+        for (int64_t k = 0; k < ncol; k++) {
+            const unsigned long long x = t[1 + sw * ncol + k];
+            if (x == 0) continue;
+            const int64_t *ci = &r.cls_info[(size_t)k * 5];
+            const int64_t row[TRACE_FIELDS] = {ph, sw, k, ci[0], ci[1], ci[2], ci[3], ci[4], (int64_t)(x - prev)};
+            g_trace.insert(g_trace.end(), row, row + TRACE_FIELDS);
+            prev = x;
+        }
+}
+
+std::vector<int64_t> take_class_trace() {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    std::vector<int64_t> out;
+    out.swap(g_trace);
+    g_trace_phase = 0;
+    return out;
+}
+
 __global__ void k_comm_volumes(const int32_t *zeta, const int64_t *vol, int64_t n, int64_t *volc) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(reinterpret_cast<unsigned long long *>(volc + zeta[i]), (unsigned long long)vol[i]);
@@ -469,6 +533,7 @@ static std::unique_ptr<PhaseRun> prepare_move(const GraphView &g, const Schedule
     a.ubits = ubits;
     a.max_sweeps = o.max_sweeps;
     a.recheck_from = RECHECK_FROM;
+    if (o.trace) prepare_trace(*r, g, S, s);
     return r;
 }
 
@@ -476,7 +541,8 @@ static std::unique_ptr<PhaseRun> prepare_move(const GraphView &g, const Schedule
 static int64_t finish_move(PhaseRun &r, RunStats &st, cudaStream_t s) {
     int32_t conv = 0;
     std::vector<Counters> per;
-    read_counters(r, &conv, per, st, s);
+    const int32_t runs = read_counters(r, &conv, per, st, s);
+    if (r.cls_ns.p) record_trace(r, runs, s);
     int64_t total = 0;
     for (const Counters &h : per) {
         st.sweeps++;

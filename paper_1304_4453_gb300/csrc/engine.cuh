@@ -27,6 +27,7 @@ struct RunOpts {
     uint64_t seed = 1;
     int32_t max_sweeps = 256, max_levels = 64, max_iters = 1000;
     bool profile = false;
+    bool trace = false;          // profile level 2: per-class times of the move phases
     int64_t team_quantum = int64_t(1) << 18;   // launch shape (speed only)
     int32_t team_min = 8;
     BinLimits bins{{4, 16, 128, BLK_MAXDEG, BLK_MAXDEG}};  // schedule degree bins (speed only)
@@ -123,5 +124,10 @@ void run_plm(const GraphView &g, bool refine, const RunOpts &o, int32_t *labels,
 void run_plp(const GraphView &g, const RunOpts &o, double theta, int32_t *labels, RunStats &st, cudaStream_t s);
 void run_epp(const GraphView &g, int b, bool final_refine, const RunOpts &o, double theta, int32_t *labels,
              RunStats &st, cudaStream_t s);
+
+// Class trace of the move phases run with RunOpts::trace (profile level 2):
+// TRACE_FIELDS int64 per class step, appended in completion order.
+constexpr int TRACE_FIELDS = 9;   // phase, sweep, class, vertices, entries, hub chunks, hub slices, hubs > HUB_RELAX, ns
+std::vector<int64_t> take_class_trace();
 
 }  // namespace cd

@@ -77,6 +77,10 @@ struct PhaseArgs {
     // profile mode: block 0 adds the wall time of each class stage (ns):
     // [0] items (+ barrier), [1] hub decide (+ barrier), [2] re-check (+ barrier)
     unsigned long long *stage_ns;
+    // class trace (profile level 2): block 0 stamps the global timer when the
+    // phase starts ([0]) and after the barrier of class k in sweep sw
+    // ([1 + sw * ncol + k]); skipped (empty) classes keep 0
+    unsigned long long *class_ns;
 };
 
 // SweepCtx of class k (layout, roles, hubs).
@@ -604,6 +608,8 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
     int conv = 0;
     unsigned long long fin_base = 0;   // same in every block of the team
     const int64_t gtid = (int64_t)tm.rank * kBlock + threadIdx.x, gthreads = (int64_t)tm.size * kBlock;
+    const bool tracer = a.class_ns && tm.rank == 0 && threadIdx.x == 0;
+    if (tracer) a.class_ns[0] = global_ns();
     for (; sw < a.max_sweeps; sw++) {
         const int par = sw & 1;
         const int late = sw >= a.recheck_from;
@@ -693,6 +699,7 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
             }
             if (!team_sync(tm, sh.gen, sh.ok)) return false;
             if (timed) a.stage_ns[0] += global_ns() - t0;
+            if (tracer) a.class_ns[1 + (int64_t)sw * a.ncol + k] = global_ns();
         }
         if (__ldcg(&a.cnt[sw].wanted) == 0) {
             conv = 1;
