@@ -7,8 +7,9 @@ unit weights (seed 1).  A step is one complete cd_plm call (colouring, every
 Louvain level, coarsening, prolongation, compaction, modularity) on the
 device-resident graph; edges/s = undirected input edges / step time.
 
-Prints one JSON line.  ``--impl reference`` times the sequential CPU oracle
-instead (a bounded sample of the workload per step).
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (its
+OpenMP build on every host core, one complete run on a bounded sample of the
+workload per step).
 """
 from __future__ import annotations
 
@@ -28,7 +29,11 @@ UNIT = "edges/s"
 SCALE = 22
 EDGE_FACTOR = 16
 ABC = (0.57, 0.19, 0.19)
-SAMPLE_SCALE = 17          # oracle sample: same generator, 2^17 vertices
+# CPU baseline samples: the same generator at a smaller scale, so that one
+# complete oracle run stays near 10 s (OpenMP build on every host core) and
+# near 10 s (sequential build on one core)
+SAMPLE_SCALE = 20
+SAMPLE_SCALE_SEQ = 18
 
 
 def args_():
@@ -52,6 +57,8 @@ def args_():
     p.add_argument("--serve-rate", type=float, default=200.0)
     p.add_argument("--serve-pool", type=int, default=256)
     p.add_argument("--serve-slots", type=int, default=64)
+    p.add_argument("--cpu-oracle-child", nargs=4, default=None, metavar=("KIND", "SIZE", "ALGO", "THREADS"),
+                   help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -106,7 +113,7 @@ def workload_spec(a):
                  "symmetrised, deduplicated, loops dropped, unit weights, seed 1")
     if a.workload == "chunglu":
         return {"name": "chunglu16m_plmr", "algo": "plm", "refine": True, "graph": ("chunglu", CHUNGLU_N),
-                "sample": ("chunglu", 1 << 17),
+                "sample": ("chunglu", 1 << 19), "sample_seq": ("chunglu", 1 << 17),
                 "metric": "PLMR edges/s (Chung-Lu 16M, exponent 2.1, degrees 4..1e5, weights 1..100, complete run)",
                 "desc": f"Chung-Lu n={CHUNGLU_N}, degree exponent 2.1, expected degrees in [4, 1e5], integer "
                         "weights uniform in 1..100, seeded permutation, deduplicated, loops dropped, seed 1",
@@ -114,13 +121,14 @@ def workload_spec(a):
     if a.workload == "epp":
         return {"name": f"rmat{EPP_SCALE}_ef16_epp{EPP_B}", "algo": "epp", "refine": False,
                 "graph": ("rmat", EPP_SCALE), "sample": ("rmat", SAMPLE_SCALE),
+                "sample_seq": ("rmat", SAMPLE_SCALE_SEQ),
                 "metric": f"EPP edges/s (R-MAT scale {EPP_SCALE} ef16, {EPP_B} PLP bases, core clustering, "
                           "final PLM, complete run)",
                 "desc": rmat_desc.format(s=EPP_SCALE),
                 "alg": f"EPP (Algorithm 5): {EPP_B} PLP bases (seeds 1..{EPP_B}) in one batched launch, exact core "
                        "communities, coarsening, PLM on the core graph, prolongation"}
     return {"name": f"rmat{a.scale}_ef16_plm", "algo": "plm", "refine": False, "graph": ("rmat", a.scale),
-            "sample": ("rmat", SAMPLE_SCALE),
+            "sample": ("rmat", SAMPLE_SCALE), "sample_seq": ("rmat", SAMPLE_SCALE_SEQ),
             "metric": f"PLM edges/s (R-MAT scale {a.scale} ef16, complete run incl. all levels)",
             "desc": rmat_desc.format(s=a.scale), "alg": "PLM (Algorithms 2-3), colour-class schedule, seed 1"}
 
@@ -189,29 +197,50 @@ class ClockSampler:
 # CPU baseline: the oracle on a bounded sample of the workload
 # ---------------------------------------------------------------------------
 
-def oracle_call(wl, rp, c, w):
+def oracle_call(algo, refine, rp, c, w, threads):
     from oracle import oracle
-    if wl["algo"] == "epp":
-        return oracle.epp(rp, c, w, b=EPP_B, final_refine=wl["refine"], seed=1)
-    return oracle.plm(rp, c, w, refine=wl["refine"], seed=1)
+    if algo == "epp":
+        return oracle.epp(rp, c, w, b=EPP_B, final_refine=refine, seed=1, threads=threads)
+    return oracle.plm(rp, c, w, refine=refine, seed=1, threads=threads)
 
 
-def oracle_sample_rate(wl):
+def cpu_oracle_child(a):
+    """Runs in a fresh process (no CUDA, no torch thread pool): one complete
+    oracle run on the sample graph; prints {"m", "n", "s", "modularity",
+    "threads"} as JSON."""
     from oracle import oracle
+    kind, size, algo, threads = a.cpu_oracle_child
     oracle.build()
-    g = make_graph(*wl["sample"], "cpu")
+    g = make_graph(kind, int(size), "cpu")
     rp, c, w = g.numpy()
+    threads = int(threads)
+    used = oracle.threads_used(threads)
+    refine = algo.endswith("r")
     t = time.perf_counter()
-    r = oracle_call(wl, rp, c, w)
+    r = oracle_call(algo.rstrip("r"), refine, rp, c, w, threads)
     dt = time.perf_counter() - t
-    return g.m / dt, dt, g, r
+    print(json.dumps({"m": g.m, "n": g.n, "s": dt, "modularity": r.modularity, "threads": used}), flush=True)
 
 
-def sample_desc(wl, g):
-    kind, size = wl["sample"]
+def oracle_sample_rate(wl, sample, threads):
+    """(edges/s, seconds, child record) of one complete oracle run on the
+    sample graph, in a child process started by exec (never a fork of this
+    CUDA process).  threads 0: the OpenMP build on every host core."""
+    kind, size = sample
+    algo = wl["algo"] + ("r" if wl["refine"] else "")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-oracle-child", kind, str(size), algo,
+                          str(threads)], capture_output=True, text=True, check=True, cwd=ROOT)
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    return rec["m"] / rec["s"], rec["s"], rec
+
+
+def sample_desc(wl, sample, rec):
+    kind, size = sample
     what = f"R-MAT scale {size} ef16" if kind == "rmat" else f"Chung-Lu n={size}"
-    return (f"one complete sequential oracle {wl['algo'].upper()}{'R' if wl['refine'] else ''} run on {what} "
-            f"(same generator and parameters; n={g.n}, m={g.m})")
+    build = (f"OpenMP oracle build on {rec['threads']} host threads (colour classes decided in parallel, "
+             "results identical to the sequential oracle)") if rec["threads"] > 1 else "sequential oracle, 1 core"
+    return (f"one complete oracle {wl['algo'].upper()}{'R' if wl['refine'] else ''} run on {what} "
+            f"(same generator and parameters; n={rec['n']}, m={rec['m']}), {build}")
 
 
 def cpu_model():
@@ -229,9 +258,15 @@ def cpu_model():
 
 
 def cpu_baseline_obj(wl):
-    rate, dt, g, r = oracle_sample_rate(wl)
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": sample_desc(wl, g) + f"; {dt:.1f} s, modularity {r.modularity:.4f}",
+    rate, dt, rec = oracle_sample_rate(wl, wl["sample"], 0)
+    rate1, dt1, rec1 = oracle_sample_rate(wl, wl["sample_seq"], 1)
+    return {"value": rate, "unit": UNIT, "cores": rec["threads"], "kind": "oracle",
+            "sample": sample_desc(wl, wl["sample"], rec) + f"; {dt:.1f} s, modularity {rec['modularity']:.4f}",
+            "sample_graph": {"n": rec["n"], "m": rec["m"]},
+            "single_core": {"value": rate1, "unit": UNIT, "cores": 1,
+                            "sample": sample_desc(wl, wl["sample_seq"], rec1)
+                            + f"; {dt1:.1f} s, modularity {rec1['modularity']:.4f}",
+                            "sample_graph": {"n": rec1["n"], "m": rec1["m"]}},
             "cpu": cpu_model(), "nproc": os.cpu_count()}
 
 
@@ -240,25 +275,36 @@ def cpu_baseline_obj(wl):
 # ---------------------------------------------------------------------------
 
 def run_reference(a):
+    """The oracle arm: every step is one complete run of the OpenMP oracle on
+    every host core on the bounded sample graph (the workload's generator at
+    a smaller scale, named in the line).  Warm-up steps run the same build on
+    a small graph of the same family (they load the library and start the
+    thread pool)."""
     rank, local, world = dist_env()
     if rank != 0:
         return
     wl = workload_spec(a)
     times = []
-    rate = None
+    rec = None
+    warm = (wl["sample"][0], 14 if wl["sample"][0] == "rmat" else 1 << 14)
     for i in range(a.warmup + a.steps):
-        rate, dt, g, r = oracle_sample_rate(wl)
-        if i >= a.warmup:
-            times.append(dt)
+        if i < a.warmup:
+            oracle_sample_rate(wl, warm, 0)
+            continue
+        rate, dt, rec = oracle_sample_rate(wl, wl["sample"], 0)
+        times.append(dt)
     tot = sum(times)
-    value = g.m * len(times) / tot
+    value = rec["m"] * len(times) / tot
+    cfg = workload_config(wl, None)
+    cfg["cpu_sample"] = {"graph": sample_desc(wl, wl["sample"], rec), "n": rec["n"], "m": rec["m"]}
     line = {
         "impl": "reference", "metric": wl["metric"], "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * tot / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": workload_config(wl, None),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step: " + sample_desc(wl, g),
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": rec["threads"], "kind": "oracle",
+                         "sample": "each step: " + sample_desc(wl, wl["sample"], rec),
+                         "sample_graph": {"n": rec["n"], "m": rec["m"]},
                          "cpu": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -269,18 +315,36 @@ def run_reference(a):
 # our arm
 # ---------------------------------------------------------------------------
 
+KERNEL_SOURCES = ("phase.cuh", "move_kernels.cuh", "barrier.cuh", "common.cuh")
+
+
+def kernel_sources_sha():
+    """SHA-256 (first 16 hex digits) of the move kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1304_4453_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profiles():
-    """Per-launch DRAM bytes of the decide kernels from the committed ncu
-    summary (a line 'traffic_bytes_per_launch: X'), else None."""
+    """Per-launch DRAM bytes of the move kernel from the committed ncu summary
+    (lines 'traffic_bytes_per_launch: X' and 'kernel_sources_sha: Y'), or None
+    when the kernel's sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", "move_phase_batch_rmat.md")
+    vals = {}
     try:
         for line in open(path):
-            if line.strip().startswith("traffic_bytes_per_launch:"):
-                v = line.split(":", 1)[1].strip()
-                return None if v in ("", "null", "None") else float(v)
+            for key in ("traffic_bytes_per_launch", "kernel_sources_sha"):
+                if line.strip().startswith(key + ":"):
+                    vals[key] = line.split(":", 1)[1].strip()
     except OSError:
-        pass
-    return None
+        return None
+    v = vals.get("traffic_bytes_per_launch")
+    if v in (None, "", "null", "None") or vals.get("kernel_sources_sha") != kernel_sources_sha():
+        return None
+    return float(v)
 
 
 def measured_hbm_peak():
@@ -336,15 +400,8 @@ def run_ours(a):
     l0 = cd.cd_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    k_ms = k_bytes = 0.0
-    k_launches = 0
-    stats = []
     for _ in range(a.steps):
-        mod, st, status = run(G.h, labels, opts_prof)
-        k_ms += st["k_ms"]
-        k_bytes += st["k_bytes"]
-        k_launches += st["k_launches"]
-        stats.append(st)
+        mod, st, status = run(G.h, labels, opts_plain)
     ev1.record(stream)
     torch.cuda.synchronize()
     ranks.barrier()
@@ -357,9 +414,27 @@ def run_ours(a):
     if a.profile_run:
         if rank == 0:
             print(json.dumps({"profile_run": True, "ms_per_step": ms, "modularity": mod,
-                              "gpu_launches": launches, "k_ms": k_ms, "k_bytes": k_bytes,
-                              "k_launches": k_launches}), flush=True)
+                              "gpu_launches": launches}), flush=True)
         return
+
+    # roofline pass, outside the timed region: the same steps with CUDA events
+    # around every persistent launch (profile mode)
+    k_ms = k_bytes = 0.0
+    k_launches = 0
+    stats = []
+    prof_steps = max(1, min(a.steps, 5))
+    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(prof_steps):
+        mod_p, st, status = run(G.h, labels, opts_prof)
+        k_ms += st["k_ms"]
+        k_bytes += st["k_bytes"]
+        k_launches += st["k_launches"]
+        stats.append(st)
+    ev3.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = ev2.elapsed_time(ev3) / prof_steps
+
 
     # end to end through the public API with host buffers: H2D of the CSR,
     # graph creation, PLM, D2H of the labels, every step
@@ -380,6 +455,31 @@ def run_ours(a):
     e2e_ok = bool(torch.equal(lab_h, labels.cpu()))
     e2e_value, _ = ranks.rate(g.m, statistics.median(e2e_t))
 
+    # the racy schedule (the paper's parallel loop on live data, Sections
+    # III-A and III-B, cut into hash rounds; not deterministic): same graph
+    # and algorithm, outside the timed region
+    racy = None
+    if wl["algo"] == "plm":
+        opts_racy = cd.default_opts(seed=1, racy=True)
+        run(G.h, labels, opts_racy)
+        r_steps = max(1, min(a.steps, 3))
+        r_mods, r_sweeps = [], []
+        ev4, ev5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev4.record(stream)
+        for _ in range(r_steps):
+            m_r, st_r, status_r = run(G.h, labels, opts_racy)
+            r_mods.append(m_r)
+            r_sweeps.append(st_r["sweeps"])
+        ev5.record(stream)
+        torch.cuda.synchronize()
+        r_ms = ev4.elapsed_time(ev5) / r_steps
+        racy = {"edges_per_s": ranks.rate(g.m, r_ms / 1000.0)[0], "ms_per_run": r_ms,
+                "modularity": r_mods, "sweeps": r_sweeps, "rounds": cd.RACY_ROUNDS,
+                "deterministic_modularity": mod, "speedup_vs_deterministic": ms / r_ms,
+                "how": f"{r_steps} complete runs with cd_opts.schedule = {cd.RACY_ROUNDS} (no colouring; hash "
+                       "rounds decide on live data in the first four sweeps of a move phase, later sweeps "
+                       "re-check wanted moves with neighbour stamps); results vary between runs"}
+
     # one PLP run on the same graph (context, outside the timed region)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -399,7 +499,10 @@ def run_ours(a):
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
             "launches_timed": k_launches, "avg_launch_us": 1000.0 * k_ms / max(k_launches, 1),
             "alg_bytes_per_launch": k_bytes / max(k_launches, 1),
-            "share_of_step": k_ms / (ms * a.steps) if ms > 0 else None}
+            "share_of_step": k_ms / (prof_ms * prof_steps) if prof_ms > 0 else None,
+            "timed_in": f"a separate pass of {prof_steps} steps with CUDA events around every persistent "
+                        f"launch ({prof_ms:.1f} ms per step there, against {ms:.1f} ms in the timed region)",
+            "kernel_sources_sha": kernel_sources_sha()}
 
     if rank != 0:
         return
@@ -420,6 +523,7 @@ def run_ours(a):
                                          "recheck": st["stage_recheck_ms"]}},
         "plp": {"edges_per_s": g.m / plp_s, "modularity": plp_mod, "iters": plp_st["iters"],
                 "communities": plp_st["ncomm"]},
+        "racy": racy,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz + (0 if g.w is None else 4 * g.nnz),
                 "d2h_bytes_per_step": 4 * g.n, "labels_match_device_run": e2e_ok},
@@ -761,6 +865,9 @@ def run_reference_other(a):
 
 def main():
     a = args_()
+    if a.cpu_oracle_child:
+        cpu_oracle_child(a)
+        return
     if a.impl == "reference":
         if a.workload in ("plm", "chunglu", "epp"):
             run_reference(a)

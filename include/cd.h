@@ -79,6 +79,35 @@ enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1 };
  *               memory, above -> multi-block hub path.  Limits may not exceed
  *               4, 16, 128, 1024, 4096 and must not decrease (0 keeps the
  *               default).  Speed only, never results.
+ *   res_num, res_den  the resolution gamma = res_num / res_den of Section
+ *               III-B, read as a factor on the volume term of the move gain:
+ *               the moves maximise sum_C omega(C)/W - gamma vol(C)^2/(4W^2)
+ *               (gamma 0: one community per connected component, 1:
+ *               modularity, 2W and above: singletons).  The gain stays an
+ *               exact integer, 2W res_den (omega(u,D) - omega(u,C\u)) -
+ *               res_num vol(u) (vol(D) - vol(C\u)).  res_num >= 0,
+ *               res_den >= 1, reduced by their gcd, and max(res_num,
+ *               res_den) (2W)^2 < 2^126, else CD_EINVAL; (0, 0) means 1 / 1.
+ *               The reported modularity is always the standard one (gamma 1).
+ *               PLP ignores it.
+ *   schedule    0 (default): the deterministic colour-class schedule, results
+ *               identical to the sequential oracle.  R in 1..4096: the
+ *               paper's racy schedule (Sections III-A, III-B) for the PLM
+ *               move phases, cut into R rounds: no colouring; a seeded hash
+ *               splits the vertices into R rounds, and adjacent vertices may
+ *               share one.  In the first four sweeps of a phase every vertex
+ *               of a round decides in parallel on the labels and community
+ *               volumes as they are at that moment and applies its move at
+ *               once.  Later sweeps decide on the round's starting state and
+ *               re-check the wanted moves one by one in vertex order; a move
+ *               waits for the next sweep when an earlier move of the round
+ *               left or entered its current or target community, so every
+ *               applied move raises the objective and the phase terminates.
+ *               Results depend on the timing of the threads in the first
+ *               sweeps and may differ between runs; they are valid partitions
+ *               with their exact modularity.  The level loop also stops when
+ *               coarsening no longer merges vertices.  PLP and EPP's base runs
+ *               keep the colour classes.  128 rounds are the binding's default.
  * cd_tune picks team_quantum, team_min and bin_max by measurement. */
 typedef struct {
     uint64_t seed;
@@ -90,6 +119,10 @@ typedef struct {
     int32_t team_min;
     int32_t reserved;   /* 0 */
     int32_t bin_max[5];
+    int64_t res_num;    /* resolution gamma = res_num / res_den of PLM / PLMR */
+    int64_t res_den;    /*   and of EPP's final phase (1 / 1: modularity) */
+    int32_t schedule;   /* 0: colour classes (deterministic); R >= 1: racy, R rounds */
+    int32_t reserved2;  /* 0 */
 } cd_opts;
 
 /* Run statistics (all optional: pass NULL to skip). */
@@ -315,13 +348,15 @@ cd_status cd_debug_plan_launch(const int64_t *work, int count, int64_t team_quan
 
 /* Diagnostic: the class trace of the move phases (Algorithm 2 under the
  * colour-class schedule) run with opts.profile = 2 since the last call.  One
- * row of nine int64 per class step, in completion order: phase number, sweep,
- * colour class, its vertices, its adjacency entries, its hub aggregation
- * chunks, its hub decide slices, its hubs above 4096 neighbours, and the wall
- * time in ns on the team's first block from the previous class's barrier to
- * this class's barrier.  With out == NULL only *count (rows) is set; then
- * out[9 * count] receives the rows (cap = rows the buffer holds) and the
- * trace is cleared.  Errors: CD_EINVAL. */
+ * row of twelve int64 per class step, in completion order: phase number,
+ * sweep, colour class, its vertices, its adjacency entries, its hub
+ * aggregation chunks, its hub decide slices, its hubs above 4096 neighbours,
+ * the wall time in ns on the team's first block from the previous class's
+ * barrier to this class's barrier, and the latest times (ns after that
+ * start, 0 when absent) at which a block finished its work items, its hub
+ * decide slices, and the class finisher its work.  With out == NULL only
+ * *count (rows) is set; then out[12 * count] receives the rows (cap = rows
+ * the buffer holds) and the trace is cleared.  Errors: CD_EINVAL. */
 cd_status cd_debug_class_trace(int64_t *out, int64_t cap, int64_t *count);
 
 #ifdef __cplusplus

@@ -971,14 +971,17 @@ int64_t or_coarsen(int64_t n, const int64_t *rp, const int32_t *col, const int64
 
 /* EPP (Algorithm 5): b PLP base runs (seed + i), exact core communities,
  * coarsen, final PLM or PLMR (final_refine) on the core graph, prolong.
+ * The final phase optimises the resolution res_num / res_den (PLP has none).
  * base_out [b*n] and core_out [n] are optional. */
 int or_epp(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
            int b, int final_refine, uint64_t seed, int32_t max_sweeps, int32_t max_levels,
-           double theta, int32_t max_iter, int32_t *labels, int32_t *base_out,
-           int32_t *core_out, double *mod, int64_t *stats)
+           double theta, int32_t max_iter, int64_t res_num, int64_t res_den,
+           int32_t *labels, int32_t *base_out, int32_t *core_out, double *mod, int64_t *stats)
 {
     OG g;
+    if (res_num < 0 || res_den < 1) return -2;
     if (og_from_input(&g, n, rp, col, w)) return -1;
+    if (og_set_resolution(&g, res_num, res_den)) { og_free(&g); return -2; }
     int64_t st[ST_N] = {0};
     st[ST_CONVERGED] = 1;
     int32_t *base = (int32_t *)malloc(((size_t)b * n + 1) * sizeof(int32_t));

@@ -77,7 +77,7 @@ def lib(threads: int = 1):
             L.or_coarsen.argtypes = [i64, P, P, P, P, P, P, P, P]
             L.or_coarsen.restype = i64
             L.or_epp.argtypes = [i64, P, P, P, ctypes.c_int, ctypes.c_int, u64, i32, i32,
-                                 dbl, i32, P, P, P, P, P]
+                                 dbl, i32, i64, i64, P, P, P, P, P]
             L.or_positive_moves.argtypes = [i64, P, P, P, P, i64, i64, P]
             L.or_positive_moves.restype = i64
             L.or_set_threads.argtypes = [ctypes.c_int]
@@ -242,7 +242,7 @@ def coarsen(row_ptr, col, w, labels):
 
 def epp(row_ptr, col, w, b=4, final_refine=True, seed=1, theta=None,
         max_sweeps=MAX_SWEEPS, max_levels=MAX_LEVELS, max_iter=MAX_PLP_ITERS,
-        want_parts=False, threads=1):
+        want_parts=False, threads=1, resolution=(1, 1)):
     g = _CSR(row_ptr, col, w)
     if theta is None:
         theta = g.n * 1e-5
@@ -251,9 +251,13 @@ def epp(row_ptr, col, w, b=4, final_refine=True, seed=1, theta=None,
     core = np.zeros(max(g.n, 1), np.int32) if want_parts else None
     mod = ctypes.c_double()
     st = np.zeros(len(STATS), np.int64)
-    if lib(threads).or_epp(*g.args(), b, int(final_refine), seed, max_sweeps, max_levels,
-                    float(theta), max_iter, _ptr(z), _ptr(base), _ptr(core),
-                    ctypes.byref(mod), _ptr(st)):
+    p, q = resolution
+    rc = lib(threads).or_epp(*g.args(), b, int(final_refine), seed, max_sweeps, max_levels,
+                             float(theta), max_iter, int(p), int(q), _ptr(z), _ptr(base), _ptr(core),
+                             ctypes.byref(mod), _ptr(st))
+    if rc == -2:
+        raise ValueError("resolution must be p >= 0, q >= 1, max(p, q) (2W)^2 < 2^126")
+    if rc:
         raise MemoryError
     r = Result(z[:g.n], mod.value, _stats(st))
     if want_parts:

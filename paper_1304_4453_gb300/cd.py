@@ -38,7 +38,8 @@ class cd_opts(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("team_quantum", ctypes.c_int64),
                 ("team_min", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("bin_max", ctypes.c_int32 * 5)]
+                ("bin_max", ctypes.c_int32 * 5), ("res_num", ctypes.c_int64), ("res_den", ctypes.c_int64),
+                ("schedule", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class cd_stats(ctypes.Structure):
@@ -164,12 +165,20 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
+RACY_ROUNDS = 128
+
+
 def default_opts(seed: int = 1, max_sweeps: int = 256, max_levels: int = 64,
                  max_iters: int = 1000, profile: bool = False, team_quantum: int = 0,
-                 team_min: int = 0, bin_max=None) -> cd_opts:
+                 team_min: int = 0, bin_max=None, resolution=(1, 1), racy=False) -> cd_opts:
+    """Options; resolution = (p, q) is gamma = p / q of the PLM move gain;
+    racy selects the paper's nondeterministic schedule (no colouring): True
+    for RACY_ROUNDS hash rounds per sweep, or an int for that many."""
     o = cd_opts()
     lib().cd_opts_default(ctypes.byref(o))
     o.seed, o.max_sweeps, o.max_levels, o.max_iters, o.profile = seed, max_sweeps, max_levels, max_iters, int(profile)
+    o.res_num, o.res_den = int(resolution[0]), int(resolution[1])
+    o.schedule = (RACY_ROUNDS if racy is True else int(racy)) if racy else 0
     if team_quantum:
         o.team_quantum = team_quantum
     if team_min:
@@ -273,7 +282,8 @@ def cd_debug_fail_alloc(k: int):
     lib().cd_debug_fail_alloc(int(k))
 
 
-TRACE_FIELDS = ("phase", "sweep", "cls", "vertices", "entries", "hub_chunks", "hub_slices", "big_hubs", "ns")
+TRACE_FIELDS = ("phase", "sweep", "cls", "vertices", "entries", "hub_chunks", "hub_slices", "big_hubs", "ns",
+                "items_end_ns", "decide_end_ns", "finisher_end_ns")
 
 
 def cd_debug_class_trace() -> np.ndarray:

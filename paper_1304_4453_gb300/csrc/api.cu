@@ -70,6 +70,10 @@ void cd_opts_default(cd_opts *o) {
     o->team_min = 8;
     o->reserved = 0;
     for (int i = 0; i < NLIM; i++) o->bin_max[i] = BIN_DEFAULT[i];
+    o->res_num = 1;
+    o->res_den = 1;
+    o->schedule = 0;
+    o->reserved2 = 0;
 }
 
 const char *cd_status_str(cd_status s) {

@@ -42,6 +42,24 @@ inline RunOpts to_run(const cd_opts *o) {
     r.max_iters = o->max_iters;
     r.profile = o->profile != 0;
     r.trace = o->profile >= 2;
+    int64_t rp_ = o->res_num, rq_ = o->res_den;
+    if (rp_ == 0 && rq_ == 0) rp_ = rq_ = 1;
+    if (rp_ < 0 || rq_ < 1) raise(CD_EINVAL, "resolution %lld / %lld: need res_num >= 0, res_den >= 1",
+                                  (long long)o->res_num, (long long)o->res_den);
+    for (int64_t a = rp_, b = rq_;;) {   // reduce by the gcd (same decisions, smaller products)
+        if (b == 0) {
+            if (a > 1) { rp_ /= a; rq_ /= a; }
+            break;
+        }
+        const int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    r.res_p = rp_;
+    r.res_q = rq_;
+    if (o->schedule < 0 || o->schedule > 4096)
+        raise(CD_EINVAL, "schedule %d: 0 (colour classes) or 1..4096 (racy rounds per sweep)", o->schedule);
+    r.racy = o->schedule;
     r.team_quantum = o->team_quantum;
     r.team_min = o->team_min;
     for (int i = 0; i < NLIM; i++) {

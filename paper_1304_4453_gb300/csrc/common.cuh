@@ -136,6 +136,22 @@ struct GraphView {
 // 2^31; otherwise the 128-bit path is used.
 inline bool needs_big(int64_t W) { return 2 * W >= (int64_t(1) << 31); }
 
+// With a resolution gamma = p/q (Section III-B; p/q reduced) both products of
+// the gain are bounded by max(p, q) (2W)^2: the 64-bit path needs that bound
+// below 2^63 as well, and no path takes a bound of 2^126 or more
+// (gain_fits_128 false: the caller rejects the resolution).
+inline bool gain_needs_big(int64_t W, int64_t p, int64_t q) {
+    if (needs_big(W)) return true;
+    const unsigned __int128 w2 = (unsigned __int128)(2 * W) * (unsigned __int128)(2 * W);
+    const unsigned __int128 m = (unsigned __int128)(p > q ? p : q);
+    return w2 > 0 && m * w2 >= ((unsigned __int128)1 << 63);
+}
+inline bool gain_fits_128(int64_t W, int64_t p, int64_t q) {
+    const unsigned __int128 w2 = (unsigned __int128)(2 * W) * (unsigned __int128)(2 * W);
+    const unsigned __int128 m = (unsigned __int128)(p > q ? p : q);
+    return w2 == 0 || m <= (((unsigned __int128)1 << 126) - 1) / w2;
+}
+
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------

@@ -125,10 +125,26 @@ static void upload_class_meta(Schedule &S, const std::vector<int32_t> &it0, cons
     CD_CUDA(cudaStreamSynchronize(s));   // the host vectors may change after return
 }
 
-static void build_schedule(const GraphView &g, uint64_t seed, const BinLimits &bins, Schedule &S, cudaStream_t s) {
+__global__ void k_hash_rounds(int64_t n, uint32_t salt, int32_t rounds, int32_t *color) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        color[i] = (int32_t)(fmix32((uint32_t)i ^ salt) % (uint32_t)rounds);
+}
+
+// racy > 0: no colouring; the vertices are split into `racy` rounds by a
+// seeded hash, adjacent vertices may share a round (the paper's parallel
+// loop on live data, Section III-B, with the loop cut into rounds so that a
+// vertex sees the moves of earlier rounds).
+static void build_schedule(const GraphView &g, uint64_t seed, const BinLimits &bins, Schedule &S, cudaStream_t s,
+                           int32_t racy = 0) {
     const int64_t n = g.n;
     DBuf<int32_t> color(n, s);
-    S.ncol = color_graph(g, seed, color.p, s);
+    if (racy > 0) {
+        if (n) { k_hash_rounds<<<grid_for(n, kBlock, 152 * 32), kBlock, 0, s>>>(n, fmix32(seed_word(seed) ^ 0x52414359u), racy, color.p); ::cd::note_launch(); }
+        CD_LAUNCH_CHECK();
+        S.ncol = n ? racy : 0;
+    } else {
+        S.ncol = color_graph(g, seed, color.p, s);
+    }
     const int64_t nbk = (int64_t)S.ncol * NBINS + 1;
     S.order.alloc(n, s);
     S.off.assign(nbk + 1, 0);
@@ -317,7 +333,7 @@ struct PhaseRun {
     DBuf<int32_t> cstamp;             // re-check community stamps
     DBuf<unsigned int> dz_n;
     // class trace (RunOpts::trace): timestamps and the per-class sizes
-    DBuf<unsigned long long> cls_ns;
+    DBuf<unsigned long long> cls_ns, cls_stage;
     std::vector<int64_t> cls_info;    // per class: vertices, entries, hub chunks, hub slices, relaxed hubs
     // set by the engine after the launch
     double launch_ms = 0, wall_ms = 0;
@@ -421,6 +437,9 @@ static void prepare_trace(PhaseRun &r, const GraphView &g, const Schedule &S, cu
     r.cls_ns.alloc((size_t)r.cap * ncol + 1, s);
     r.cls_ns.zero();
     r.a.class_ns = r.cls_ns.p;
+    r.cls_stage.alloc((size_t)r.cap * ncol * 3 + 1, s);
+    r.cls_stage.zero();
+    r.a.stage_max = r.cls_stage.p;
     const int64_t listed = S.off[(size_t)ncol * NBINS];
     std::vector<int32_t> order((size_t)listed);
     std::vector<int64_t> rp((size_t)g.n + 1);
@@ -443,8 +462,10 @@ static void prepare_trace(PhaseRun &r, const GraphView &g, const Schedule &S, cu
 
 static void record_trace(PhaseRun &r, int32_t runs, cudaStream_t s) {
     const int64_t ncol = r.a.ncol;
-    std::vector<unsigned long long> t((size_t)runs * ncol + 1);
+    std::vector<unsigned long long> t((size_t)runs * ncol + 1), sm((size_t)runs * ncol * 3 + 1);
     CD_CUDA(cudaMemcpyAsync(t.data(), r.cls_ns.p, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaMemcpyAsync(sm.data(), r.cls_stage.p, sm.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            s));
     CD_CUDA(cudaStreamSynchronize(s));
     std::lock_guard<std::mutex> lk(g_trace_mu);
     const int64_t ph = g_trace_phase++;
@@ -454,7 +475,11 @@ static void record_trace(PhaseRun &r, int32_t runs, cudaStream_t s) {
             const unsigned long long x = t[1 + sw * ncol + k];
             if (x == 0) continue;
             const int64_t *ci = &r.cls_info[(size_t)k * 5];
-            const int64_t row[TRACE_FIELDS] = {ph, sw, k, ci[0], ci[1], ci[2], ci[3], ci[4], (int64_t)(x - prev)};
+            const unsigned long long *q = &sm[(size_t)(sw * ncol + k) * 3];
+            // stage ends relative to the class start (0: the stage did not run)
+            auto rel = [&](unsigned long long y) { return y > prev ? (int64_t)(y - prev) : (int64_t)0; };
+            const int64_t row[TRACE_FIELDS] = {ph, sw, k, ci[0], ci[1], ci[2], ci[3], ci[4], (int64_t)(x - prev),
+                                               rel(q[0]), rel(q[1]), rel(q[2])};
             g_trace.insert(g_trace.end(), row, row + TRACE_FIELDS);
             prev = x;
         }
@@ -481,7 +506,10 @@ static std::unique_ptr<PhaseRun> prepare_move(const GraphView &g, const Schedule
     const int64_t n = g.n, ncol = S.ncol;
     r->plp = false;
     r->wk = g.wk;
-    r->big = needs_big(g.W);
+    if (!gain_fits_128(g.W, o.res_p, o.res_q))
+        raise(CD_EINVAL, "resolution %lld / %lld: max(p, q) (2W)^2 reaches 2^126 for 2W = %lld",
+              (long long)o.res_p, (long long)o.res_q, (long long)(2 * g.W));
+    r->big = gain_needs_big(g.W, o.res_p, o.res_q);
     r->profile = o.profile;
     r->work = g.nnz + n;
     r->quantum = o.team_quantum;
@@ -533,6 +561,9 @@ static std::unique_ptr<PhaseRun> prepare_move(const GraphView &g, const Schedule
     a.ubits = ubits;
     a.max_sweeps = o.max_sweeps;
     a.recheck_from = RECHECK_FROM;
+    a.res_p = o.res_p;
+    a.res_q = o.res_q;
+    a.racy = o.racy > 0 ? 1 : 0;
     if (o.trace) prepare_trace(*r, g, S, s);
     return r;
 }
@@ -542,6 +573,7 @@ static int64_t finish_move(PhaseRun &r, RunStats &st, cudaStream_t s) {
     int32_t conv = 0;
     std::vector<Counters> per;
     const int32_t runs = read_counters(r, &conv, per, st, s);
+    if (r.a.g.n == 0) return 0;   // an empty graph runs no sweep (nothing to decide)
     if (r.cls_ns.p) record_trace(r, runs, s);
     int64_t total = 0;
     for (const Counters &h : per) {
@@ -705,7 +737,7 @@ static void start_level(Job &j, cudaStream_t s) {
     JobState &x = *j.state;
     Level &lv = *x.L.back();
     auto t = Clock::now();
-    build_schedule(lv.g, j.spec.o.seed, j.spec.o.bins, lv.S, s);
+    build_schedule(lv.g, j.spec.o.seed, j.spec.o.bins, lv.S, s, j.spec.o.racy);
     j.st.ms_color += ms_since(t);
     if (x.L.size() == 1 && j.st.colors0 < 0) j.st.colors0 = lv.S.ncol;
     lv.zeta.alloc(lv.g.n, s);
@@ -737,7 +769,7 @@ static void advance_impl(Job &j, cudaStream_t s) {
                 Level &lv = *x.L[0];
                 lv.g = sp.g;
                 auto t = Clock::now();
-                build_schedule(sp.g, sp.o.seed, sp.o.bins, lv.S, s);
+                build_schedule(sp.g, sp.o.seed, sp.o.bins, lv.S, s);   // PLP keeps the colour classes
                 st.ms_color += ms_since(t);
                 if (st.colors0 < 0) st.colors0 = lv.S.ncol;
                 x.run = prepare_plp(sp.g, lv.S, j.labels(), sp.o.seed, sp.theta, sp.o, s);
@@ -802,7 +834,8 @@ static void advance_impl(Job &j, cudaStream_t s) {
             const int64_t moved = finish_move(*x.run, st, s);
             x.run.reset();
             if (moved == 0 || (int)x.L.size() >= sp.o.max_levels) {
-                st.levels += (int32_t)x.L.size();
+                // an empty graph has no level that ran a move phase
+                st.levels += lv.g.n > 0 ? (int32_t)x.L.size() : 0;
                 st.ncomm = (int32_t)compact_labels(lv.zeta.p, lv.g.n, s);
                 x.up = (int)x.L.size() - 2;
                 x.stage = ST_UP;
@@ -812,9 +845,20 @@ static void advance_impl(Job &j, cudaStream_t s) {
             lv.rank.alloc(lv.g.n, s);
             auto nx = std::make_unique<Level>();
             coarsen_graph(lv.g, lv.zeta.p, lv.rank.p, nx->own, s);
+            st.ms_coarsen += ms_since(t);
+            if (sp.o.racy > 0 && nx->own.view.n == lv.g.n) {
+                // the racy schedule's moves only exchanged labels (every community
+                // is still one vertex): no coarser level, this one is the deepest
+                nx.reset();
+                lv.rank.release();
+                st.levels += (int32_t)x.L.size();
+                st.ncomm = (int32_t)compact_labels(lv.zeta.p, lv.g.n, s);
+                x.up = (int)x.L.size() - 2;
+                x.stage = ST_UP;
+                break;
+            }
             nx->g = nx->own.view;
             x.L.push_back(std::move(nx));
-            st.ms_coarsen += ms_since(t);
             start_level(j, s);
             return;
         }

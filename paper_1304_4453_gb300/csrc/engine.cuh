@@ -28,6 +28,8 @@ struct RunOpts {
     int32_t max_sweeps = 256, max_levels = 64, max_iters = 1000;
     bool profile = false;
     bool trace = false;          // profile level 2: per-class times of the move phases
+    int64_t res_p = 1, res_q = 1;   // PLM resolution gamma = res_p / res_q (reduced)
+    int32_t racy = 0;            // > 0: the racy schedule with this many hash rounds per sweep (not deterministic)
     int64_t team_quantum = int64_t(1) << 18;   // launch shape (speed only)
     int32_t team_min = 8;
     BinLimits bins{{4, 16, 128, BLK_MAXDEG, BLK_MAXDEG}};  // schedule degree bins (speed only)
@@ -127,7 +129,10 @@ void run_epp(const GraphView &g, int b, bool final_refine, const RunOpts &o, dou
 
 // Class trace of the move phases run with RunOpts::trace (profile level 2):
 // TRACE_FIELDS int64 per class step, appended in completion order.
-constexpr int TRACE_FIELDS = 9;   // phase, sweep, class, vertices, entries, hub chunks, hub slices, hubs > HUB_RELAX, ns
+// phase, sweep, class, vertices, entries, hub chunks, hub slices, hubs >
+// HUB_RELAX, ns, then the latest end of the items, the hub-decide slices and
+// the finisher's work, in ns from the class start (0: stage absent)
+constexpr int TRACE_FIELDS = 12;
 std::vector<int64_t> take_class_trace();
 
 }  // namespace cd

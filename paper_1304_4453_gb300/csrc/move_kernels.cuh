@@ -79,6 +79,11 @@ struct Counters {              // per sweep / iteration, device
     unsigned long long wanted, moved, entries, candidates, decisions;
     unsigned long long overflow;   // hash-table probes that found no slot (must stay 0)
 };
+// A block sums its share of the first five counters in shared memory
+// (SweepCtx::bcnt, in this order) and adds it to the sweep's Counters once,
+// before the barrier that ends the sweep: thousands of warps adding to one
+// record directly would serialise on a single cache line.
+enum { BC_WANTED = 0, BC_MOVED, BC_ENTRIES, BC_CAND, BC_DEC, BC_N };
 
 struct HubInfo {               // one hub vertex of a class
     int32_t v;
@@ -107,6 +112,7 @@ struct SliceDesc {             // one decide slice of a hub's occupied-slot list
 
 struct SweepCtx {
     GraphView g;
+    int64_t res_p, res_q;      // PLM resolution gamma = res_p / res_q (Section III-B); 1 / 1: modularity
     int32_t *zeta;
     // class layout
     const int32_t *order;      // class vertices, bin by bin
@@ -114,7 +120,8 @@ struct SweepCtx {
     int32_t bend[NBINS];       // exclusive end block of each role
     int32_t *gt_keys;          // this block's role-3b table (all -1 between uses)
     void *gt_vals;             //   values (all 0 between uses)
-    Counters *cnt;
+    Counters *cnt;             // the sweep's counters (overflow only; see bcnt)
+    unsigned long long *bcnt;  // this block's counter sums of the sweep (shared memory, BC_*)
     // PLM
     const int64_t *volc;       // volumes at class start (read)
     int64_t *volw;             // early sweeps: volumes after this class (write)
@@ -132,6 +139,8 @@ struct SweepCtx {
     // PLP
     uint8_t *active;
     uint32_t tie_salt;
+    int32_t racy;              // racy schedule: adjacent vertices share rounds, so a hub's
+                               // activity may change during its round and every hub is evaluated
     // hubs of this class
     const HubInfo *hubs;
     const int32_t *hub_b1, *hub_b2;      // exclusive prefix of hub blocks
@@ -275,18 +284,22 @@ struct PlpBest {
     }
 };
 
+// Gain of moving u from C to D times 2 W^2 q (Section III-B, Delta mod,
+// with the resolution gamma = p / q scaling the volume term):
+//   g = 2W q (omega(u,D) - omega(u,C\u)) - p vol(u) (vol(D) - vol(C\u)),
+// volC = vol(C) including u.  Exact in T: the host bounds max(p, q) (2W)^2.
 template <bool BIG>
-__device__ __forceinline__ typename GainT<BIG>::T plm_gain(int64_t twoW, int64_t wD, int64_t wC, int64_t vu,
-                                                           int64_t volD, int64_t volC) {
+__device__ __forceinline__ typename GainT<BIG>::T plm_gain(int64_t twoW, int64_t q, int64_t p, int64_t wD,
+                                                           int64_t wC, int64_t vu, int64_t volD, int64_t volC) {
     using T = typename GainT<BIG>::T;
-    return (T)twoW * (T)(wD - wC) - (T)vu * (T)(volD - volC + vu);
+    return (T)twoW * (T)q * (T)(wD - wC) - (T)p * (T)vu * (T)(volD - volC + vu);
 }
 
 template <bool BIG>
 using ValT = std::conditional_t<BIG, unsigned long long, unsigned int>;
 
-// Warp-wide sums of per-lane counters, one atomic per warp.
-__device__ __forceinline__ void add_counters(Counters *c, unsigned wanted, unsigned moved, unsigned entries,
+// Warp-wide sums of per-lane counters into the block's shared sums.
+__device__ __forceinline__ void add_counters(unsigned long long *bc, unsigned wanted, unsigned moved, unsigned entries,
                                              unsigned cand, unsigned dec) {
     wanted = __reduce_add_sync(0xffffffffu, wanted);
     moved = __reduce_add_sync(0xffffffffu, moved);
@@ -294,12 +307,26 @@ __device__ __forceinline__ void add_counters(Counters *c, unsigned wanted, unsig
     cand = __reduce_add_sync(0xffffffffu, cand);
     dec = __reduce_add_sync(0xffffffffu, dec);
     if ((threadIdx.x & 31) == 0) {
-        if (wanted) atomicAdd(&c->wanted, (unsigned long long)wanted);
-        if (moved) atomicAdd(&c->moved, (unsigned long long)moved);
-        if (entries) atomicAdd(&c->entries, (unsigned long long)entries);
-        if (cand) atomicAdd(&c->candidates, (unsigned long long)cand);
-        if (dec) atomicAdd(&c->decisions, (unsigned long long)dec);
+        if (wanted) atomicAdd(&bc[BC_WANTED], (unsigned long long)wanted);
+        if (moved) atomicAdd(&bc[BC_MOVED], (unsigned long long)moved);
+        if (entries) atomicAdd(&bc[BC_ENTRIES], (unsigned long long)entries);
+        if (cand) atomicAdd(&bc[BC_CAND], (unsigned long long)cand);
+        if (dec) atomicAdd(&bc[BC_DEC], (unsigned long long)dec);
     }
+}
+
+// Adds the block's sums to the sweep's counters and clears them (whole
+// block; the caller's next team barrier publishes the additions).
+__device__ __forceinline__ void flush_counters(unsigned long long *bc, Counters *dst) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long *d[BC_N] = {&dst->wanted, &dst->moved, &dst->entries, &dst->candidates, &dst->decisions};
+        for (int i = 0; i < BC_N; i++) {
+            if (bc[i]) atomicAdd(d[i], bc[i]);
+            bc[i] = 0;
+        }
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ void vol_add(int64_t *v, int32_t c, int64_t x) {
@@ -408,7 +435,7 @@ __device__ __forceinline__ void role_group(const SweepCtx &c, int64_t rb, const 
         for (int j = 0; j < SPL; j++)
             if (ky[j] >= 0 && ky[j] != C) {
                 const int64_t w = (int64_t)vals[gl + j * G];
-                b.offer(plm_gain<BIG>(twoW, w, wC, vu, vk[j], volC), ky[j], w);
+                b.offer(plm_gain<BIG>(twoW, c.res_q, c.res_p, w, wC, vu, vk[j], volC), ky[j], w);
             }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) b.merge(b.shfl_xor(gmask, o));
@@ -418,7 +445,7 @@ __device__ __forceinline__ void role_group(const SweepCtx &c, int64_t rb, const 
         if (lane == 0 && ballot) base = atomicAdd(c.late ? c.ncand : c.nmv, (unsigned long long)__popc(ballot));
         base = __shfl_sync(0xffffffffu, base, 0);
         if (want) take_move(c, base + __popc(ballot & ((1u << lane) - 1u)), u, C, b.id, b.w, wC);
-        add_counters(c.cnt, want, want && !c.late, gl == 0 && valid ? deg : 0, ncand, gl == 0 && valid);
+        add_counters(c.bcnt, want, want && !c.late, gl == 0 && valid ? deg : 0, ncand, gl == 0 && valid);
     } else {
         PlpBest b;
         b.init();
@@ -440,7 +467,7 @@ __device__ __forceinline__ void role_group(const SweepCtx &c, int64_t rb, const 
         }
         if (adopt)
             for (int k = gl; k < deg; k += G) c.active[c.g.col[beg + k]] = 1;
-        add_counters(c.cnt, 0, gl == 0 && adopt, gl == 0 && valid ? deg : 0, ncand, gl == 0 && valid);
+        add_counters(c.bcnt, 0, gl == 0 && adopt, gl == 0 && valid ? deg : 0, ncand, gl == 0 && valid);
     }
 }
 
@@ -531,7 +558,7 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
                 if (ky[j] >= 0) {
                     ncand++;
                     const int64_t w = GLOBAL ? (int64_t)__ldcg(vals + s) : (int64_t)vals[s];
-                    if (ky[j] != C) b.offer(plm_gain<BIG>(twoW, w, wC, vu, vk[j], volC), ky[j], w);
+                    if (ky[j] != C) b.offer(plm_gain<BIG>(twoW, c.res_q, c.res_p, w, wC, vu, vk[j], volC), ky[j], w);
                     if constexpr (GLOBAL) { keys[s] = -1; vals[s] = 0; }
                 }
             }
@@ -542,11 +569,11 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
         if (threadIdx.x == 0) {
             const bool want = b.id >= 0 && b.g > 0;
             if (want) take_move(c, atomicAdd(c.late ? c.ncand : c.nmv, 1ull), u, C, b.id, b.w, wC);
-            atomicAdd(&c.cnt->wanted, (unsigned long long)want);
-            atomicAdd(&c.cnt->moved, (unsigned long long)(want && !c.late));
-            atomicAdd(&c.cnt->entries, (unsigned long long)deg);
-            atomicAdd(&c.cnt->candidates, (unsigned long long)*s_cand);
-            atomicAdd(&c.cnt->decisions, 1ull);
+            c.bcnt[BC_WANTED] += want;
+            c.bcnt[BC_MOVED] += want && !c.late;
+            c.bcnt[BC_ENTRIES] += deg;
+            c.bcnt[BC_CAND] += *s_cand;
+            c.bcnt[BC_DEC] += 1;
         }
     } else {
         PlpBest b;
@@ -569,10 +596,10 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
         if (threadIdx.x == 0) {
             if (adopt) c.zeta[u] = b.id;
             else c.active[u] = 0;
-            atomicAdd(&c.cnt->moved, (unsigned long long)adopt);
-            atomicAdd(&c.cnt->entries, (unsigned long long)deg);
-            atomicAdd(&c.cnt->candidates, (unsigned long long)*s_cand);
-            atomicAdd(&c.cnt->decisions, 1ull);
+            c.bcnt[BC_MOVED] += adopt;
+            c.bcnt[BC_ENTRIES] += deg;
+            c.bcnt[BC_CAND] += *s_cand;
+            c.bcnt[BC_DEC] += 1;
         }
     }
 }
@@ -590,8 +617,8 @@ __device__ __forceinline__ void hub_finish(const SweepCtx &c, int32_t u, int32_t
         if constexpr (!PLP) {
             const bool want = r.id >= 0 && r.g > 0;
             if (want) take_move(c, atomicAdd(c.late ? c.ncand : c.nmv, 1ull), u, C, r.id, r.w, wC, relax);
-            atomicAdd(&c.cnt->wanted, (unsigned long long)want);
-            atomicAdd(&c.cnt->moved, (unsigned long long)(want && !c.late));
+            c.bcnt[BC_WANTED] += want;
+            c.bcnt[BC_MOVED] += want && !c.late;
             *s_last = 1;
         } else {
             const bool adopt = r.id >= 0 && r.w > wC;
@@ -601,10 +628,10 @@ __device__ __forceinline__ void hub_finish(const SweepCtx &c, int32_t u, int32_t
             } else {
                 c.active[u] = 0;
             }
-            atomicAdd(&c.cnt->moved, (unsigned long long)adopt);
+            c.bcnt[BC_MOVED] += adopt;
             *s_last = adopt ? 2 : 1;
         }
-        atomicAdd(&c.cnt->decisions, 1ull);
+        c.bcnt[BC_DEC] += 1;
     }
     __syncthreads();
     if constexpr (PLP) {
@@ -643,7 +670,7 @@ __device__ __forceinline__ void hub_decide_occ(const SweepCtx &c, const ChunkDes
             const int32_t sl = __ldcg(occ + i);
             const int32_t key = __ldcg(gk + sl);
             const int64_t val = (int64_t)__ldcg(gv + sl);
-            if (key != C) b.offer(plm_gain<BIG>(twoW, val, wC, vu, c.volc[key], volC), key, val);
+            if (key != C) b.offer(plm_gain<BIG>(twoW, c.res_q, c.res_p, val, wC, vu, c.volc[key], volC), key, val);
         }
     } else {
         for (int64_t i = threadIdx.x; i < nocc; i += kBlock) {
@@ -662,7 +689,7 @@ __device__ __forceinline__ void hub_decide_occ(const SweepCtx &c, const ChunkDes
     if (threadIdx.x == 0) {
         c.hub_done1[h] = 0;
         c.hub_nocc[h] = 0;
-        atomicAdd(&c.cnt->candidates, (unsigned long long)nocc);
+        c.bcnt[BC_CAND] += nocc;
     }
     hub_finish<BIG, PLP>(c, u, C, wC, b, s_last, hi.relax != 0);
 }
@@ -683,7 +710,7 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
     if constexpr (PLP) {
         // whole block; the decision skips it too.  Hubs that may share the
         // class with hub neighbours are evaluated every iteration.
-        if (!hi.relax && !c.active[u]) return;
+        if (!hi.relax && !c.racy && !c.active[u]) return;
     }
     const int64_t beg = hi.beg, end = hi.end;
     for (int s = threadIdx.x; s < HUB_CHUNK_SLOTS; s += kBlock) { keys[s] = -1; vals[s] = 0; }
@@ -732,7 +759,7 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
     if (threadIdx.x == 0) {
         unsigned done = atomicAdd(&c.hub_done1[h], 1u);
         *s_last = (done == (unsigned)hi.nb1 - 1);
-        atomicAdd(&c.cnt->entries, (unsigned long long)(end - beg));
+        c.bcnt[BC_ENTRIES] += end - beg;
     }
     __syncthreads();
     // hubs with decide slices: the count reaching nb1 releases the slices

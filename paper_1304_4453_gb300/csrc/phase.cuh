@@ -68,6 +68,9 @@ struct PhaseArgs {
     uint64_t *rc_cd, *rc_vu;
     int64_t *rc_dw;
     int32_t max_sweeps, recheck_from;
+    int64_t res_p, res_q;                  // resolution gamma = res_p / res_q of the gain (1 / 1: modularity)
+    int32_t racy;                          // racy schedule: live volumes (read and written in vol_a), no
+    int32_t pad_racy;                      //   replay, no re-check
     // PLP
     uint8_t *active;
     unsigned long long *sched;             // [1] class finish counter (starts at 0)
@@ -81,6 +84,9 @@ struct PhaseArgs {
     // phase starts ([0]) and after the barrier of class k in sweep sw
     // ([1 + sw * ncol + k]); skipped (empty) classes keep 0
     unsigned long long *class_ns;
+    // with class_ns: per class step, the latest time any block finished its
+    // items, its hub-decide slices, and the finisher's work ([3 * step + i])
+    unsigned long long *stage_max;
 };
 
 // SweepCtx of class k (layout, roles, hubs).
@@ -135,8 +141,9 @@ __device__ __forceinline__ void run_item(const SweepCtx &c, int32_t b, unsigned 
 }
 
 // Hub decide: slice `item` of a hub table; the last slice of a hub decides.
-// A PLM slice ranks the candidates D != C by 2W omega(u,D) - vol(u) vol(D),
-// which differs from the gain only by a term that is the same for every D,
+// A PLM slice ranks the candidates D != C by 2W q omega(u,D) - p vol(u) vol(D)
+// (gamma = p / q), which differs from the gain only by a term that is the
+// same for every D,
 // so the slices need not know omega(u, C); the slice that finds C in the
 // table records omega(u, C) for the last slice, which completes the gain of
 // the best candidate.  The hub's aggregation is complete when the slice
@@ -150,7 +157,7 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
     const int h = hi.h;
     const int32_t u = hi.u;
     if constexpr (PLP) {
-        if (!hi.relax && !c.active[u]) return;
+        if (!hi.relax && !c.racy && !c.active[u]) return;
     }
     int32_t *gk = c.hub_keys + hi.tab;
     VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
@@ -185,7 +192,7 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
             for (int j = 0; j < 4; j++) {
                 if (sl[j] < 0) continue;
                 ncand++;
-                if (ky[j] != C) b.offer((T)twoW * (T)wv[j] - (T)vu * (T)vk[j], ky[j], wv[j]);
+                if (ky[j] != C) b.offer((T)twoW * (T)c.res_q * (T)wv[j] - (T)c.res_p * (T)vu * (T)vk[j], ky[j], wv[j]);
                 else { *hwc = (VT)wv[j]; __threadfence(); }
                 gk[sl[j]] = -1;
                 gv[sl[j]] = 0;
@@ -220,7 +227,7 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
             c.part_tk[item] = b.tk;
         }
         c.part_id[item] = b.id;
-        atomicAdd(&c.cnt->candidates, (unsigned long long)*s_cand);
+        c.bcnt[BC_CAND] += *s_cand;
         __threadfence();
         const unsigned done = atomicAdd(&c.hub_done2[h], 1u);
         *s_last = (done == (unsigned)hi.nb2 - 1);
@@ -256,7 +263,8 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
     const int64_t wC = (int64_t)__ldcg(hwc);
     if constexpr (!PLP) {
         using T = typename GainT<BIG>::T;
-        if (b.id >= 0) b.g = b.g - (T)(2 * c.g.W) * (T)wC + (T)c.g.vol[u] * (T)(c.volc[C] - c.g.vol[u]);
+        if (b.id >= 0)
+            b.g = b.g - (T)(2 * c.g.W) * (T)c.res_q * (T)wC + (T)c.res_p * (T)c.g.vol[u] * (T)(c.volc[C] - c.g.vol[u]);
     }
     __syncthreads();   // every thread has read omega(u, C)
     if (threadIdx.x == 0) {
@@ -281,7 +289,7 @@ __device__ __forceinline__ bool wait_hub_ready(const SweepCtx &c, int32_t item, 
         const int32_t u = d.u;
         const unsigned need = (unsigned)d.nb1;
         bool skip = false;
-        if constexpr (PLP) skip = !d.relax && !c.active[u];   // inactive hubs are neither aggregated nor decided
+        if constexpr (PLP) skip = !d.relax && !c.racy && !c.active[u];   // inactive hubs are neither aggregated nor decided
         if (!skip) {
             const uint64_t t0 = global_ns();
             while (__ldcg(c.hub_done1 + h) != need) {
@@ -317,6 +325,7 @@ struct RecheckArgs {
     const int64_t *vol;
     int64_t *volc;
     int64_t twoW;
+    int64_t res_p, res_q;      // resolution gamma = res_p / res_q
     uint64_t *tmp_a, *tmp_b;   // class-sized scratch for long candidate lists
     int ubits;                 // bits of the largest vertex id
     int32_t *rc_u;             // class-sized: the candidates' records in id order
@@ -327,6 +336,13 @@ struct RecheckArgs {
     int32_t *cstamp;           // cstamp[X] == step: a hub of this class moved into or out of X
     int32_t step;              // id of this class step (> 0)
     unsigned long long *stage_ns;   // profile mode: [1] += sort time; else nullptr
+    // racy schedule: candidates of a round may be adjacent.  Every accepted
+    // mover stamps its neighbours (cstamp is then indexed by vertex), and a
+    // candidate stamped earlier in the round waits for the next sweep: only a
+    // moving neighbour changes omega(u, C) or omega(u, D), so the gains of
+    // the candidates that go ahead are exact.
+    int32_t nbr_stamp;
+    const int32_t *col;        // adjacency (neighbour stamps)
 };
 
 
@@ -461,7 +477,7 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
         const uint32_t ci = (uint32_t)(keys[i] & 0xffffffffull);
         const int32_t u = __ldcg(a.cu + ci);
         const uint32_t C = (uint32_t)__ldcg(a.cc + ci), D = (uint32_t)__ldcg(a.cd + ci);
-        const bool hub = a.rp[u + 1] - a.rp[u] > HUB_RELAX;
+        const bool hub = !a.nbr_stamp && a.rp[u + 1] - a.rp[u] > HUB_RELAX;
         a.rc_u[i] = u;
         a.rc_cd[i] = ((uint64_t)D << 32) | C;
         a.rc_vu[i] = (uint64_t)a.vol[u] | ((uint64_t)hub << 63);
@@ -494,6 +510,7 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
             // a hub whose omega(u, C) or omega(u, D) a hub moved earlier in
             // this class may have changed waits for the next sweep
             bool blocked = hub && (__ldcg(a.cstamp + C) == a.step || __ldcg(a.cstamp + D) == a.step);
+            if (a.nbr_stamp) blocked = valid && __ldcg(a.cstamp + u) == a.step;
             bool mine = false;
             // Every undecided lane evaluates its gain with the volumes as
             // updated by the moves accepted so far.  The lowest accepting lane
@@ -505,7 +522,7 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
             unsigned pending = __ballot_sync(0xffffffffu, valid);
             while (pending) {
                 const bool acc = ((pending >> lane) & 1u) && !blocked &&
-                                 plm_gain<BIG>(a.twoW, dw, 0, vu, volD, volC) > 0;
+                                 plm_gain<BIG>(a.twoW, a.res_q, a.res_p, dw, 0, vu, volD, volC) > 0;
                 const unsigned am = __ballot_sync(0xffffffffu, acc);
                 if (am == 0) break;
                 const int k = __ffs(am) - 1;
@@ -523,6 +540,14 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
                     if (C == Ck) volC -= vk; else if (C == Dk) volC += vk;
                     if (D == Ck) volD -= vk; else if (D == Dk) volD += vk;
                     if (hk && hub && (C == Ck || C == Dk || D == Ck || D == Dk)) blocked = true;
+                }
+                if (a.nbr_stamp) {
+                    // the whole warp stamps the accepted mover's neighbours
+                    const int32_t uk = __shfl_sync(0xffffffffu, u, k);
+                    const int64_t e1 = a.rp[uk + 1];
+                    for (int64_t e = a.rp[uk] + lane; e < e1; e += 32) a.cstamp[a.col[e]] = a.step;
+                    __syncwarp();
+                    if (lane > k && !blocked) blocked = __ldcg(a.cstamp + u) == a.step;
                 }
             }
             if (valid && mine) {
@@ -554,6 +579,7 @@ struct BlockShared {
     int *last, *ok, *nb2;
     long long *grab;           // decide slice taken by the block
     SweepCtx *c;
+    unsigned long long *bcnt;  // [BC_N] the block's counter sums of the current sweep
 };
 
 // True in the block that finishes the class last (every block of the team
@@ -629,9 +655,20 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
                 c.gt_keys = gt_keys;
                 c.gt_vals = gt_vals;
                 c.cnt = a.cnt + sw;
+                c.bcnt = sh.bcnt;
+                c.res_p = a.res_p;
+                c.res_q = a.res_q;
+                c.racy = a.racy;
                 c.late = late;
                 c.rp_n = nullptr;
-                if (!late) {
+                if (a.racy && !late) {
+                    // early racy sweeps: every vertex reads and updates the live volumes
+                    c.volc = vb[0];
+                    c.volw = vb[0];
+                    c.mv_u = a.mv_u + cb;
+                    c.mv_c = a.mv_c + cb;
+                    c.nmv = a.nmv + par * a.ncol + k;
+                } else if (!late) {
                     c.volc = vb[t & 1];
                     c.volw = vb[(t + 1) & 1];
                     c.mv_u = a.mv_u + cb;
@@ -650,7 +687,7 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
             }
             __syncthreads();
             const int32_t nb2 = *sh.nb2;
-            if (!late && prev_k >= 0) {
+            if (!late && !a.racy && prev_k >= 0) {
                 // replay the previous class's moves into this class's write buffer
                 const int64_t pa = a.class_off[(int64_t)prev_k * NBINS];
                 const int64_t nr = (int64_t)__ldcg(a.nmv + prev_par * a.ncol + prev_k);
@@ -671,9 +708,12 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
                 run_item<WK, BIG, false>(c, c.bend[5] - 1 - b, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
             }
+            const int64_t step = (int64_t)sw * a.ncol + k;
+            if (a.stage_max && threadIdx.x == 0) atomicMax(a.stage_max + 3 * step, global_ns());
             if (nb2 > 0) {
                 if (!decide_pool<WK, BIG, false>(tm, c, nb2, sh)) return false;
             }
+            if (a.stage_max && threadIdx.x == 0) atomicMax(a.stage_max + 3 * step + 1, global_ns());
             if (late || c.nrelax > 0) {
                 // the block that finishes the class last re-checks its wanted
                 // moves (late sweeps) or writes the hubs' deferred labels
@@ -684,15 +724,16 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
                     } else if (__ldcg(c.ncand) != 0) {
                         const uint64_t r0 = a.stage_ns ? global_ns() : 0;
                         RecheckArgs ra{c.cand_u, c.cand_c, c.cand_d, c.cand_wd, c.cand_wc, c.ncand, a.zeta,
-                                       a.g.vol, c.volw, 2 * a.g.W, a.tmp_a, a.tmp_b, a.ubits,
+                                       a.g.vol, c.volw, 2 * a.g.W, a.res_p, a.res_q, a.tmp_a, a.tmp_b, a.ubits,
                                        a.rc_u, a.rc_cd, a.rc_vu, a.rc_dw, c.cnt,
-                                       a.g.rp, a.cstamp, sw * a.ncol + k + 1, a.stage_ns};
+                                       a.g.rp, a.cstamp, sw * a.ncol + k + 1, a.stage_ns, a.racy, a.g.col};
                         recheck_block<BIG>(ra, sh.smem);
                         if (a.stage_ns && threadIdx.x == 0) atomicAdd(a.stage_ns + 2, global_ns() - r0);
                     }
+                    if (a.stage_max && threadIdx.x == 0) atomicMax(a.stage_max + 3 * step + 2, global_ns());
                 }
             }
-            if (!late) {
+            if (!late && !a.racy) {
                 prev_k = k;
                 prev_par = par;
                 t++;
@@ -701,6 +742,9 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
             if (timed) a.stage_ns[0] += global_ns() - t0;
             if (tracer) a.class_ns[1 + (int64_t)sw * a.ncol + k] = global_ns();
         }
+        // the sweep's counters are complete once every block has added its sums
+        flush_counters(sh.bcnt, a.cnt + sw);
+        if (!team_sync(tm, sh.gen, sh.ok)) return false;
         if (__ldcg(&a.cnt[sw].wanted) == 0) {
             conv = 1;
             sw++;
@@ -739,6 +783,8 @@ __device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<P
                 c.gt_keys = gt_keys;
                 c.gt_vals = gt_vals;
                 c.cnt = a.cnt + it;
+                c.bcnt = sh.bcnt;
+                c.racy = a.racy;
                 c.active = a.active;
                 c.tie_salt = salt;
             }
@@ -754,6 +800,7 @@ __device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<P
             if (c.nrelax > 0 && class_finisher(a, tm, fin_base, sh.last)) apply_deferred_labels(c);
             if (!team_sync(tm, sh.gen, sh.ok)) return false;
         }
+        flush_counters(sh.bcnt, a.cnt + it);
         if (!team_sync(tm, sh.gen, sh.ok)) return false;
         updated = __ldcg(&a.cnt[it].moved);
         it++;
@@ -800,9 +847,11 @@ struct BatchArgs {
     __shared__ long long s_grab;                                                \
     __shared__ SweepCtx s_ctx;                                                  \
     __shared__ __align__(16) unsigned long long s_args[sizeof(PhaseArgs) / 8];  \
+    __shared__ unsigned long long s_bcnt[BC_N];                                 \
     if (threadIdx.x == 0) s_gen = 0;                                            \
+    if (threadIdx.x < BC_N) s_bcnt[threadIdx.x] = 0;                            \
     __syncthreads();                                                            \
-    const BlockShared<BT> sh{smem, s_best, &s_cand, &s_gen, &s_last, &s_ok, &s_nb2, &s_grab, &s_ctx};
+    const BlockShared<BT> sh{smem, s_best, &s_cand, &s_gen, &s_last, &s_ok, &s_nb2, &s_grab, &s_ctx, s_bcnt};
 
 static_assert(sizeof(PhaseArgs) % 8 == 0, "PhaseArgs is copied in 64-bit words");
 

@@ -1,6 +1,8 @@
 """bench.py's reference arm (the oracle on the host cores) keeps the JSON
 contract: one line with the metric, the rate and its unit, the CPU baseline
-it measured and an e2e object without transfers."""
+it measured and an e2e object without transfers.  The rate is measured on a
+bounded sample graph, and the line names that graph (scale, n, m) beside
+the workload it stands in for."""
 import json
 import os
 import subprocess
@@ -23,7 +25,11 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["unit"] == "edges/s" and d["higher_is_better"] is True
     assert d["config"]["workload"] == "rmat22_ef16_plm"
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["sample"]
+    assert cb["cores"] == os.cpu_count()            # the OpenMP build on every host core
+    sample = d["config"]["cpu_sample"]
+    assert sample["n"] == 1 << 20 and sample["m"] == cb["sample_graph"]["m"] > 0
+    assert "R-MAT scale 20" in sample["graph"] and f"m={sample['m']}" in cb["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

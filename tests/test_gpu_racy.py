@@ -1,0 +1,133 @@
+"""The racy schedule (cd_opts.schedule = R rounds): the paper's parallel loop
+over every vertex on live labels and volumes (Sections III-A, III-B), cut into
+R hash rounds, without a colouring or a re-check.  Its results depend on thread timing, so they are
+judged by properties: a dense partition, the reported modularity equal to the
+exact Eq. 1 value of the labels (checked with the oracle), quality within a
+stated margin of the deterministic schedule, and the resolution honoured."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1304_4453_gb300 import cd, synth
+
+from . import properties as P
+
+pytestmark = pytest.mark.gpu
+
+MOD_TOL = 1e-12
+# The racy schedule may end in another local optimum of the same method; the
+# margin is an absolute modularity difference (modularity lies in [-1/2, 1]).
+QUALITY_MARGIN = 0.02
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1304_4453_gb300 import build
+    build.build()
+    cd.lib()
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+GRAPHS = {
+    "pp_small": synth.planted_partition(2000, 8, 0.03, 0.002, seed=2),
+    "config1": synth.planted_partition_config1(),
+    "rmat14_hubs": synth.rmat(14, seed=5),
+    "rmat18": synth.rmat(18, seed=1),
+    "chunglu_w": synth.chung_lu(20000, seed=3),
+    "rand_w_loops": synth.random_graph(300, 1500, seed=7, loops=20, wmax=50),
+}
+
+
+def _valid(O, g, r):
+    lab = r.labels.cpu().numpy()
+    k = P.check_dense_labels(lab)
+    assert k == r.stats["ncomm"]
+    assert abs(r.modularity - O.modularity(*g.numpy(), lab)[0]) <= MOD_TOL
+    return lab
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+@pytest.mark.parametrize("refine", [False, True])
+def test_racy_plm_is_valid_and_close_to_deterministic(O, name, refine):
+    g = GRAPHS[name]
+    G = cd.Graph.from_synth(g, device="cuda")
+    det = G.plm(refine=refine, seed=1)
+    r = G.plm(refine=refine, seed=1, racy=True)
+    _valid(O, g, r)
+    assert r.stats["colors0"] == cd.RACY_ROUNDS   # hash rounds, no colouring
+    assert r.modularity >= det.modularity - QUALITY_MARGIN, (r.modularity, det.modularity)
+
+
+@pytest.mark.parametrize("name", ["pp_small", "config1", "rmat14_hubs", "chunglu_w"])
+def test_racy_option_leaves_plp_deterministic_and_epp_valid(O, name):
+    """PLP (and EPP's base runs) keep the colour classes under the racy
+    option; EPP's final phase runs racy and gives a valid partition."""
+    g = GRAPHS[name]
+    G = cd.Graph.from_synth(g, device="cuda")
+    r = G.plp(seed=1, racy=True)
+    o = O.plp(*g.numpy(), seed=1)
+    assert np.array_equal(r.labels.cpu().numpy(), o.labels)
+    e = G.epp(b=3, final_refine=True, seed=1, racy=True)
+    _valid(O, g, e)
+    det = G.epp(b=3, final_refine=True, seed=1)
+    assert e.modularity >= det.modularity - QUALITY_MARGIN
+
+
+@pytest.mark.parametrize("name", ["rmat14_hubs", "chunglu_w", "pp_small"])
+def test_racy_late_sweeps_converge_without_positive_moves(O, name):
+    """The stamped re-check makes every late move raise the objective, so the
+    racy move phases terminate; a converged PLMR result has no positive-gain
+    move left (Algorithm 2's stopping rule)."""
+    g = GRAPHS[name]
+    G = cd.Graph.from_synth(g, device="cuda")
+    r = G.plm(refine=True, seed=1, racy=True)
+    assert r.stats["converged"] == 1 and r.stats["sweeps"] < 256 * r.stats["levels"]
+    assert O.positive_moves(*g.numpy(), r.labels.cpu().numpy()) == 0
+
+
+def test_racy_planted_partition_recovers_the_blocks(O):
+    """On the n = 10,000 planted partition (20 blocks of 500) the racy PLMR
+    lands near the planted partition's modularity, as the deterministic
+    schedule does."""
+    g = GRAPHS["config1"]
+    G = cd.Graph.from_synth(g, device="cuda")
+    truth = np.arange(g.n, dtype=np.int32) // 500
+    q_truth = O.modularity(*g.numpy(), truth)[0]
+    det = G.plm(refine=True)
+    assert det.modularity >= q_truth - 0.01
+    r = G.plm(refine=True, racy=True)
+    assert r.modularity >= det.modularity - 2 * QUALITY_MARGIN, (r.modularity, det.modularity, q_truth)
+
+
+def test_racy_resolution_extremes(O):
+    """gamma = 0 merges every connected component (no move lowers the
+    objective), gamma = 2W keeps singletons, on the racy schedule too."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    g = GRAPHS["pp_small"]
+    G = cd.Graph.from_synth(g, device="cuda")
+    rp, c, w = g.numpy()
+    ncc = connected_components(csr_matrix((np.ones(len(c)), c, rp), shape=(g.n, g.n)), directed=False)[0]
+    r = G.plm(refine=True, racy=True, resolution=(0, 1))
+    assert r.stats["ncomm"] == ncc
+    s = G.plm(refine=True, racy=True, resolution=(2 * G.W, 1))
+    assert s.stats["ncomm"] == g.n
+
+
+def test_racy_schedule_value_checked():
+    g = GRAPHS["pp_small"]
+    G = cd.Graph.from_synth(g, device="cuda")
+    for bad in (-1, 4097):
+        o = cd.default_opts()
+        o.schedule = bad
+        with pytest.raises(cd.CDError) as e:
+            cd.cd_plm(G.h, torch.empty(g.n, dtype=torch.int32, device="cuda"), False, o)
+        assert e.value.status == cd.CD_EINVAL

@@ -44,3 +44,24 @@ def test_status_strings_without_gpu():
     assert L.cd_status_str(4) == b"CD_ENOTCONV"
     o = cd.default_opts()
     assert (o.seed, o.max_sweeps, o.max_levels, o.max_iters) == (1, 256, 64, 1000)
+
+
+def test_option_defaults_and_struct_layout(tmp_path):
+    """cd_opts_default fills the resolution 1 / 1 and the colour-class
+    schedule, and the binding's structs have the header's layout (a C
+    program compiled against include/cd.h reports sizes and offsets)."""
+    o = cd.default_opts()
+    assert (o.res_num, o.res_den, o.schedule) == (1, 1, 0)
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "cd.h"\n'
+        'int main(void) { printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(cd_opts), offsetof(cd_opts, bin_max),'
+        ' offsetof(cd_opts, res_num), offsetof(cd_opts, res_den), offsetof(cd_opts, schedule),'
+        ' sizeof(cd_stats)); return 0; }\n')
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(cd.cd_opts), cd.cd_opts.bin_max.offset, cd.cd_opts.res_num.offset,
+            cd.cd_opts.res_den.offset, cd.cd_opts.schedule.offset, ctypes.sizeof(cd.cd_stats)]
+    assert got == want
