@@ -53,7 +53,7 @@ typedef enum {
     CD_ETIMEOUT = 6    /* a bounded wait ran out */
 } cd_status;
 
-enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1 };
+enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1, CD_BORROW = 2 };
 
 /* Options.  cd_opts_default() fills: seed 1, max_sweeps 256, max_levels 64,
  * max_iters 1000, profile 0, team_quantum 262144, team_min 8,
@@ -157,6 +157,11 @@ const char *cd_last_error(void);
  * vol(u) = sum of weights to other vertices + 2 * loop weight and the total
  * weight omega(E) (Section III-B).  `stream` is a cudaStream_t (NULL: the
  * legacy default stream) used by every later call on this handle.
+ * mem_flags CD_BORROW: row_ptr, col and w are device arrays that the handle
+ * reads in place instead of copying; the caller keeps them alive and
+ * unchanged until cd_graph_destroy.  When the graph has self-loops the
+ * handle still keeps a copy of the adjacency without them (the kernels read
+ * loop-free rows); the input arrays are never duplicated as they are.
  * Errors: CD_EINVAL (bad sizes, unsorted or duplicate columns, column out of
  * range, non-positive weight, asymmetric entry or weight) with nothing
  * allocated; CD_ENOMEM; CD_ECUDA. */
@@ -200,6 +205,22 @@ cd_status cd_plm(cd_graph *g, int refine, const cd_opts *o, int32_t *labels,
  * core graph, prolongation.  b >= 1. */
 cd_status cd_epp(cd_graph *g, int ensemble_size, int final_refine, const cd_opts *o,
                  int32_t *labels, int labels_mem, double *mod, cd_stats *st);
+
+/* EPP(b, Base, Final) of Section III-D, which leaves the base and final
+ * algorithms open, with iterated ensembles (the hierarchy of core graphs of
+ * the scheme EPP adapts, Section II).  base: CD_BASE_PLP, CD_BASE_PLM or
+ * CD_BASE_PLMR; Final = PLM (final_refine 0) or PLMR (1).  Round r = 0, 1,
+ * ..., rounds - 1 runs the b base algorithms on the current graph (run i
+ * seeded seed + r b + i), forms their core communities (Eq. 2) and coarsens
+ * by them.  Round 0 is Algorithm 5; a later round is taken only if its core
+ * merges vertices and has strictly higher modularity than the previous
+ * round's core, else the rounds stop.  The final algorithm runs on the last
+ * core graph (seed), and its labels are prolonged to the input graph.
+ * cd_stats.levels is the number of core graphs taken.  base = CD_BASE_PLP
+ * with rounds = 1 is cd_epp.  b >= 1, 1 <= rounds <= 64, else CD_EINVAL. */
+enum { CD_BASE_PLP = 0, CD_BASE_PLM = 1, CD_BASE_PLMR = 2 };
+cd_status cd_epp_general(cd_graph *g, int ensemble_size, int base, int final_refine, int rounds,
+                         const cd_opts *o, int32_t *labels, int labels_mem, double *mod, cd_stats *st);
 
 /* Batched and served runs.  The paper runs one graph at a time; its only
  * multi-instance notion is the nested parallelism of EPP's base runs

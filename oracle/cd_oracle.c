@@ -1012,6 +1012,90 @@ int or_epp(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
     return 0;
 }
 
+/* Generic EPP(b, Base, Final) (Section III-D: the scheme is agnostic to its
+ * base and final algorithms) with iterated ensembles (the hierarchy of core
+ * graphs that Section II describes for the scheme EPP adapts).
+ *   base: 0 PLP, 1 PLM, 2 PLMR; final: PLM, or PLMR when final_refine.
+ *   Round r = 0, 1, ... < rounds: b base runs on the current graph (seeds
+ *   seed + r b + i), their exact core communities (Eq. 2).  Round 0's core
+ *   is always taken (Algorithm 5).  A later round's core is taken only if it
+ *   merges vertices of the current graph and its modularity is strictly
+ *   higher than the previous core's (quality must improve); else the rounds
+ *   stop.  A taken core coarsens the current graph.  The final algorithm runs
+ *   on the last graph (seed), and its labels are prolonged back through
+ *   every core graph and compacted.  rounds = 1 with PLP bases is or_epp.
+ * The final phase optimises the resolution res_num / res_den. */
+int or_epp_general(int64_t n, const int64_t *rp, const int32_t *col, const int64_t *w,
+                   int b, int base, int final_refine, int rounds, uint64_t seed,
+                   int32_t max_sweeps, int32_t max_levels, double theta, int32_t max_iter,
+                   int64_t res_num, int64_t res_den, int32_t *labels, double *mod, int64_t *stats)
+{
+    if (b < 1 || base < 0 || base > 2 || rounds < 1 || rounds > 64) return -2;
+    if (res_num < 0 || res_den < 1) return -2;
+    OG g;
+    if (og_from_input(&g, n, rp, col, w)) return -1;
+    if (og_set_resolution(&g, res_num, res_den)) { og_free(&g); return -2; }
+    int64_t st[ST_N] = {0};
+    st[ST_CONVERGED] = 1;
+    OG lv[64];                 /* taken core graphs */
+    int32_t *pi[64];           /* pi[l]: vertex of level l -> vertex of lv[l] (level 0 = g) */
+    int nl = 0;
+    const OG *cur = &g;
+    double prev = 0.0;
+    for (int r = 0; r < rounds; r++) {
+        const int64_t nc = cur->n;
+        int32_t *bl = (int32_t *)malloc(((size_t)b * nc + 1) * sizeof(int32_t));
+        int32_t *core = (int32_t *)malloc(((size_t)nc + 1) * sizeof(int32_t));
+        for (int i = 0; i < b; i++) {
+            const uint64_t sd = seed + (uint64_t)r * (uint64_t)b + (uint64_t)i;
+            int64_t sb[ST_N] = {0};
+            sb[ST_CONVERGED] = 1;
+            int32_t *zi = bl + (size_t)i * nc;
+            if (base == 0) {
+                if (nc > 0) plp_run(cur, sd, theta, max_iter, 1, 0, zi, sb);
+            } else {
+                Opts ob = { sd, max_sweeps, max_levels, 0 };
+                if (nc > 0) plm_rec(cur, base == 2, &ob, 0, zi, sb);
+            }
+            st[ST_ITERS] += sb[ST_ITERS];
+        }
+        const int64_t k = nc > 0 ? combine(nc, b, bl, core) : 0;
+        const double q = og_modularity(cur, core);
+        if (r > 0 && (k == nc || q <= prev)) {      /* no contraction or no gain */
+            free(bl); free(core);
+            break;
+        }
+        prev = q;
+        pi[nl] = (int32_t *)malloc(((size_t)nc + 1) * sizeof(int32_t));
+        coarsen(cur, core, &lv[nl], pi[nl]);
+        cur = &lv[nl];
+        nl++;
+        free(bl); free(core);
+    }
+    int32_t *z = (int32_t *)malloc(((size_t)cur->n + 1) * sizeof(int32_t));
+    Opts o = { seed, max_sweeps, max_levels, 0 };
+    if (cur->n > 0) plm_rec(cur, final_refine, &o, 0, z, st);
+    for (int l = nl - 1; l >= 0; l--) {            /* prolong */
+        const int64_t nb = l == 0 ? g.n : lv[l - 1].n;
+        int32_t *zb = (int32_t *)malloc(((size_t)nb + 1) * sizeof(int32_t));
+        for (int64_t v = 0; v < nb; v++) zb[v] = z[pi[l][v]];
+        free(z);
+        z = zb;
+    }
+    for (int64_t v = 0; v < n; v++) labels[v] = z[v];
+    compact(n, labels);
+    *mod = og_modularity(&g, labels);
+    int64_t k = 0;
+    for (int64_t u = 0; u < n; u++) if (labels[u] + 1 > k) k = labels[u] + 1;
+    st[ST_NCOMM] = k;
+    st[ST_LEVELS] = nl;        /* core graphs taken (ensemble rounds) */
+    memcpy(stats, st, sizeof(st));
+    free(z);
+    for (int l = 0; l < nl; l++) { og_free(&lv[l]); free(pi[l]); }
+    og_free(&g);
+    return 0;
+}
+
 /* Number of vertices that have a neighbour community with positive gain
  * under `labels` (the convergence condition of Algorithm 2) for the
  * resolution res_num / res_den; the largest such gain numerator goes to

@@ -79,6 +79,8 @@ def lib(threads: int = 1):
             L.or_epp.argtypes = [i64, P, P, P, ctypes.c_int, ctypes.c_int, u64, i32, i32,
                                  dbl, i32, i64, i64, P, P, P, P, P]
             L.or_positive_moves.argtypes = [i64, P, P, P, P, i64, i64, P]
+            L.or_epp_general.argtypes = [i64, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         u64, i32, i32, dbl, i32, i64, i64, P, P, P]
             L.or_positive_moves.restype = i64
             L.or_set_threads.argtypes = [ctypes.c_int]
             L.or_set_threads.restype = ctypes.c_int
@@ -263,6 +265,32 @@ def epp(row_ptr, col, w, b=4, final_refine=True, seed=1, theta=None,
     if want_parts:
         return r, base[:b * g.n].reshape(b, g.n), core[:g.n]
     return r
+
+
+BASE_PLP, BASE_PLM, BASE_PLMR = 0, 1, 2
+
+
+def epp_general(row_ptr, col, w, b=4, base=BASE_PLP, final_refine=True, rounds=1, seed=1, theta=None,
+                max_sweeps=MAX_SWEEPS, max_levels=MAX_LEVELS, max_iter=MAX_PLP_ITERS, resolution=(1, 1),
+                threads=1) -> Result:
+    """EPP(b, Base, Final) with up to `rounds` ensemble rounds (Section
+    III-D; see or_epp_general).  stats["levels"] is the number of core
+    graphs taken."""
+    g = _CSR(row_ptr, col, w)
+    if theta is None:
+        theta = g.n * 1e-5
+    z = np.zeros(max(g.n, 1), np.int32)
+    mod = ctypes.c_double()
+    st = np.zeros(len(STATS), np.int64)
+    p, q = resolution
+    rc = lib(threads).or_epp_general(*g.args(), int(b), int(base), int(final_refine), int(rounds), seed,
+                                     max_sweeps, max_levels, float(theta), max_iter, int(p), int(q),
+                                     _ptr(z), ctypes.byref(mod), _ptr(st))
+    if rc == -2:
+        raise ValueError("b >= 1, base in {0, 1, 2}, 1 <= rounds <= 64, valid resolution")
+    if rc:
+        raise MemoryError
+    return Result(z[:g.n], mod.value, _stats(st))
 
 
 def positive_moves(row_ptr, col, w, labels, resolution=(1, 1)):

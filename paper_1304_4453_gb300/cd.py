@@ -75,7 +75,7 @@ SYMBOLS = ["cd_opts_default", "cd_status_str", "cd_last_error", "cd_graph_create
            "cd_epp", "cd_color", "cd_coarsen", "cd_graph_export", "cd_debug_fail_alloc",
            "cd_launch_count", "cd_modularity_static", "cd_run_batch", "cd_plm_batch",
            "cd_server_create", "cd_server_submit", "cd_server_poll", "cd_server_info",
-           "cd_server_destroy", "cd_tune", "cd_debug_plan_launch", "cd_debug_class_trace"]
+           "cd_server_destroy", "cd_tune", "cd_debug_plan_launch", "cd_debug_class_trace", "cd_epp_general"]
 
 
 def library_path() -> str:
@@ -102,6 +102,7 @@ def lib():
             L.cd_plp.argtypes = [P, P, ctypes.c_double, P, c_int, P, P]
             L.cd_plm.argtypes = [P, c_int, P, P, c_int, P, P]
             L.cd_epp.argtypes = [P, c_int, c_int, P, P, c_int, P, P]
+            L.cd_epp_general.argtypes = [P, c_int, c_int, c_int, c_int, P, P, c_int, P, P]
             L.cd_color.argtypes = [P, ctypes.c_uint64, P, c_int, P]
             L.cd_coarsen.argtypes = [P, P, c_int, P]
             L.cd_graph_export.argtypes = [P, P, P, P, c_int, P]
@@ -193,17 +194,27 @@ def default_opts(seed: int = 1, max_sweeps: int = 256, max_levels: int = 64,
 # C-named wrappers
 # ---------------------------------------------------------------------------
 
-def cd_graph_create(row_ptr, col, w=None, stream=None):
+CD_BORROW = 2
+
+
+def cd_graph_create(row_ptr, col, w=None, stream=None, borrow=False):
     """Returns an opaque handle (ctypes pointer).  All three arrays must live
-    in the same memory (host or one CUDA device)."""
+    in the same memory (host or one CUDA device).  borrow=True (device arrays
+    of the right dtypes only): the handle reads them in place; the caller
+    keeps them alive and unchanged until the handle is destroyed."""
     rp, m1, k1 = _arr(row_ptr, np.int64)
     cp, m2, k2 = _arr(col, np.int32)
     wp, m3, k3 = _arr(w, np.int32)
     n = (k1.numel() if hasattr(k1, "numel") else len(k1)) - 1
     if w is not None and m3 != m1 or m2 != m1:
         raise CDError(CD_EINVAL, "row_ptr, col and w must live in the same memory")
+    mem = m1
+    if borrow:
+        if m1 != CD_MEM_DEVICE or k1 is not row_ptr or k2 is not col or (w is not None and k3 is not w):
+            raise CDError(CD_EINVAL, "borrow needs contiguous CUDA tensors of dtypes int64, int32, int32")
+        mem = CD_BORROW
     h = ctypes.c_void_p()
-    _check(lib().cd_graph_create(n, rp, cp, wp, m1, _stream(stream), ctypes.byref(h)), False)
+    _check(lib().cd_graph_create(n, rp, cp, wp, mem, _stream(stream), ctypes.byref(h)), False)
     return h
 
 
@@ -248,6 +259,18 @@ def cd_epp(h, labels_out, ensemble_size: int = 4, final_refine: bool = True, opt
     o = opts or default_opts()
     return _run(lib().cd_epp, h,
                 lambda lp, mem, mp, sp: (int(ensemble_size), int(final_refine), ctypes.byref(o), lp, mem, mp, sp),
+                labels_out)
+
+
+CD_BASE_PLP, CD_BASE_PLM, CD_BASE_PLMR = 0, 1, 2
+
+
+def cd_epp_general(h, labels_out, ensemble_size: int = 4, base: int = CD_BASE_PLP, final_refine: bool = True,
+                   rounds: int = 1, opts=None):
+    o = opts or default_opts()
+    return _run(lib().cd_epp_general, h,
+                lambda lp, mem, mp, sp: (int(ensemble_size), int(base), int(final_refine), int(rounds),
+                                         ctypes.byref(o), lp, mem, mp, sp),
                 labels_out)
 
 
@@ -435,8 +458,10 @@ class Graph:
     """Owns a cd_graph handle.  Results come back as torch tensors on the
     device of ``device`` (default cuda:0)."""
 
-    def __init__(self, row_ptr, col, w=None, stream=None):
-        self.h = cd_graph_create(row_ptr, col, w, stream)
+    def __init__(self, row_ptr, col, w=None, stream=None, borrow=False):
+        self.h = cd_graph_create(row_ptr, col, w, stream, borrow)
+        # a borrowed CSR must outlive the handle
+        self._borrowed = (row_ptr, col, w) if borrow else None
         self.n, self.m, self.W = cd_graph_info(self.h)
 
     @classmethod
@@ -475,6 +500,11 @@ class Graph:
     def epp(self, b=4, final_refine=True, out=None, **kw) -> Result:
         out = self._out(out)
         mod, st, status = cd_epp(self.h, out, b, final_refine, default_opts(**kw))
+        return Result(out, mod, st, status)
+
+    def epp_general(self, b=4, base=CD_BASE_PLP, final_refine=True, rounds=1, out=None, **kw) -> Result:
+        out = self._out(out)
+        mod, st, status = cd_epp_general(self.h, out, b, base, final_refine, rounds, default_opts(**kw))
         return Result(out, mod, st, status)
 
     def modularity(self, labels) -> float:

@@ -190,6 +190,26 @@ cd_status cd_epp(cd_graph *g, int ensemble_size, int final_refine, const cd_opts
     });
 }
 
+cd_status cd_epp_general(cd_graph *g, int ensemble_size, int base, int final_refine, int rounds, const cd_opts *o,
+                         int32_t *labels, int labels_mem, double *mod, cd_stats *st) {
+    if (!g) return CD_EINVAL;
+    return guarded([&]() {
+        const GraphView &v = g->g.view;
+        if (ensemble_size < 1) raise(CD_EINVAL, "ensemble_size must be >= 1");
+        if (base < CD_BASE_PLP || base > CD_BASE_PLMR) raise(CD_EINVAL, "base must be CD_BASE_PLP, _PLM or _PLMR");
+        if (final_refine != 0 && final_refine != 1) raise(CD_EINVAL, "final_refine must be 0 or 1");
+        if (rounds < 1 || rounds > 64) raise(CD_EINVAL, "rounds must be in [1, 64]");
+        RunOpts ro = to_run(o);
+        LabelsOut out(labels, labels_mem, v.n, g->stream);
+        RunStats r;
+        run_epp_general(v, ensemble_size, base, final_refine == 1, rounds, ro, (double)v.n * 1e-5, out.p, r,
+                        g->stream);
+        if (mod) *mod = modularity(v, out.p, g->stream);
+        out.finish();
+        return finish_run(r, st);
+    });
+}
+
 cd_status cd_run_batch(cd_graph *const *gs, int count, const cd_task *task, const cd_opts *o,
                        int32_t *const *labels, int labels_mem, double *mods, cd_stats *st, void *stream) {
     return guarded([&]() {

@@ -1316,4 +1316,84 @@ void run_epp(const GraphView &g, int b, bool final_refine, const RunOpts &o, dou
     run_single(sp, st, s);
 }
 
+// EPP(b, Base, Final) with iterated ensembles.  Round r runs b base jobs
+// (seeds seed + r b + i) on the current graph in one batch, folds their exact
+// core communities (Eq. 2), and coarsens by them; a round after the first
+// is taken only if its core merges vertices and has strictly higher
+// modularity than the previous round's.  The final PLM / PLMR job runs on
+// the last core graph and its labels are prolonged through every round.
+void run_epp_general(const GraphView &g, int b, int base, bool final_refine, int rounds, const RunOpts &o,
+                     double theta, int32_t *labels, RunStats &st, cudaStream_t s) {
+    if (base == EPP_BASE_PLP && rounds == 1) {   // Algorithm 5 as one job: the bases share one launch
+        run_epp(g, b, final_refine, o, theta, labels, st, s);
+        st.levels = 1;                            // one core graph taken
+        return;
+    }
+    struct Round {
+        OwnedGraph cg;
+        DBuf<int32_t> core;    // core community of each vertex of the round's input graph
+        DBuf<int64_t> rank;    // core label -> vertex of cg
+    };
+    std::vector<std::unique_ptr<Round>> taken;
+    GraphView cur = g;
+    double prev = 0.0;
+    int64_t base_iters = 0;
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int workers = std::max(1, std::min({16, b, hw > 0 ? hw : 4}));
+    for (int r = 0; r < rounds; r++) {
+        const int64_t nc = cur.n;
+        DBuf<int32_t> bl((size_t)b * nc, s);
+        std::vector<std::unique_ptr<Job>> jobs;
+        std::vector<Job *> jp;
+        for (int i = 0; i < b; i++) {
+            JobSpec sp;
+            sp.g = cur;
+            sp.algo = base == EPP_BASE_PLP ? ALGO_PLP : ALGO_PLM;
+            sp.refine = base == EPP_BASE_PLMR;
+            sp.theta = theta;
+            sp.o = o;
+            sp.o.seed = o.seed + (uint64_t)r * (uint64_t)b + (uint64_t)i;
+            sp.labels = bl.p + (size_t)i * nc;
+            jobs.push_back(std::make_unique<Job>(sp));
+            jp.push_back(jobs.back().get());
+        }
+        if (nc > 0) run_jobs(jp, s, workers);
+        for (const auto &j : jobs) base_iters += j->st.iters;
+        auto rd = std::make_unique<Round>();
+        rd->core.alloc(nc, s);
+        if (nc) {
+            CD_CUDA(cudaMemcpyAsync(rd->core.p, bl.p, nc * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            for (int i = 1; i < b; i++) fold_core(rd->core.p, bl.p + (size_t)i * nc, nc, s);
+        }
+        const int64_t k = nc ? compact_labels(rd->core.p, nc, s) : 0;
+        const double q = modularity(cur, rd->core.p, s);
+        if (r > 0 && (k == nc || q <= prev)) break;     // no contraction or no gain
+        prev = q;
+        rd->rank.alloc(nc, s);
+        coarsen_graph(cur, rd->core.p, rd->rank.p, rd->cg, s);
+        cur = rd->cg.view;
+        taken.push_back(std::move(rd));
+    }
+    DBuf<int32_t> zf(cur.n, s);
+    RunStats fs;
+    run_plm(cur, final_refine, o, zf.p, fs, s);
+    // prolong through the rounds, deepest first: core <- final labels of its
+    // coarse vertex (k_prolong, in place)
+    const int32_t *up = zf.p;
+    for (int l = (int)taken.size() - 1; l >= 0; l--) {
+        Round &rd = *taken[l];
+        const int64_t nl = l == 0 ? g.n : taken[l - 1]->cg.view.n;
+        if (nl) { k_prolong<<<grid_for(nl, kBlock, 152 * 32), kBlock, 0, s>>>(rd.core.p, rd.rank.p, up, nl); ::cd::note_launch(); }
+        CD_LAUNCH_CHECK();
+        up = rd.core.p;
+    }
+    if (g.n) CD_CUDA(cudaMemcpyAsync(labels, up, g.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    const int64_t k = g.n ? compact_labels(labels, g.n, s) : 0;
+    CD_CUDA(cudaStreamSynchronize(s));
+    st = fs;
+    st.iters += base_iters;
+    st.levels = (int32_t)taken.size();
+    st.ncomm = (int32_t)k;
+}
+
 }  // namespace cd

@@ -126,6 +126,10 @@ void run_plm(const GraphView &g, bool refine, const RunOpts &o, int32_t *labels,
 void run_plp(const GraphView &g, const RunOpts &o, double theta, int32_t *labels, RunStats &st, cudaStream_t s);
 void run_epp(const GraphView &g, int b, bool final_refine, const RunOpts &o, double theta, int32_t *labels,
              RunStats &st, cudaStream_t s);
+// EPP(b, Base, Final) with up to `rounds` ensemble rounds (cd_epp_general).
+enum { EPP_BASE_PLP = 0, EPP_BASE_PLM = 1, EPP_BASE_PLMR = 2 };
+void run_epp_general(const GraphView &g, int b, int base, bool final_refine, int rounds, const RunOpts &o,
+                     double theta, int32_t *labels, RunStats &st, cudaStream_t s);
 
 // Class trace of the move phases run with RunOpts::trace (profile level 2):
 // TRACE_FIELDS int64 per class step, appended in completion order.

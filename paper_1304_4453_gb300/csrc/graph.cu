@@ -110,10 +110,12 @@ __global__ void k_volumes(int64_t n, const int64_t *rp, const void *w, int wk, c
     }
 }
 
-void finish_graph(OwnedGraph &g, cudaStream_t s) {
+void finish_graph(OwnedGraph &g, cudaStream_t s, bool borrowed) {
     GraphView &v = g.view;
-    v.rp = g.rp.p;
-    v.col = g.col.p;
+    if (!borrowed) {   // else rp and col already point at the caller's arrays
+        v.rp = g.rp.p;
+        v.col = g.col.p;
+    }
     v.self = g.self.p;
     g.vol.alloc(v.n, s);
     v.vol = g.vol.p;
@@ -140,7 +142,7 @@ void build_graph(int64_t n, const int64_t *rp_in, const int32_t *col_in, const i
     if (mem == CD_MEM_HOST) {
         first = rp_in[0];
         nnz = rp_in[n];
-    } else if (mem == CD_MEM_DEVICE) {
+    } else if (mem == CD_MEM_DEVICE || mem == CD_BORROW) {
         CD_CUDA(cudaMemcpy(&first, rp_in, sizeof(int64_t), cudaMemcpyDeviceToHost));
         CD_CUDA(cudaMemcpy(&nnz, rp_in + n, sizeof(int64_t), cudaMemcpyDeviceToHost));
     } else {
@@ -148,23 +150,33 @@ void build_graph(int64_t n, const int64_t *rp_in, const int32_t *col_in, const i
     }
     if (first != 0 || nnz < 0) raise(CD_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
     if (nnz > 0 && !col_in) raise(CD_EINVAL, "col is NULL");
+    const bool borrow = mem == CD_BORROW;
     cudaMemcpyKind kind = mem == CD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
 
-    // staging copies of the input
-    DBuf<int64_t> rp(n + 1, s);
-    DBuf<int32_t> col(nnz, s);
+    // staging copies of the input (borrowed arrays are read in place)
+    DBuf<int64_t> rp;
+    DBuf<int32_t> col;
     DBuf<int32_t> w;
-    CD_CUDA(cudaMemcpyAsync(rp.p, rp_in, (n + 1) * sizeof(int64_t), kind, s));
-    if (nnz) CD_CUDA(cudaMemcpyAsync(col.p, col_in, nnz * sizeof(int32_t), kind, s));
-    if (w_in) {
-        w.alloc(nnz, s);
-        if (nnz) CD_CUDA(cudaMemcpyAsync(w.p, w_in, nnz * sizeof(int32_t), kind, s));
+    const int64_t *rp_d = rp_in;
+    const int32_t *col_d = col_in, *w_d = w_in;
+    if (!borrow) {
+        rp.alloc(n + 1, s);
+        col.alloc(nnz, s);
+        CD_CUDA(cudaMemcpyAsync(rp.p, rp_in, (n + 1) * sizeof(int64_t), kind, s));
+        if (nnz) CD_CUDA(cudaMemcpyAsync(col.p, col_in, nnz * sizeof(int32_t), kind, s));
+        if (w_in) {
+            w.alloc(nnz, s);
+            if (nnz) CD_CUDA(cudaMemcpyAsync(w.p, w_in, nnz * sizeof(int32_t), kind, s));
+        }
+        rp_d = rp.p;
+        col_d = col.p;
+        w_d = w_in ? w.p : nullptr;
     }
     DBuf<int> err(1, s);
     err.zero();
     DBuf<int32_t> loops(n + 1, s);
     if (n) {
-        { k_validate<<<grid_for(n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(n, nnz, rp.p, col.p, w_in ? w.p : nullptr,
+        { k_validate<<<grid_for(n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(n, nnz, rp_d, col_d, w_d,
                                                                         err.p, loops.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
     }
@@ -194,7 +206,14 @@ void build_graph(int64_t n, const int64_t *rp_in, const int32_t *col_in, const i
     v.nnz = m_nnz;
     v.wk = w_in ? W_I32 : W_UNIT;
     out.self.alloc(n, s);
-    if (nloops == 0) {
+    bool borrowed = false;
+    if (nloops == 0 && borrow) {
+        v.rp = rp_d;
+        v.col = col_d;
+        v.w = w_d;
+        out.self.zero();
+        borrowed = true;
+    } else if (nloops == 0) {
         out.rp = std::move(rp);
         out.col = std::move(col);
         if (w_in) out.w32 = std::move(w);
@@ -205,15 +224,15 @@ void build_graph(int64_t n, const int64_t *rp_in, const int32_t *col_in, const i
         if (w_in) out.w32.alloc(m_nnz, s);
         unsigned gb = grid_for(n * 32, kBlock, 152 * 64);
         if (w_in)
-            { k_strip_loops<true><<<gb, kBlock, 0, s>>>(n, rp.p, col.p, w.p, loops_before.p, out.rp.p, out.col.p,
+            { k_strip_loops<true><<<gb, kBlock, 0, s>>>(n, rp_d, col_d, w_d, loops_before.p, out.rp.p, out.col.p,
                                                      out.w32.p, out.self.p); ::cd::note_launch(); }
         else
-            { k_strip_loops<false><<<gb, kBlock, 0, s>>>(n, rp.p, col.p, nullptr, loops_before.p, out.rp.p, out.col.p,
+            { k_strip_loops<false><<<gb, kBlock, 0, s>>>(n, rp_d, col_d, nullptr, loops_before.p, out.rp.p, out.col.p,
                                                       nullptr, out.self.p); ::cd::note_launch(); }
         CD_LAUNCH_CHECK();
     }
-    v.w = w_in ? (const void *)out.w32.p : nullptr;
-    finish_graph(out, s);
+    if (!borrowed) v.w = w_in ? (const void *)out.w32.p : nullptr;
+    finish_graph(out, s, borrowed);
 }
 
 // ---------------------------------------------------------------------------

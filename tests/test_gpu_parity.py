@@ -326,3 +326,36 @@ def test_adjacent_hubs_share_classes(O, nh, leaves, seed):
     r = G.epp(b=3, seed=4)
     o = O.epp(*g.numpy(), b=3, seed=4)
     assert np.array_equal(_np_labels(r.labels), o.labels)
+
+
+@pytest.mark.parametrize("name", ["rmat14_hubs", "rand_w_loops", "chunglu_w"])
+def test_borrowed_csr_gives_identical_results(O, name):
+    """CD_BORROW: the handle reads the caller's device arrays in place (with
+    self-loops it keeps only a loop-free copy); every result equals the
+    copying handle's and the oracle's."""
+    g = GRAPHS[name].to("cuda")
+    rp, col = g.row_ptr.contiguous(), g.col.contiguous()
+    w = None if g.w is None else g.w.contiguous()
+    B = cd.Graph(rp, col, w, borrow=True)
+    C = cd.Graph(rp.clone(), col.clone(), None if w is None else w.clone())
+    assert (B.n, B.m, B.W) == (C.n, C.m, C.W)
+    for fn in (lambda G: G.plm(seed=2), lambda G: G.plm(refine=True, seed=2), lambda G: G.plp(seed=2),
+               lambda G: G.epp(b=3, seed=2)):
+        rb, rc = fn(B), fn(C)
+        assert torch.equal(rb.labels, rc.labels) and rb.modularity == rc.modularity
+    o = O.plm(*GRAPHS[name].numpy(), refine=True, seed=2)
+    assert np.array_equal(B.plm(refine=True, seed=2).labels.cpu().numpy(), o.labels)
+    lab = B.plm(seed=2).labels
+    assert B.modularity(lab) == C.modularity(lab)
+    rpx, colx, wx = cd.cd_graph_export(B.h)
+    rpy, coly, wy = cd.cd_graph_export(C.h)
+    assert np.array_equal(rpx, rpy) and np.array_equal(colx, coly) and np.array_equal(wx, wy)
+    B.close()
+    C.close()
+
+
+def test_borrow_rejects_host_arrays():
+    g = GRAPHS["rmat12"]
+    with pytest.raises(cd.CDError) as e:
+        cd.Graph(g.row_ptr, g.col, g.w, borrow=True)
+    assert e.value.status == cd.CD_EINVAL

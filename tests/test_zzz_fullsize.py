@@ -18,7 +18,9 @@ seed 1 (4,194,304 vertices, 128M CSR entries), and Chung-Lu n = 16M,
 exponent 2.1, degrees 4..1e5, weights 1..100, seed 1, whose 2W >= 2^31
 takes the 128-bit gain path.  Properties that hold at any size
 (tests/properties.py, pinned in tests/test_properties_cpu.py) are checked
-as well.
+as well.  R-MAT scale 26 (about 2.1 billion CSR entries), where a borrowed
+device CSR (CD_BORROW) spares the graph's second copy, is checked against the
+copying handle and the properties.
 
 This file is collected last: it holds the largest graphs of the suite.
 """
@@ -148,3 +150,24 @@ def test_chunglu16m_plmr_equals_oracle(chunglu16m):
     assert 2 * G.W >= 2**31          # the 128-bit gain path
     r = G.plm(refine=True, seed=1)
     _check_run(r, rec["plmr"], STAT_KEYS)
+
+
+def test_rmat26_borrowed_equals_copied():
+    """R-MAT scale 26, edge factor 16 (67M vertices, 2.1 billion CSR entries,
+    64-bit row offsets): PLM on a handle that borrows the device CSR
+    and on one that copies it gives identical labels and modularity, and the
+    labels are a dense partition carrying their exact modularity."""
+    g = synth.rmat(26, 16, 0.57, 0.19, 0.19, seed=1, device="cuda")
+    assert g.n == 1 << 26 and g.nnz > 2_000_000_000
+    B = cd.Graph(g.row_ptr, g.col, g.w, borrow=True)
+    rb = B.plm(refine=False, seed=1)
+    lab_b = rb.labels.cpu()
+    B.close()
+    C = cd.Graph(g.row_ptr, g.col, g.w)
+    rc = C.plm(refine=False, seed=1)
+    assert torch.equal(lab_b, rc.labels.cpu()) and rb.modularity == rc.modularity
+    assert rb.stats["converged"] == 1
+    assert P.check_dense_labels(lab_b.numpy()) == rb.stats["ncomm"]
+    assert abs(C.modularity(rc.labels) - rb.modularity) <= MOD_TOL
+    C.close()
+
