@@ -108,6 +108,16 @@ enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1, CD_BORROW = 2 };
  *               with their exact modularity.  The level loop also stops when
  *               coarsening no longer merges vertices.  PLP and EPP's base runs
  *               keep the colour classes.  128 rounds are the binding's default.
+ *   scratch_budget  0 (default), or the low-memory mode (the GPU analogue
+ *               of the paper's memory-lean PLM*, Section III-B): coarsening,
+ *               whose sort scratch otherwise takes about 52 bytes per
+ *               inter-community adjacency entry of a level (the largest
+ *               working buffer of a run), processes ranges of coarse rows so
+ *               that one pass uses at most this many bytes (a single coarse
+ *               row above the budget forms a pass of its own).  A level's
+ *               schedule (colour classes and hub tables) is also freed once
+ *               its move phase is done and rebuilt for PLMR's refinement on
+ *               the way up.  Slower, same results.
  * cd_tune picks team_quantum, team_min and bin_max by measurement. */
 typedef struct {
     uint64_t seed;
@@ -123,6 +133,7 @@ typedef struct {
     int64_t res_den;    /*   and of EPP's final phase (1 / 1: modularity) */
     int32_t schedule;   /* 0: colour classes (deterministic); R >= 1: racy, R rounds */
     int32_t reserved2;  /* 0 */
+    int64_t scratch_budget;   /* low-memory mode: bytes of coarsening scratch; 0: none */
 } cd_opts;
 
 /* Run statistics (all optional: pass NULL to skip). */
@@ -350,6 +361,13 @@ cd_status cd_modularity_static(int64_t n, const int64_t *row_ptr, const int32_t 
 /* Number of CUDA kernels this library has launched since it was loaded
  * (all threads, all devices). */
 uint64_t cd_launch_count(void);
+
+/* Device memory of the library's pool on the current device, in bytes: in
+ * use now, the high-water mark of use since the last reset (reset_high != 0
+ * restarts it after reading), and reserved from the driver (freed memory
+ * stays reserved for later runs).  Any pointer may be NULL.  Errors:
+ * CD_ECUDA. */
+cd_status cd_memory_stats(uint64_t *used, uint64_t *used_high, uint64_t *reserved, int reset_high);
 
 /* Testing hook: the k-th device allocation from now fails with CD_ENOMEM
  * (k <= 0 disables).  Used to check that failures leak nothing. */

@@ -39,7 +39,7 @@ class cd_opts(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("team_quantum", ctypes.c_int64),
                 ("team_min", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("bin_max", ctypes.c_int32 * 5), ("res_num", ctypes.c_int64), ("res_den", ctypes.c_int64),
-                ("schedule", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("reserved2", ctypes.c_int32), ("scratch_budget", ctypes.c_int64)]
 
 
 class cd_stats(ctypes.Structure):
@@ -75,7 +75,8 @@ SYMBOLS = ["cd_opts_default", "cd_status_str", "cd_last_error", "cd_graph_create
            "cd_epp", "cd_color", "cd_coarsen", "cd_graph_export", "cd_debug_fail_alloc",
            "cd_launch_count", "cd_modularity_static", "cd_run_batch", "cd_plm_batch",
            "cd_server_create", "cd_server_submit", "cd_server_poll", "cd_server_info",
-           "cd_server_destroy", "cd_tune", "cd_debug_plan_launch", "cd_debug_class_trace", "cd_epp_general"]
+           "cd_server_destroy", "cd_tune", "cd_debug_plan_launch", "cd_debug_class_trace", "cd_epp_general",
+           "cd_memory_stats"]
 
 
 def library_path() -> str:
@@ -103,6 +104,7 @@ def lib():
             L.cd_plm.argtypes = [P, c_int, P, P, c_int, P, P]
             L.cd_epp.argtypes = [P, c_int, c_int, P, P, c_int, P, P]
             L.cd_epp_general.argtypes = [P, c_int, c_int, c_int, c_int, P, P, c_int, P, P]
+            L.cd_memory_stats.argtypes = [P, P, P, c_int]
             L.cd_color.argtypes = [P, ctypes.c_uint64, P, c_int, P]
             L.cd_coarsen.argtypes = [P, P, c_int, P]
             L.cd_graph_export.argtypes = [P, P, P, P, c_int, P]
@@ -171,7 +173,8 @@ RACY_ROUNDS = 128
 
 def default_opts(seed: int = 1, max_sweeps: int = 256, max_levels: int = 64,
                  max_iters: int = 1000, profile: bool = False, team_quantum: int = 0,
-                 team_min: int = 0, bin_max=None, resolution=(1, 1), racy=False) -> cd_opts:
+                 team_min: int = 0, bin_max=None, resolution=(1, 1), racy=False,
+                 scratch_budget: int = 0) -> cd_opts:
     """Options; resolution = (p, q) is gamma = p / q of the PLM move gain;
     racy selects the paper's nondeterministic schedule (no colouring): True
     for RACY_ROUNDS hash rounds per sweep, or an int for that many."""
@@ -180,6 +183,7 @@ def default_opts(seed: int = 1, max_sweeps: int = 256, max_levels: int = 64,
     o.seed, o.max_sweeps, o.max_levels, o.max_iters, o.profile = seed, max_sweeps, max_levels, max_iters, int(profile)
     o.res_num, o.res_den = int(resolution[0]), int(resolution[1])
     o.schedule = (RACY_ROUNDS if racy is True else int(racy)) if racy else 0
+    o.scratch_budget = int(scratch_budget)
     if team_quantum:
         o.team_quantum = team_quantum
     if team_min:
@@ -260,6 +264,13 @@ def cd_epp(h, labels_out, ensemble_size: int = 4, final_refine: bool = True, opt
     return _run(lib().cd_epp, h,
                 lambda lp, mem, mp, sp: (int(ensemble_size), int(final_refine), ctypes.byref(o), lp, mem, mp, sp),
                 labels_out)
+
+
+def cd_memory_stats(reset_high: bool = False):
+    """(used, used_high, reserved) bytes of the library's device pool."""
+    u, hgh, r = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().cd_memory_stats(ctypes.byref(u), ctypes.byref(hgh), ctypes.byref(r), int(reset_high)), False)
+    return u.value, hgh.value, r.value
 
 
 CD_BASE_PLP, CD_BASE_PLM, CD_BASE_PLMR = 0, 1, 2

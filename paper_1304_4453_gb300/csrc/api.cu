@@ -74,6 +74,7 @@ void cd_opts_default(cd_opts *o) {
     o->res_den = 1;
     o->schedule = 0;
     o->reserved2 = 0;
+    o->scratch_budget = 0;
 }
 
 const char *cd_status_str(cd_status s) {
@@ -337,5 +338,12 @@ cd_status cd_debug_class_trace(int64_t *out, int64_t cap, int64_t *count) {
 }
 
 uint64_t cd_launch_count(void) { return launch_count(); }
+
+cd_status cd_memory_stats(uint64_t *used, uint64_t *used_high, uint64_t *reserved, int reset_high) {
+    return guarded([&]() {
+        pool_stats(used, used_high, reserved, reset_high != 0);
+        return CD_OK;
+    });
+}
 
 }  // extern "C"

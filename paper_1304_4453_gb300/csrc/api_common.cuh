@@ -60,6 +60,8 @@ inline RunOpts to_run(const cd_opts *o) {
     if (o->schedule < 0 || o->schedule > 4096)
         raise(CD_EINVAL, "schedule %d: 0 (colour classes) or 1..4096 (racy rounds per sweep)", o->schedule);
     r.racy = o->schedule;
+    if (o->scratch_budget < 0) raise(CD_EINVAL, "scratch_budget must be >= 0");
+    r.scratch_budget = o->scratch_budget;
     r.team_quantum = o->team_quantum;
     r.team_min = o->team_min;
     for (int i = 0; i < NLIM; i++) {

@@ -45,6 +45,9 @@ void set_last_error(const std::string &m);
 void note_launch();
 uint64_t launch_count();
 
+// Bytes of the library's device pool on the current device: in use now, the
+// high-water mark of use (reset_high restarts it), and reserved.
+void pool_stats(uint64_t *used, uint64_t *used_high, uint64_t *reserved, bool reset_high);
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);
 // Test hook: make the k-th next allocation fail with CD_ENOMEM (k <= 0: off).
@@ -279,8 +282,10 @@ struct OwnedGraph {
 // Coarsening (coarsen.cu): one coarse vertex per distinct label.  Computes
 // the dense ranks of the labels into rank_of_label (n entries) and builds the
 // coarse graph.
+// scratch_budget > 0 (the low-memory mode): the sort scratch of one pass
+// stays within that many bytes; ranges of coarse rows are coarsened in turn.
 void coarsen_graph(const GraphView &g, const int32_t *labels, int64_t *rank_of_label,
-                   OwnedGraph &out, cudaStream_t s);
+                   OwnedGraph &out, cudaStream_t s, int64_t scratch_budget = 0);
 
 }  // namespace cd
 

@@ -821,7 +821,7 @@ static void advance_impl(Job &j, cudaStream_t s) {
             x.base.release();
             auto t = Clock::now();
             x.core_rank.alloc(n0, s);
-            coarsen_graph(sp.g, x.core.p, x.core_rank.p, x.cg, s);
+            coarsen_graph(sp.g, x.core.p, x.core_rank.p, x.cg, s, sp.o.scratch_budget);
             x.core_rank.release();
             st.ms_coarsen += ms_since(t);
             x.g = x.cg.view;
@@ -841,10 +841,11 @@ static void advance_impl(Job &j, cudaStream_t s) {
                 x.stage = ST_UP;
                 break;
             }
+            if (sp.o.scratch_budget > 0) lv.S = Schedule();   // low-memory mode: rebuilt if a refinement needs it
             auto t = Clock::now();
             lv.rank.alloc(lv.g.n, s);
             auto nx = std::make_unique<Level>();
-            coarsen_graph(lv.g, lv.zeta.p, lv.rank.p, nx->own, s);
+            coarsen_graph(lv.g, lv.zeta.p, lv.rank.p, nx->own, s, sp.o.scratch_budget);
             st.ms_coarsen += ms_since(t);
             if (sp.o.racy > 0 && nx->own.view.n == lv.g.n) {
                 // the racy schedule's moves only exchanged labels (every community
@@ -873,6 +874,13 @@ static void advance_impl(Job &j, cudaStream_t s) {
             CD_LAUNCH_CHECK();
             x.L.pop_back();
             if (sp.refine) {
+                if (lv.S.ncol == 0 && lv.g.n > 0) {
+                    // low-memory mode freed this level's schedule: the same
+                    // seed colours the level again into the same classes
+                    auto t = Clock::now();
+                    build_schedule(lv.g, sp.o.seed, sp.o.bins, lv.S, s, sp.o.racy);
+                    st.ms_color += ms_since(t);
+                }
                 x.run = prepare_move(lv.g, lv.S, lv.zeta.p, nullptr, sp.o, s);
                 x.stage = ST_UP_WAIT;
                 return;
@@ -1370,7 +1378,7 @@ void run_epp_general(const GraphView &g, int b, int base, bool final_refine, int
         if (r > 0 && (k == nc || q <= prev)) break;     // no contraction or no gain
         prev = q;
         rd->rank.alloc(nc, s);
-        coarsen_graph(cur, rd->core.p, rd->rank.p, rd->cg, s);
+        coarsen_graph(cur, rd->core.p, rd->rank.p, rd->cg, s, o.scratch_budget);
         cur = rd->cg.view;
         taken.push_back(std::move(rd));
     }

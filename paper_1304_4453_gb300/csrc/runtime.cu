@@ -70,6 +70,18 @@ void *dev_alloc(size_t bytes, cudaStream_t s) {
     return p;
 }
 
+void pool_stats(uint64_t *used, uint64_t *used_high, uint64_t *reserved, bool reset_high) {
+    cudaMemPool_t p = pool_for_current_device();
+    uint64_t v = 0;
+    if (used) { CD_CUDA(cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemCurrent, &v)); *used = v; }
+    if (used_high) { CD_CUDA(cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemHigh, &v)); *used_high = v; }
+    if (reserved) { CD_CUDA(cudaMemPoolGetAttribute(p, cudaMemPoolAttrReservedMemCurrent, &v)); *reserved = v; }
+    if (reset_high) {
+        uint64_t zero = 0;
+        CD_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+}
+
 void dev_free(void *p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);  // never throws (destructors)
 }

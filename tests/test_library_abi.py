@@ -51,17 +51,18 @@ def test_option_defaults_and_struct_layout(tmp_path):
     schedule, and the binding's structs have the header's layout (a C
     program compiled against include/cd.h reports sizes and offsets)."""
     o = cd.default_opts()
-    assert (o.res_num, o.res_den, o.schedule) == (1, 1, 0)
+    assert (o.res_num, o.res_den, o.schedule, o.scratch_budget) == (1, 1, 0, 0)
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "cd.h"\n'
-        'int main(void) { printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(cd_opts), offsetof(cd_opts, bin_max),'
+        'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(cd_opts), offsetof(cd_opts, bin_max),'
         ' offsetof(cd_opts, res_num), offsetof(cd_opts, res_den), offsetof(cd_opts, schedule),'
-        ' sizeof(cd_stats)); return 0; }\n')
+        ' sizeof(cd_stats), offsetof(cd_opts, scratch_budget)); return 0; }\n')
     exe = tmp_path / "layout"
     import subprocess
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(cd.cd_opts), cd.cd_opts.bin_max.offset, cd.cd_opts.res_num.offset,
-            cd.cd_opts.res_den.offset, cd.cd_opts.schedule.offset, ctypes.sizeof(cd.cd_stats)]
+            cd.cd_opts.res_den.offset, cd.cd_opts.schedule.offset, ctypes.sizeof(cd.cd_stats),
+            cd.cd_opts.scratch_budget.offset]
     assert got == want

@@ -154,13 +154,16 @@ def test_chunglu16m_plmr_equals_oracle(chunglu16m):
 
 def test_rmat26_borrowed_equals_copied():
     """R-MAT scale 26, edge factor 16 (67M vertices, 2.1 billion CSR entries,
-    64-bit row offsets): PLM on a handle that borrows the device CSR
-    and on one that copies it gives identical labels and modularity, and the
+    64-bit row offsets): PLM on a handle that borrows the device CSR, run in
+    the low-memory mode (8 GiB of coarsening scratch), and on a copying
+    handle in the default mode give identical labels and modularity, and the
     labels are a dense partition carrying their exact modularity."""
     g = synth.rmat(26, 16, 0.57, 0.19, 0.19, seed=1, device="cuda")
     assert g.n == 1 << 26 and g.nnz > 2_000_000_000
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()   # the generator's scratch goes back before the library allocates
     B = cd.Graph(g.row_ptr, g.col, g.w, borrow=True)
-    rb = B.plm(refine=False, seed=1)
+    rb = B.plm(refine=False, seed=1, scratch_budget=8 << 30)   # and the low-memory mode
     lab_b = rb.labels.cpu()
     B.close()
     C = cd.Graph(g.row_ptr, g.col, g.w)
