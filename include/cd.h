@@ -108,6 +108,11 @@ enum { CD_MEM_HOST = 0, CD_MEM_DEVICE = 1, CD_BORROW = 2 };
  *               with their exact modularity.  The level loop also stops when
  *               coarsening no longer merges vertices.  PLP and EPP's base runs
  *               keep the colour classes.  128 rounds are the binding's default.
+ *   int_path    0 (default): the move gains are computed in 64 bits when
+ *               max(res_num, res_den) (2W)^2 < 2^63 and 2W < 2^31, else in 128
+ *               bits; 128 forces the 128-bit path (same results); 64 demands
+ *               the 64-bit path and fails with CD_EINVAL where it would not be
+ *               exact.
  *   scratch_budget  0 (default), or the low-memory mode (the GPU analogue
  *               of the paper's memory-lean PLM*, Section III-B): coarsening,
  *               whose sort scratch otherwise takes about 52 bytes per
@@ -132,7 +137,7 @@ typedef struct {
     int64_t res_num;    /* resolution gamma = res_num / res_den of PLM / PLMR */
     int64_t res_den;    /*   and of EPP's final phase (1 / 1: modularity) */
     int32_t schedule;   /* 0: colour classes (deterministic); R >= 1: racy, R rounds */
-    int32_t reserved2;  /* 0 */
+    int32_t int_path;   /* gain width of PLM: 0 automatic, 64 or 128 */
     int64_t scratch_budget;   /* low-memory mode: bytes of coarsening scratch; 0: none */
 } cd_opts;
 

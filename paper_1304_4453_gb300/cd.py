@@ -39,7 +39,7 @@ class cd_opts(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("team_quantum", ctypes.c_int64),
                 ("team_min", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("bin_max", ctypes.c_int32 * 5), ("res_num", ctypes.c_int64), ("res_den", ctypes.c_int64),
-                ("schedule", ctypes.c_int32), ("reserved2", ctypes.c_int32), ("scratch_budget", ctypes.c_int64)]
+                ("schedule", ctypes.c_int32), ("int_path", ctypes.c_int32), ("scratch_budget", ctypes.c_int64)]
 
 
 class cd_stats(ctypes.Structure):
@@ -174,7 +174,7 @@ RACY_ROUNDS = 128
 def default_opts(seed: int = 1, max_sweeps: int = 256, max_levels: int = 64,
                  max_iters: int = 1000, profile: bool = False, team_quantum: int = 0,
                  team_min: int = 0, bin_max=None, resolution=(1, 1), racy=False,
-                 scratch_budget: int = 0) -> cd_opts:
+                 scratch_budget: int = 0, int_path: int = 0) -> cd_opts:
     """Options; resolution = (p, q) is gamma = p / q of the PLM move gain;
     racy selects the paper's nondeterministic schedule (no colouring): True
     for RACY_ROUNDS hash rounds per sweep, or an int for that many."""
@@ -184,6 +184,7 @@ def default_opts(seed: int = 1, max_sweeps: int = 256, max_levels: int = 64,
     o.res_num, o.res_den = int(resolution[0]), int(resolution[1])
     o.schedule = (RACY_ROUNDS if racy is True else int(racy)) if racy else 0
     o.scratch_budget = int(scratch_budget)
+    o.int_path = int(int_path)
     if team_quantum:
         o.team_quantum = team_quantum
     if team_min:

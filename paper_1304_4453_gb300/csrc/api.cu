@@ -73,7 +73,7 @@ void cd_opts_default(cd_opts *o) {
     o->res_num = 1;
     o->res_den = 1;
     o->schedule = 0;
-    o->reserved2 = 0;
+    o->int_path = 0;
     o->scratch_budget = 0;
 }
 

@@ -62,6 +62,9 @@ inline RunOpts to_run(const cd_opts *o) {
     r.racy = o->schedule;
     if (o->scratch_budget < 0) raise(CD_EINVAL, "scratch_budget must be >= 0");
     r.scratch_budget = o->scratch_budget;
+    if (o->int_path != 0 && o->int_path != 64 && o->int_path != 128)
+        raise(CD_EINVAL, "int_path %d: 0 (automatic), 64 or 128", o->int_path);
+    r.int_path = o->int_path;
     r.team_quantum = o->team_quantum;
     r.team_min = o->team_min;
     for (int i = 0; i < NLIM; i++) {

@@ -509,7 +509,9 @@ static std::unique_ptr<PhaseRun> prepare_move(const GraphView &g, const Schedule
     if (!gain_fits_128(g.W, o.res_p, o.res_q))
         raise(CD_EINVAL, "resolution %lld / %lld: max(p, q) (2W)^2 reaches 2^126 for 2W = %lld",
               (long long)o.res_p, (long long)o.res_q, (long long)(2 * g.W));
-    r->big = gain_needs_big(g.W, o.res_p, o.res_q);
+    r->big = o.int_path == 128 || gain_needs_big(g.W, o.res_p, o.res_q);
+    if (o.int_path == 64 && r->big)
+        raise(CD_EINVAL, "int_path 64: the gains of this graph and resolution need 128 bits");
     r->profile = o.profile;
     r->work = g.nnz + n;
     r->quantum = o.team_quantum;

@@ -31,6 +31,7 @@ struct RunOpts {
     int64_t res_p = 1, res_q = 1;   // PLM resolution gamma = res_p / res_q (reduced)
     int32_t racy = 0;            // > 0: the racy schedule with this many hash rounds per sweep (not deterministic)
     int64_t scratch_budget = 0;  // > 0: low-memory mode, bytes of coarsening scratch per pass
+    int32_t int_path = 0;        // gain width: 0 the narrowest exact one, 64, or 128
     int64_t team_quantum = int64_t(1) << 18;   // launch shape (speed only)
     int32_t team_min = 8;
     BinLimits bins{{4, 16, 128, BLK_MAXDEG, BLK_MAXDEG}};  // schedule degree bins (speed only)

@@ -359,3 +359,29 @@ def test_borrow_rejects_host_arrays():
     with pytest.raises(cd.CDError) as e:
         cd.Graph(g.row_ptr, g.col, g.w, borrow=True)
     assert e.value.status == cd.CD_EINVAL
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_forced_128_bit_gains_change_nothing(O, name):
+    """int_path 128 runs the 128-bit gain path on graphs whose gains fit 64
+    bits: the decisions, and so every result, are the same."""
+    g = GRAPHS[name]
+    G = gpu_graph(g)
+    for refine in (False, True):
+        r = G.plm(refine=refine, seed=3, int_path=128)
+        o = O.plm(*g.numpy(), refine=refine, seed=3)
+        assert np.array_equal(_np_labels(r.labels), o.labels)
+        _same_stats(r.stats, o.stats, ["levels", "sweeps", "moves", "entries", "candidates", "decisions"])
+
+
+def test_int_path_64_rejected_where_inexact():
+    base = synth.random_graph(400, 2500, seed=21, loops=10, wmax=50)
+    w = (base.w.to(torch.int64) * 3_000_000 + 7).clamp(max=2**31 - 1).to(torch.int32)
+    G = gpu_graph(synth.Graph(base.n, base.row_ptr, base.col, w, "heavy"))
+    with pytest.raises(cd.CDError) as e:
+        G.plm(int_path=64)
+    assert e.value.status == cd.CD_EINVAL
+    H = gpu_graph(GRAPHS["rmat12"])
+    assert H.plm(int_path=64).stats["converged"] == 1
+    with pytest.raises(cd.CDError):
+        H.plm(int_path=32)

@@ -51,7 +51,7 @@ def test_option_defaults_and_struct_layout(tmp_path):
     schedule, and the binding's structs have the header's layout (a C
     program compiled against include/cd.h reports sizes and offsets)."""
     o = cd.default_opts()
-    assert (o.res_num, o.res_den, o.schedule, o.scratch_budget) == (1, 1, 0, 0)
+    assert (o.res_num, o.res_den, o.schedule, o.scratch_budget, o.int_path) == (1, 1, 0, 0, 0)
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "cd.h"\n'
