@@ -51,8 +51,8 @@ constexpr int GBLK_MAXDEG = 4096;   // role 3b
 constexpr int GT_SLOTS = 8192;      // role 3b table slots per block
 static_assert(GT_SLOTS >= 2 * GBLK_MAXDEG, "role 3b table must hold twice its largest degree");
 constexpr int BLK_SLOTS = 2048;     // block role table (deg <= 1024)
-constexpr int HUB_CHUNK = 256;      // adjacency entries per hub-aggregation item
-constexpr int HUB_CHUNK_SLOTS = 512;  // shared table of one hub-aggregation item
+constexpr int HUB_CHUNK = 512;      // adjacency entries per hub-aggregation item
+constexpr int HUB_CHUNK_SLOTS = 1024;  // shared table of one hub-aggregation item
 constexpr int HUB_SCAN = 1024;      // occupied-list entries per hub-decide slice
 constexpr int HUB_LAST = 2048;      // hubs up to this degree: decided by their last aggregation item
 constexpr int SMEM_BYTES = 32768;   // shared memory the roles may use (the phase kernels' dynamic shared memory)
@@ -390,6 +390,11 @@ __device__ __forceinline__ void role_group(const SweepCtx &c, int64_t rb, const 
     __syncwarp();
     int64_t beg = 0;
     int deg = 0;
+    // the vertex's own label and volume travel with its row offsets: only u
+    // writes zeta[u] during its class
+    const int32_t C = valid ? c.zeta[u] : 0;
+    int64_t vu = 0;
+    if constexpr (!PLP) vu = valid ? c.g.vol[u] : 0;
     if (valid) {
         beg = c.g.rp[u];
         deg = (int)(c.g.rp[u + 1] - beg);
@@ -403,6 +408,8 @@ __device__ __forceinline__ void role_group(const SweepCtx &c, int64_t rb, const 
         const int k = gl + j * G;
         nb[j] = (valid && k < deg) ? c.g.col[beg + k] : -1;
     }
+    int64_t volC = 0;
+    if constexpr (!PLP) volC = valid ? c.volc[C] : 0;
 #pragma unroll
     for (int j = 0; j < PER; j++) nb[j] = nb[j] >= 0 ? c.zeta[nb[j]] : -1;
 #pragma unroll
@@ -410,12 +417,9 @@ __device__ __forceinline__ void role_group(const SweepCtx &c, int64_t rb, const 
         if (nb[j] >= 0)
             tab_insert<VT>(keys, vals, SLOTS - 1, nb[j], (VT)edge_weight<WK>(c.g.w, beg + gl + j * G), &c.cnt->overflow);
     __syncwarp();
-    const int32_t C = valid ? c.zeta[u] : 0;
     const int64_t wC = valid ? (int64_t)tab_lookup<VT>(keys, vals, SLOTS - 1, C) : 0;
     unsigned ncand = 0;
     if constexpr (!PLP) {
-        const int64_t vu = valid ? c.g.vol[u] : 0;
-        const int64_t volC = valid ? c.volc[C] : 0;
         const int64_t twoW = 2 * c.g.W;
         PlmBest<BIG> b;
         b.init();
@@ -512,6 +516,14 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
     }
     const int64_t beg = c.g.rp[u];
     const int deg = (int)(c.g.rp[u + 1] - beg);
+    // own label, volume and community volume early (only u writes zeta[u]
+    // during its class)
+    const int32_t C = c.zeta[u];
+    int64_t vu = 0, volC = 0;
+    if constexpr (!PLP) {
+        vu = c.g.vol[u];
+        volC = c.volc[C];
+    }
     int slots = 64;
     while (slots < 2 * deg) slots <<= 1;
     const uint32_t mask = slots - 1;
@@ -533,12 +545,11 @@ __device__ __forceinline__ void role_block(const SweepCtx &c, int64_t rb, const 
                                &c.cnt->overflow);
     }
     __syncthreads();
-    const int32_t C = c.zeta[u];
     const int64_t wC = GLOBAL ? (int64_t)tab_lookup_cg<VT>(keys, vals, mask, C) : (int64_t)tab_lookup<VT>(keys, vals, mask, C);
     if constexpr (GLOBAL) __syncthreads();   // every lookup is done before slots are emptied
     unsigned ncand = 0;
     if constexpr (!PLP) {
-        const int64_t vu = c.g.vol[u], volC = c.volc[C], twoW = 2 * c.g.W;
+        const int64_t twoW = 2 * c.g.W;
         PlmBest<BIG> b;
         b.init();
         // four slots per thread and step: keys, then candidate volumes, then gains
