@@ -59,6 +59,10 @@ def args_():
     p.add_argument("--serve-slots", type=int, default=64)
     p.add_argument("--cpu-oracle-child", nargs=4, default=None, metavar=("KIND", "SIZE", "ALGO", "THREADS"),
                    help=argparse.SUPPRESS)
+    p.add_argument("--no-extras", action="store_true",
+                   help="leave out the batch, serve and EPP sub-objects of the default line")
+    p.add_argument("--extra-batch-graphs", type=int, default=128)
+    p.add_argument("--extra-serve-requests", type=int, default=100)
     return p.parse_args()
 
 
@@ -480,6 +484,12 @@ def run_ours(a):
                        "rounds decide on live data in the first four sweeps of a move phase, later sweeps "
                        "re-check wanted moves with neighbour stamps); results vary between runs"}
 
+    # bounded forms of the batched and served workloads and EPP where its
+    # bases disagree (context, outside the timed region; single process)
+    batch = serve = epp = None
+    if wl["algo"] == "plm" and not a.no_extras and world == 1:
+        batch, serve, epp = extras(a, dev, ranks)
+
     # one PLP run on the same graph (context, outside the timed region)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -524,6 +534,9 @@ def run_ours(a):
         "plp": {"edges_per_s": g.m / plp_s, "modularity": plp_mod, "iters": plp_st["iters"],
                 "communities": plp_st["ncomm"]},
         "racy": racy,
+        "batch": batch,
+        "serve": serve,
+        "epp": epp,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz + (0 if g.w is None else 4 * g.nnz),
                 "d2h_bytes_per_step": 4 * g.n, "labels_match_device_run": e2e_ok},
@@ -536,6 +549,51 @@ def run_ours(a):
                          "(uk-2007-05, 3.3B edges); context only",
     }
     print(json.dumps(line), flush=True)
+
+
+def extras(a, dev, ranks):
+    """Sub-objects of the default line: the batched workload on its first
+    graphs, the serving workload on its first requests, and EPP(4, PLP, PLMR)
+    on graphs where the PLP bases disagree."""
+    import torch
+    from paper_1304_4453_gb300 import cd, synth
+    b = argparse.Namespace(**vars(a))
+    b.batch_graphs, b.steps, b.warmup, b.tune = a.extra_batch_graphs, 2, 1, 0
+    bl = batch_line(b, dev, ranks)
+    batch = {k: bl[k] for k in ("metric", "value", "unit", "ms_per_step", "plain", "speedup_vs_plain",
+                                "labels_identical_to_plain", "edges_per_s", "e2e", "generation_s", "clocks")}
+    batch["config"] = bl["config"]
+    batch["sample"] = f"the first {b.batch_graphs} graphs of the 512-graph batch, 2 timed batched calls"
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    v = argparse.Namespace(**vars(a))
+    v.serve_requests = a.extra_serve_requests
+    sl = serve_line(v, dev, ranks)
+    serve = {k: sl[k] for k in ("metric", "value", "unit", "ms_per_step", "latency_ms", "plain_fifo",
+                                "labels_identical_to_plain", "generation_s", "clocks")}
+    serve["config"] = sl["config"]
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    epp = []
+    for name, g in (("planted partition n=10,000 (20 blocks of 500, p_in 0.02, p_out 0.0005)",
+                     synth.planted_partition_config1(device=dev)),
+                    ("Chung-Lu n=1,000,000 (exponent 2.1, degrees 4..1e5, weights 1..100)",
+                     synth.chung_lu(1_000_000, seed=1, device=dev))):
+        G = cd.Graph(g.row_ptr, g.col, g.w)
+        row = {"graph": name, "n": G.n, "m": G.m}
+        for key, fn in (("epp4_plp_plmr", lambda: G.epp(b=4, final_refine=True, seed=1)),
+                        ("plp", lambda: G.plp(seed=1)), ("plmr", lambda: G.plm(refine=True, seed=1))):
+            fn()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            row[key] = {"edges_per_s": G.m / dt, "ms": 1e3 * dt, "modularity": r.modularity,
+                        "communities": r.stats["ncomm"]}
+        epp.append(row)
+        G.close()
+    return batch, serve, epp
 
 
 # ---------------------------------------------------------------------------
@@ -571,6 +629,18 @@ def run_batch_workload(a):
     ranks = Ranks(world, dev)
     build.build()
     cd.lib()
+    line = batch_line(a, dev, ranks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def batch_line(a, dev, ranks):
+    """The batched workload measured on this rank's GPU (a.batch_graphs
+    graphs, a.steps timed batched calls after a.warmup): the JSON line."""
+    import torch
+    from paper_1304_4453_gb300 import cd
+    world = ranks.world
+    local = dev.index if dev.index is not None else 0
     t0 = time.perf_counter()
     Gs = []
     for spec, make in batch_graph_list(a.batch_graphs, dev):
@@ -640,8 +710,6 @@ def run_batch_workload(a):
     e2e_same = all(torch.equal(lh, ob.cpu()) for lh, ob in zip(lab_h, outs_batch))
     e2e_value, _ = ranks.rate(len(Gs), e2e_s)
     h2d = sum(8 * (G.n + 1) + 4 * 2 * G.m for G in Gs)
-    if rank != 0:
-        return
     line = {
         "metric": BATCH_METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1000.0 * s_max, "higher_is_better": True, "scaling": "weak",
@@ -660,7 +728,7 @@ def run_batch_workload(a):
         "generation_s": gen_s,
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ---------------------------------------------------------------------------
@@ -710,29 +778,45 @@ def serve_requests(count, rate, pool):
 
 def run_serve_workload(a):
     import torch
-    from paper_1304_4453_gb300 import build, cd, synth
+    from paper_1304_4453_gb300 import build, cd
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ranks = Ranks(world, dev)
     build.build()
     cd.lib()
+    line = serve_line(a, dev, ranks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serve_line(a, dev, ranks):
+    """The serving workload on this rank's GPU (the first a.serve_requests
+    requests of the Poisson stream): the JSON line.  Only the pool graphs
+    that those requests pick are generated."""
+    import torch
+    from paper_1304_4453_gb300 import cd, synth
+    world = ranks.world
+    local = dev.index if dev.index is not None else 0
     t0 = time.perf_counter()
-    pool = []
-    for kind, par, sd in serve_pool_specs(a.serve_pool):
+    specs = serve_pool_specs(a.serve_pool)
+    arrivals, picks = serve_requests(a.serve_requests, a.serve_rate, len(specs))
+    pool = {}
+    for p in sorted(set(picks)):
+        kind, par, sd = specs[p]
         if kind == "rmat":
             g = synth.rmat(par, EDGE_FACTOR, *ABC, seed=sd, device=dev)
         else:
             g = synth.planted_partition_fast(*par, seed=sd, device=dev)
-        pool.append(cd.Graph(g.row_ptr, g.col, g.w))
+        pool[p] = cd.Graph(g.row_ptr, g.col, g.w)
         del g
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     gen_s = time.perf_counter() - t0
-    arrivals, picks = serve_requests(a.serve_requests, a.serve_rate, len(pool))
     opts = cd.default_opts(seed=1)
-    # warm-up: one run of every size class through both paths
-    for G in pool[:4]:
-        G.plm()
+    # warm-up: a few runs through the library
+    for p in sorted(pool)[:4]:
+        pool[p].plm()
 
     def pct(xs, q):
         xs = sorted(xs)
@@ -783,8 +867,6 @@ def run_serve_workload(a):
     ranks.barrier()
     nreq = len(arrivals)
     value, span_max = ranks.rate(nreq, srv_span)
-    if rank != 0:
-        return
     m_req = sum(pool[p].m for p in picks)
     line = {
         "metric": SERVE_METRIC, "value": value, "unit": "graphs/s", "n_gpus": world,
@@ -792,7 +874,7 @@ def run_serve_workload(a):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"serve{nreq}_poisson{a.serve_rate:g}",
                    "requests": f"first {nreq} requests of a Poisson stream (rate {a.serve_rate:g}/s, seed 7), "
-                               f"each a PLM run on one of {len(pool)} pooled graphs: even pool slots R-MAT "
+                               f"each a PLM run on one of {len(specs)} pooled graphs: even pool slots R-MAT "
                                "scale uniform 14..22 ef16, odd slots planted partition n log-uniform "
                                "[1e3, 4e6], k in [8, 64], degree 16",
                    "edges_requested": m_req, "slots": a.serve_slots,
@@ -807,7 +889,7 @@ def run_serve_workload(a):
                 "note": "requests reference resident graphs; labels stay on the device"},
         "gpu_launches": launches, "generation_s": gen_s, "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_reference_other(a):

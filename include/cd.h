@@ -289,17 +289,22 @@ cd_status cd_tune(cd_graph *const *gs, int count, const cd_task *task, const cd_
 cd_status cd_plm_batch(cd_graph *const *gs, int count, int refine, const cd_opts *o,
                        int32_t *const *labels, int labels_mem, double *mods, cd_stats *st);
 
-/* Server: continuous batching of submitted runs.  A host thread admits
- * queued runs in submission order while at most max_slots run at once and
- * the estimated device memory of the admitted runs stays within
- * device_mem_budget bytes (0: 80% of the device memory free at creation).
- * An admitted run joins the next batched launch, so runs submitted while
+/* Server: continuous batching of submitted runs in two lanes, small runs
+ * (adjacency entries plus vertices up to 2^21) and large runs.  Each lane is
+ * a host thread with its own stream.  Small runs' launches use a quarter of
+ * the device's resident blocks, large runs' launches the rest while small
+ * runs are active and the whole device otherwise, so the lanes' launches run
+ * side by side and a small run does not wait for a large run's phases.  A lane admits
+ * its queued runs in submission order while at most max_slots runs (both
+ * lanes together) are admitted and their estimated device memory stays within
+ * device_mem_budget bytes (0: 80% of the device memory free at creation).  An
+ * admitted run joins its lane's next batched launch, so runs submitted while
  * others are on the GPU overlap with them; a finished run frees its slot and
  * memory at once.  Graphs, labels and volumes of every level stay on the
  * device for the whole run.
  *   max_queue   submitted runs not yet admitted, at most (CD_EBUSY beyond)
- *   stream      cudaStream_t of the batched launches (NULL: the server
- *               creates its own) */
+ *   stream      cudaStream_t of the large lane's launches (NULL: the server
+ *               creates its own; the small lane always has its own) */
 cd_status cd_server_create(size_t device_mem_budget, int max_slots, int max_queue, void *stream, cd_server **out);
 /* Queues `task` on g; g must stay alive until the run's result is taken.
  * ticket receives the run's id.  Errors: CD_EBUSY (queue full), CD_EINVAL

@@ -1199,7 +1199,8 @@ void Engine::launch(std::vector<PhaseRun *> &runs) {
     try {
         for (auto &g : groups) {
             const void *kern = g[0]->plp ? plp_batch_kernel(g[0]->wk, g[0]->big) : move_batch_kernel(g[0]->wk, g[0]->big);
-            const int G = persistent_grid(kern);
+            int G = persistent_grid(kern);
+            if (share_ < 1.0) G = std::max(1, (int)(G * share_));
             ensure_block_tables(G);
             auto is = std::make_unique<Issued>();
             is->plan = plan_launch(g, G);

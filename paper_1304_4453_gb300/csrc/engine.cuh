@@ -88,6 +88,10 @@ class Engine {
     Engine &operator=(const Engine &) = delete;
     void add(Job *j);            // the caller keeps ownership; j stays valid until done
     void step();                 // advances every unfinished job through one phase
+    // Fraction (0, 1] of the device's resident blocks that this engine's
+    // launches use, so that engines with shares summing to at most 1 run
+    // their persistent launches side by side.
+    void set_grid_share(double share) { share_ = share; }
     bool busy() const { return !active_.empty(); }
     size_t active() const { return active_.size(); }
     int64_t launches = 0;        // batched launches so far
@@ -96,6 +100,7 @@ class Engine {
     void launch(std::vector<PhaseRun *> &runs);
     void ensure_block_tables(int blocks);
     cudaStream_t s_;
+    double share_ = 1.0;
     DBuf<int32_t> gt_keys_;            // role-3b tables of the launches
     DBuf<unsigned long long> gt_vals_;
     int gt_blocks_ = 0;

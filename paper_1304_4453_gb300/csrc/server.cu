@@ -1,10 +1,17 @@
 // Server (cd_server_* in include/cd.h): continuous batching of submitted
-// runs.  One host thread owns an Engine; between two engine steps it admits
-// queued runs in submission order while slots and the device-memory budget
-// allow, so a run submitted while others are on the GPU joins the very next
-// batched launch.  Finished runs wait in a table until their owner takes
-// the result.
+// runs in two lanes.  Small runs (adjacency entries plus vertices up to
+// SMALL_WORK) and large runs each have a lane: a host thread owning an
+// Engine and its own stream.  The small lane's launches use a quarter of the
+// device's resident blocks; the large lane's use the rest while small runs
+// are active and the whole device otherwise, so the two lanes' persistent
+// launches run side by side and a small run does not wait for a large run's
+// phases.  Between
+// two engine steps a lane admits its queued runs in submission order while
+// the shared slots and device-memory budget allow, so a run submitted while
+// others are on the GPU joins its lane's very next batched launch.  Finished
+// runs wait in a table until their owner takes the result.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -23,9 +30,13 @@ using Clock = std::chrono::steady_clock;
 
 enum { E_QUEUED, E_RUNNING, E_DONE };
 
+constexpr int64_t SMALL_WORK = int64_t(1) << 21;   // entries + vertices of a small-lane run
+constexpr double SMALL_SHARE = 0.25;               // the small lane's share of the resident blocks
+
 struct Entry {
     uint64_t ticket = 0;
     JobSpec spec;
+    int lane = 1;               // 0: small runs, 1: large runs
     size_t est = 0;
     int state = E_QUEUED;
     std::unique_ptr<Job> job;
@@ -46,8 +57,14 @@ size_t estimate_bytes(const JobSpec &sp) {
 }  // namespace
 
 struct cd_server {
+    struct Lane {
+        std::unique_ptr<Engine> engine;
+        cudaStream_t stream = nullptr;
+        bool own_stream = false;
+        std::thread th;
+    };
     std::mutex mu;
-    std::condition_variable wake;   // server thread: new work or stop
+    std::condition_variable wake;   // lane threads: new work or stop
     std::condition_variable done;   // pollers: a run finished
     std::deque<Entry *> queue;
     std::unordered_map<uint64_t, std::unique_ptr<Entry>> entries;
@@ -57,27 +74,39 @@ struct cd_server {
     uint64_t next_ticket = 1;
     bool stop = false;
     int dev = 0;
-    cudaStream_t stream = nullptr, copy_stream = nullptr;
-    bool own_stream = false;
-    std::unique_ptr<Engine> engine;
-    std::thread th;
+    cudaStream_t copy_stream = nullptr;
+    Lane lanes[2];
+    std::atomic<int> small_active{0};   // runs in the small lane
 
-    bool admissible() const {
-        return !queue.empty() && running < max_slots && used + queue.front()->est <= budget;
+    // The large lane takes the whole device while the small lane is idle and
+    // leaves the small lane its share otherwise (a launch already running
+    // with the whole device delays the small lane by one phase at most).
+    double share(int lane) const {
+        if (lane == 0) return SMALL_SHARE;
+        return small_active.load() > 0 ? 1.0 - SMALL_SHARE : 1.0;
     }
 
-    void loop() {
+    // The lane's first queued run, if it fits the free slots and memory.
+    std::deque<Entry *>::iterator admissible(int lane) {
+        if (running >= max_slots) return queue.end();
+        for (auto it = queue.begin(); it != queue.end(); ++it)
+            if ((*it)->lane == lane) return used + (*it)->est <= budget ? it : queue.end();
+        return queue.end();
+    }
+
+    void loop(int lane) {
         cudaSetDevice(dev);
+        Engine &engine = *lanes[lane].engine;
         std::vector<Entry *> active;
         for (;;) {
             std::vector<Entry *> admitted;
             {
                 std::unique_lock<std::mutex> lk(mu);
-                wake.wait(lk, [&]() { return stop || !active.empty() || admissible(); });
+                wake.wait(lk, [&]() { return stop || !active.empty() || admissible(lane) != queue.end(); });
                 if (stop) return;
-                while (admissible()) {
-                    Entry *e = queue.front();
-                    queue.pop_front();
+                for (auto it = admissible(lane); it != queue.end(); it = admissible(lane)) {
+                    Entry *e = *it;
+                    queue.erase(it);
                     e->state = E_RUNNING;
                     used += e->est;
                     running++;
@@ -87,7 +116,7 @@ struct cd_server {
             for (Entry *e : admitted) {
                 e->job = std::make_unique<Job>(e->spec);
                 try {
-                    engine->add(e->job.get());
+                    engine.add(e->job.get());
                 } catch (const Error &err) {
                     e->job->status = err.status;
                     e->job->msg = err.msg;
@@ -95,8 +124,10 @@ struct cd_server {
                 }
                 active.push_back(e);
             }
+            if (lane == 0) small_active.store((int)active.size());
+            engine.set_grid_share(share(lane));
             try {
-                engine->step();
+                engine.step();
             } catch (const Error &err) {
                 for (Entry *e : active)
                     if (!e->job->done) {
@@ -121,7 +152,11 @@ struct cd_server {
             }
             active.erase(std::remove_if(active.begin(), active.end(), [](Entry *e) { return e->state == E_DONE; }),
                          active.end());
-            if (any) done.notify_all();
+            if (lane == 0) small_active.store((int)active.size());
+            if (any) {
+                done.notify_all();
+                wake.notify_all();   // freed slots and memory may admit the other lane's runs
+            }
         }
     }
 };
@@ -143,17 +178,25 @@ cd_status cd_server_create(size_t device_mem_budget, int max_slots, int max_queu
         S->budget = device_mem_budget;
         S->max_slots = max_slots;
         S->max_queue = max_queue;
+        // the large lane runs on the caller's stream (or one of its own), the
+        // small lane on a stream of its own
         if (stream) {
-            S->stream = static_cast<cudaStream_t>(stream);
+            S->lanes[1].stream = static_cast<cudaStream_t>(stream);
         } else {
-            CD_CUDA(cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking));
-            S->own_stream = true;
+            CD_CUDA(cudaStreamCreateWithFlags(&S->lanes[1].stream, cudaStreamNonBlocking));
+            S->lanes[1].own_stream = true;
         }
+        CD_CUDA(cudaStreamCreateWithFlags(&S->lanes[0].stream, cudaStreamNonBlocking));
+        S->lanes[0].own_stream = true;
         CD_CUDA(cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking));
         const int hw = (int)std::thread::hardware_concurrency();
-        S->engine = std::make_unique<Engine>(S->stream, std::max(1, std::min(16, hw > 0 ? hw : 4)));
+        const int workers = std::max(1, std::min(16, hw > 0 ? hw : 4));
+        for (int l = 0; l < 2; l++) {
+            S->lanes[l].engine = std::make_unique<Engine>(S->lanes[l].stream, l == 0 ? std::max(1, workers / 2) : workers);
+            S->lanes[l].engine->set_grid_share(l == 0 ? SMALL_SHARE : 1.0 - SMALL_SHARE);
+        }
         cd_server *raw = S.get();
-        S->th = std::thread([raw]() { raw->loop(); });
+        for (int l = 0; l < 2; l++) S->lanes[l].th = std::thread([raw, l]() { raw->loop(l); });
         *out = S.release();
         return CD_OK;
     });
@@ -166,6 +209,7 @@ cd_status cd_server_submit(cd_server *S, cd_graph *g, const cd_task *task, const
         auto e = std::make_unique<Entry>();
         e->spec = task_spec(g->g.view, task, ro, nullptr);
         e->est = estimate_bytes(e->spec);
+        e->lane = g->g.view.nnz + g->g.view.n <= SMALL_WORK ? 0 : 1;
         CD_CUDA(cudaStreamSynchronize(g->stream));
         std::lock_guard<std::mutex> lk(S->mu);
         if (e->est > S->budget)
@@ -235,14 +279,18 @@ cd_status cd_server_destroy(cd_server *S) {
             S->stop = true;
         }
         S->wake.notify_all();
-        if (S->th.joinable()) S->th.join();
+        for (auto &L : S->lanes)
+            if (L.th.joinable()) L.th.join();
         S->done.notify_all();
         S->queue.clear();
-        S->entries.clear();   // frees every run while the engine's streams exist
-        CD_CUDA(cudaStreamSynchronize(S->stream));
-        S->engine.reset();
+        S->entries.clear();   // frees every run while the engines' streams exist
+        for (auto &L : S->lanes) {
+            CD_CUDA(cudaStreamSynchronize(L.stream));
+            L.engine.reset();
+        }
         cudaStreamDestroy(S->copy_stream);
-        if (S->own_stream) cudaStreamDestroy(S->stream);
+        for (auto &L : S->lanes)
+            if (L.own_stream) cudaStreamDestroy(L.stream);
         delete S;
         return CD_OK;
     });

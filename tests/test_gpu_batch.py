@@ -241,6 +241,35 @@ def test_server_admission_limits():
         S.close()
 
 
+def test_server_lanes_small_runs_pass_large_ones(O):
+    """Runs above 2^21 entries + vertices go to the large lane, the rest to
+    the small lane; both lanes give single-run results, and a small run
+    submitted right after a large one does not wait for the large one's
+    phases (it finishes first)."""
+    big_g = synth.rmat(20, seed=4)
+    small_g = [GRAPHS[i] for i in (0, 1, 3, 5, 9)]
+    big = cd.Graph.from_synth(big_g, device="cuda")
+    smalls = [cd.Graph.from_synth(g, device="cuda") for g in small_g]
+    assert big.m * 2 + big.n > 1 << 21 and all(G.m * 2 + G.n <= 1 << 21 for G in smalls)
+    ref_big = big.plm(seed=5)
+    S = cd.Server(max_slots=8)
+    try:
+        t_big = S.submit(big, cd.CD_ALGO_PLM, seed=5)
+        t_small = [S.submit(G, cd.CD_ALGO_PLM, seed=5) for G in smalls]
+        lat_small = []
+        for g, G, tk in zip(small_g, smalls, t_small):
+            out = torch.empty(max(G.n, 1), dtype=torch.int32, device="cuda")[:G.n]
+            status, mod, lat, st = S.poll(tk, out, timeout_ms=-1)
+            assert np.array_equal(out.cpu().numpy(), O.plm(*g.numpy(), seed=5).labels)
+            lat_small.append(lat)
+        out = torch.empty(big.n, dtype=torch.int32, device="cuda")
+        status, mod, lat_big, st = S.poll(t_big, out, timeout_ms=-1)
+        assert torch.equal(out, ref_big.labels) and mod == ref_big.modularity
+        assert max(lat_small) < lat_big, (lat_small, lat_big)
+    finally:
+        S.close()
+
+
 def test_server_destroy_with_pending_runs():
     Gs = [cd.Graph.from_synth(g, device="cuda") for g in GRAPHS[:5]]
     S = cd.Server(max_slots=2)
