@@ -3,7 +3,7 @@
 Only the oracle (``oracle/``, its OpenMP build, whose results equal the
 sequential build's: tests/test_oracle_openmp.py) and the seeded generators
 are called; no value comes from the CUDA library.  The GPU tests in
-tests/test_zzz_fullsize.py compare the library's results on the same graphs
+tests/test_zy_fullsize.py compare the library's results on the same graphs
 with these records, bit for bit.
 
 Each record holds what a GPU run must reproduce exactly:

@@ -22,7 +22,8 @@ as well.  R-MAT scale 26 (about 2.1 billion CSR entries), where a borrowed
 device CSR (CD_BORROW) spares the graph's second copy, is checked against the
 copying handle and the properties.
 
-This file is collected last: it holds the largest graphs of the suite.
+This file is collected late (only the allocation-free entry point's test comes
+after it): it holds the largest graphs of the suite.
 """
 import hashlib
 import json
