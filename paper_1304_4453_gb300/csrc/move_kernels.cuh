@@ -725,25 +725,67 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
     }
     const int64_t beg = hi.beg, end = hi.end;
     for (int s = threadIdx.x; s < HUB_CHUNK_SLOTS; s += kBlock) { keys[s] = -1; vals[s] = 0; }
-    __syncthreads();
-    for (int64_t e = beg + threadIdx.x; e < end; e += kBlock)
-        tab_insert<VT>(keys, vals, HUB_CHUNK_SLOTS - 1, c.zeta[c.g.col[e]], (VT)edge_weight<WK>(c.g.w, e),
-                       &c.cnt->overflow);
+    {
+        // every neighbour id of the thread, then every label, before the inserts
+        constexpr int EPT = (HUB_CHUNK + kBlock - 1) / kBlock;
+        int32_t nb[EPT];
+#pragma unroll
+        for (int j = 0; j < EPT; j++) {
+            const int64_t e = beg + threadIdx.x + j * kBlock;
+            nb[j] = e < end ? c.g.col[e] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < EPT; j++) nb[j] = nb[j] >= 0 ? c.zeta[nb[j]] : -1;
+        __syncthreads();   // the table is cleared
+#pragma unroll
+        for (int j = 0; j < EPT; j++)
+            if (nb[j] >= 0)
+                tab_insert<VT>(keys, vals, HUB_CHUNK_SLOTS - 1, nb[j],
+                               (VT)edge_weight<WK>(c.g.w, beg + threadIdx.x + j * kBlock), &c.cnt->overflow);
+    }
     __syncthreads();
     int32_t *gk = c.hub_keys + hi.tab;
     VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
     const uint32_t gmask = (uint32_t)(hi.slots - 1);
     {
-        // merge into the hub table; slots created here go to the occupied list
-        int32_t fresh[PER];
-        int nf = 0;
+        // merge into the hub table; slots created here go to the occupied
+        // list.  All keys of the thread probe at once: in each round every
+        // pending key tries its current slot with one compare-and-swap (which
+        // also reports a slot that already holds the key), so a round costs
+        // one round trip to L2 however many keys the thread holds.
+        int32_t fresh[PER], ky[PER];
+        VT vl[PER];
+        uint32_t at[PER];
+        unsigned pend = 0;
 #pragma unroll
         for (int i = 0; i < PER; i++) {
             const int s = threadIdx.x + i * kBlock;
+            ky[i] = keys[s];
+            vl[i] = vals[s];
             fresh[i] = -1;
-            if (keys[s] >= 0) fresh[i] = tab_insert_new<VT>(gk, gv, gmask, keys[s], vals[s], &c.cnt->overflow);
-            nf += fresh[i] >= 0;
+            at[i] = hmix(ky[i]) & gmask;
+            if (ky[i] >= 0) pend |= 1u << i;
         }
+        for (uint32_t probe = 0; pend && probe <= gmask; probe++) {
+            int32_t prev[PER];
+#pragma unroll
+            for (int i = 0; i < PER; i++) prev[i] = (pend >> i) & 1u ? atomicCAS(&gk[at[i]], -1, ky[i]) : 0;
+#pragma unroll
+            for (int i = 0; i < PER; i++) {
+                if (!((pend >> i) & 1u)) continue;
+                if (prev[i] == -1 || prev[i] == ky[i]) {
+                    atomicAdd(&gv[at[i]], vl[i]);
+                    if (prev[i] == -1) fresh[i] = (int32_t)at[i];
+                    pend &= ~(1u << i);
+                } else {
+                    at[i] = (at[i] + 1) & gmask;
+                }
+            }
+        }
+        if (pend) atomicAdd(&c.cnt->overflow, (unsigned long long)__popc(pend));
+        int nf = 0;
+#pragma unroll
+        for (int i = 0; i < PER; i++) nf += fresh[i] >= 0;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         int incl = nf;
 #pragma unroll

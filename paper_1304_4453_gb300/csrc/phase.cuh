@@ -391,6 +391,101 @@ __device__ __forceinline__ void rc_radix_pass(const uint64_t *in, uint64_t *out,
     }
 }
 
+// One re-check candidate as warp 0 walks it: its record, and the volumes of
+// its two communities and its hub block flag as of the start of its window.
+struct RcLane {
+    int32_t C, D, u;
+    int64_t vu, dw;
+    bool hub;
+};
+
+__device__ __forceinline__ RcLane rc_load(const RecheckArgs &a, int64_t i, int64_t m) {
+    RcLane r{-1, -2, 0, 0, 0, false};
+    if (i < m) {
+        const uint64_t cd = __ldcg(a.rc_cd + i), vh = __ldcg(a.rc_vu + i);
+        r.C = (int32_t)(uint32_t)cd;
+        r.D = (int32_t)(cd >> 32);
+        r.vu = (int64_t)(vh & ~(1ull << 63));
+        r.hub = (vh >> 63) != 0;
+        r.dw = __ldcg(a.rc_dw + i);
+        r.u = __ldcg(a.rc_u + i);
+    }
+    return r;
+}
+
+// Walk of the sorted candidates by warp 0 (deterministic schedule), in
+// windows of 32 as described above, with the volume and stamp reads taken
+// off the sequential path: the reads for window w + 1 are issued when window
+// w starts (they see every move of the windows before w, which are committed
+// by then), and each move that window w accepts is folded into them as a
+// volume difference (and, for hubs, as the stamp it would have written), so
+// that window w + 1 starts from exactly the state the sequential order gives
+// it.  Records are read two windows ahead.
+template <bool BIG>
+__device__ __forceinline__ void recheck_walk_pipelined(const RecheckArgs &a, int64_t m) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long moved = 0;
+    RcLane cur = rc_load(a, lane, m), nxt = rc_load(a, 32 + lane, m);
+    int64_t volC = cur.C >= 0 ? __ldcg(a.volc + cur.C) : 0, volD = cur.C >= 0 ? __ldcg(a.volc + cur.D) : 0;
+    bool blocked = cur.hub && (__ldcg(a.cstamp + cur.C) == a.step || __ldcg(a.cstamp + cur.D) == a.step);
+    for (int64_t w0 = 0; w0 < m; w0 += 32) {
+        const bool valid = w0 + lane < m;
+        // next window: its volumes and stamps as of now, then the records after it
+        const bool nvalid = nxt.C >= 0;
+        const int64_t nvC = nvalid ? __ldcg(a.volc + nxt.C) : 0, nvD = nvalid ? __ldcg(a.volc + nxt.D) : 0;
+        const bool nstamped =
+            nxt.hub && (__ldcg(a.cstamp + nxt.C) == a.step || __ldcg(a.cstamp + nxt.D) == a.step);
+        const RcLane nn = rc_load(a, w0 + 64 + lane, m);
+        int64_t dC = 0, dD = 0;
+        bool nblk = false;
+        bool mine = false;
+        unsigned pending = __ballot_sync(0xffffffffu, valid);
+        while (pending) {
+            const bool acc = ((pending >> lane) & 1u) && !blocked &&
+                             plm_gain<BIG>(a.twoW, a.res_q, a.res_p, cur.dw, 0, cur.vu, volD, volC) > 0;
+            const unsigned am = __ballot_sync(0xffffffffu, acc);
+            if (am == 0) break;
+            const int k = __ffs(am) - 1;
+            pending &= ~(0xffffffffu >> (31 - k));   // lanes 0..k are decided
+            const int32_t Ck = __shfl_sync(0xffffffffu, cur.C, k), Dk = __shfl_sync(0xffffffffu, cur.D, k);
+            const int64_t vk = __shfl_sync(0xffffffffu, cur.vu, k);
+            const bool hk = __shfl_sync(0xffffffffu, (int)cur.hub, k) != 0;
+            if (lane == k) {
+                mine = true;
+                if (cur.hub) {
+                    a.cstamp[cur.C] = a.step;
+                    a.cstamp[cur.D] = a.step;
+                }
+            } else if (lane > k) {
+                if (cur.C == Ck) volC -= vk; else if (cur.C == Dk) volC += vk;
+                if (cur.D == Ck) volD -= vk; else if (cur.D == Dk) volD += vk;
+                if (hk && cur.hub && (cur.C == Ck || cur.C == Dk || cur.D == Ck || cur.D == Dk)) blocked = true;
+            }
+            // every candidate of the next window comes after this move
+            if (nxt.C == Ck) dC -= vk; else if (nxt.C == Dk) dC += vk;
+            if (nxt.D == Ck) dD -= vk; else if (nxt.D == Dk) dD += vk;
+            if (hk && nxt.hub && (nxt.C == Ck || nxt.C == Dk || nxt.D == Ck || nxt.D == Dk)) nblk = true;
+        }
+        // the next window's volume reads are ordered before this window's
+        // commits (a stamp written above may or may not be seen by them:
+        // nblk holds it either way)
+        __syncwarp();
+        if (valid && mine) {
+            a.zeta[cur.u] = cur.D;
+            vol_add(a.volc, cur.C, -cur.vu);
+            vol_add(a.volc, cur.D, cur.vu);
+        }
+        moved += __popc(__ballot_sync(0xffffffffu, valid && mine));
+        __syncwarp();
+        cur = nxt;
+        volC = nvC + dC;
+        volD = nvD + dD;
+        blocked = nstamped || nblk;
+        nxt = nn;
+    }
+    if (lane == 0 && moved) atomicAdd(&a.cnt->moved, moved);
+}
+
 template <bool BIG>
 __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *smem) {
     const int64_t m = (int64_t)__ldcg(a.ncand);
@@ -484,7 +579,9 @@ __device__ __noinline__ void recheck_block(const RecheckArgs &a, unsigned char *
         a.rc_dw[i] = __ldcg(a.cwd + ci) - __ldcg(a.cwc + ci);
     }
     __syncthreads();
-    if (tid < 32) {
+    if (tid < 32 && !a.nbr_stamp) {
+        recheck_walk_pipelined<BIG>(a, m);
+    } else if (tid < 32) {
         unsigned long long moved = 0;
         // records are read one window ahead; they never change, only the
         // volumes and stamps do, and those are read after the previous
