@@ -397,14 +397,18 @@ cd_status cd_debug_plan_launch(const int64_t *work, int count, int64_t team_quan
 
 /* Diagnostic: the class trace of the move phases (Algorithm 2 under the
  * colour-class schedule) run with opts.profile = 2 since the last call.  One
- * row of twelve int64 per class step, in completion order: phase number,
+ * row of nineteen int64 per class step, in completion order: phase number,
  * sweep, colour class, its vertices, its adjacency entries, its hub
  * aggregation chunks, its hub decide slices, its hubs above 4096 neighbours,
  * the wall time in ns on the team's first block from the previous class's
- * barrier to this class's barrier, and the latest times (ns after that
- * start, 0 when absent) at which a block finished its work items, its hub
- * decide slices, and the class finisher its work.  With out == NULL only
- * *count (rows) is set; then out[12 * count] receives the rows (cap = rows
+ * barrier to this class's barrier, the latest times (ns after that start, 0
+ * when absent) at which a block finished its work items, its hub decide
+ * slices, and the class finisher its work, and at which a block began its
+ * first item; the longest single lane-group item, block item and hub-chunk
+ * item, the longest wait of a decide slice for its hub's table and the
+ * longest decide slice after it (ns); the class's applied moves (early
+ * sweeps) or re-check candidates (late sweeps).  With out == NULL only
+ * *count (rows) is set; then out[19 * count] receives the rows (cap = rows
  * the buffer holds) and the trace is cleared.  Errors: CD_EINVAL. */
 cd_status cd_debug_class_trace(int64_t *out, int64_t cap, int64_t *count);
 

@@ -318,7 +318,8 @@ def cd_debug_fail_alloc(k: int):
 
 
 TRACE_FIELDS = ("phase", "sweep", "cls", "vertices", "entries", "hub_chunks", "hub_slices", "big_hubs", "ns",
-                "items_end_ns", "decide_end_ns", "finisher_end_ns")
+                "items_end_ns", "decide_end_ns", "finisher_end_ns", "first_item_ns", "max_group_ns", "max_block_ns",
+                "max_chunk_ns", "max_slice_wait_ns", "max_slice_ns", "moves_or_candidates")
 
 
 def cd_debug_class_trace() -> np.ndarray:

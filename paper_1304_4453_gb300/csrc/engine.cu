@@ -437,7 +437,7 @@ static void prepare_trace(PhaseRun &r, const GraphView &g, const Schedule &S, cu
     r.cls_ns.alloc((size_t)r.cap * ncol + 1, s);
     r.cls_ns.zero();
     r.a.class_ns = r.cls_ns.p;
-    r.cls_stage.alloc((size_t)r.cap * ncol * 3 + 1, s);
+    r.cls_stage.alloc((size_t)r.cap * ncol * STAGE_SLOTS + 1, s);
     r.cls_stage.zero();
     r.a.stage_max = r.cls_stage.p;
     const int64_t listed = S.off[(size_t)ncol * NBINS];
@@ -462,7 +462,7 @@ static void prepare_trace(PhaseRun &r, const GraphView &g, const Schedule &S, cu
 
 static void record_trace(PhaseRun &r, int32_t runs, cudaStream_t s) {
     const int64_t ncol = r.a.ncol;
-    std::vector<unsigned long long> t((size_t)runs * ncol + 1), sm((size_t)runs * ncol * 3 + 1);
+    std::vector<unsigned long long> t((size_t)runs * ncol + 1), sm((size_t)runs * ncol * STAGE_SLOTS + 1);
     CD_CUDA(cudaMemcpyAsync(t.data(), r.cls_ns.p, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CD_CUDA(cudaMemcpyAsync(sm.data(), r.cls_stage.p, sm.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                             s));
@@ -475,11 +475,14 @@ static void record_trace(PhaseRun &r, int32_t runs, cudaStream_t s) {
             const unsigned long long x = t[1 + sw * ncol + k];
             if (x == 0) continue;
             const int64_t *ci = &r.cls_info[(size_t)k * 5];
-            const unsigned long long *q = &sm[(size_t)(sw * ncol + k) * 3];
+            const unsigned long long *q = &sm[(size_t)(sw * ncol + k) * STAGE_SLOTS];
             // stage ends relative to the class start (0: the stage did not run)
             auto rel = [&](unsigned long long y) { return y > prev ? (int64_t)(y - prev) : (int64_t)0; };
             const int64_t row[TRACE_FIELDS] = {ph, sw, k, ci[0], ci[1], ci[2], ci[3], ci[4], (int64_t)(x - prev),
-                                               rel(q[0]), rel(q[1]), rel(q[2])};
+                                               rel(q[ST_ITEMS_END]), rel(q[ST_DECIDE_END]), rel(q[ST_FINISH_END]),
+                                               rel(q[ST_FIRST_ITEM]), (int64_t)q[ST_GROUP], (int64_t)q[ST_BLOCK],
+                                               (int64_t)q[ST_CHUNK], (int64_t)q[ST_SLICE_WAIT], (int64_t)q[ST_SLICE],
+                                               (int64_t)q[ST_MOVES]};
             g_trace.insert(g_trace.end(), row, row + TRACE_FIELDS);
             prev = x;
         }

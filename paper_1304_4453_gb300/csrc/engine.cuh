@@ -142,8 +142,11 @@ void run_epp_general(const GraphView &g, int b, int base, bool final_refine, int
 // TRACE_FIELDS int64 per class step, appended in completion order.
 // phase, sweep, class, vertices, entries, hub chunks, hub slices, hubs >
 // HUB_RELAX, ns, then the latest end of the items, the hub-decide slices and
-// the finisher's work, in ns from the class start (0: stage absent)
-constexpr int TRACE_FIELDS = 12;
+// the finisher's work and the latest start of a block's first item, in ns
+// from the class start (0: stage absent), the longest lane-group, block and
+// hub-chunk item, decide-slice wait and decide slice (ns), and the class's
+// applied moves (early sweeps) or re-check candidates (late sweeps)
+constexpr int TRACE_FIELDS = 19;
 std::vector<int64_t> take_class_trace();
 
 }  // namespace cd

@@ -41,6 +41,7 @@
 #pragma once
 #include <type_traits>
 
+#include "barrier.cuh"
 #include "common.cuh"
 
 namespace cd {
@@ -109,6 +110,14 @@ struct SliceDesc {             // one decide slice of a hub's occupied-slot list
     int32_t nb1, nb2;
     int32_t p0, relax;         // first slice of the hub inside the class; more than HUB_RELAX neighbours
 };
+
+// Class-trace words per class step (profile level 2): ends of the stages
+// (global ns), the latest start of a block's first item, the longest lane-
+// group, block and hub-chunk item and decide slice (ns, the slice's wait for
+// its hub's table apart), and the class's applied moves (early sweeps) or
+// re-check candidates (late sweeps).
+enum { ST_ITEMS_END = 0, ST_DECIDE_END, ST_FINISH_END, ST_FIRST_ITEM, ST_GROUP, ST_BLOCK, ST_CHUNK, ST_SLICE_WAIT,
+       ST_SLICE, ST_MOVES, STAGE_SLOTS };
 
 struct SweepCtx {
     GraphView g;
@@ -225,6 +234,40 @@ __device__ __forceinline__ VT tab_lookup_cg(const int32_t *keys, const VT *vals,
     }
     return 0;
 }
+
+// Global hub tables (open addressing, linear probing, slots a power of two):
+// int32 keys (-1: empty) and values of type VT (32 bits on the 64-bit gain
+// path, where omega(u, c) <= vol(u) <= 2W < 2^32; 64 bits on the 128-bit
+// path) in two arrays at the same slot offsets.
+template <typename VT>
+struct HubTable {
+    int32_t *k;
+    VT *v;
+    __device__ __forceinline__ HubTable(int32_t *keys, void *vals, int64_t tab)
+        : k(keys + tab), v(static_cast<VT *>(vals) + tab) {}
+    __device__ __forceinline__ void read(int64_t s, int32_t &key, int64_t &w) const {
+        key = __ldcg(k + s);
+        w = (int64_t)__ldcg(v + s);
+    }
+    __device__ __forceinline__ void clear(int64_t s) const {
+        k[s] = -1;
+        v[s] = 0;
+    }
+    // Insertion in two steps, so that a thread can have the compare-and-swaps
+    // of all its keys in flight before it looks at any result: claim() tries
+    // slot s and returns the key it held; settle() returns 1 (the key was new
+    // here) or 0 (the key was here), adding w in both cases, or -1 (another
+    // key: probe on).
+    __device__ __forceinline__ int32_t claim(int64_t s, int32_t key) const { return atomicCAS(k + s, -1, key); }
+    __device__ __forceinline__ int settle(int64_t s, int32_t key, VT w, int32_t prev) const {
+        if (prev != -1 && prev != key) return -1;
+        atomicAdd(v + s, w);
+        return prev == -1 ? 1 : 0;
+    }
+    __device__ __forceinline__ int64_t lookup(uint32_t mask, int32_t key) const {
+        return (int64_t)tab_lookup_cg<VT>(k, v, mask, key);
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Candidate ordering
@@ -661,40 +704,53 @@ __device__ __forceinline__ void hub_finish(const SweepCtx &c, int32_t u, int32_t
 template <int WK, bool BIG, bool PLP>
 __device__ __forceinline__ void hub_decide_occ(const SweepCtx &c, const ChunkDesc &hi,
                                                typename BestOf<PLP, BIG>::T *s_best, int *s_last) {
-    using VT = ValT<BIG>;
     using BT = typename BestOf<PLP, BIG>::T;
     __threadfence();
-    int32_t *gk = c.hub_keys + hi.tab;
-    VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
+    const HubTable<ValT<BIG>> tb(c.hub_keys, c.hub_vals, hi.tab);
     const int32_t *occ = c.hub_occ + hi.tab;
     const uint32_t gmask = (uint32_t)(hi.slots - 1);
     const int32_t u = hi.u;
     const int h = hi.h;
     const int32_t C = c.zeta[u];
     const int64_t nocc = (int64_t)__ldcg(c.hub_nocc + h);
-    const int64_t wC = (int64_t)tab_lookup_cg<VT>(gk, gv, gmask, C);
+    const int64_t wC = tb.lookup(gmask, C);
+    __syncthreads();   // every thread's lookup of C is done before slots are cleared below
     BT b;
     b.init();
+    // four list entries per thread and step (two steps for nocc <= HUB_LAST):
+    // slot numbers, then the slots, then candidate volumes, then the offers
+    constexpr int OPT = 4;
+    int64_t vu = 0, volC = 0;
     if constexpr (!PLP) {
-        const int64_t vu = c.g.vol[u], volC = c.volc[C], twoW = 2 * c.g.W;
-        for (int64_t i = threadIdx.x; i < nocc; i += kBlock) {
-            const int32_t sl = __ldcg(occ + i);
-            const int32_t key = __ldcg(gk + sl);
-            const int64_t val = (int64_t)__ldcg(gv + sl);
-            if (key != C) b.offer(plm_gain<BIG>(twoW, c.res_q, c.res_p, val, wC, vu, c.volc[key], volC), key, val);
-        }
-    } else {
-        for (int64_t i = threadIdx.x; i < nocc; i += kBlock) {
-            const int32_t sl = __ldcg(occ + i);
-            const int32_t key = __ldcg(gk + sl);
-            b.offer((int64_t)__ldcg(gv + sl), fmix32((uint32_t)key ^ c.tie_salt), key);
-        }
+        vu = c.g.vol[u];
+        volC = c.volc[C];
     }
-    __syncthreads();   // every lookup of C is done before slots are cleared
-    for (int64_t i = threadIdx.x; i < nocc; i += kBlock) {
-        const int32_t sl = __ldcg(occ + i);
-        gk[sl] = -1;
-        gv[sl] = 0;
+    for (int64_t i0 = threadIdx.x; i0 < nocc; i0 += OPT * kBlock) {
+        int32_t sl[OPT], ky[OPT];
+        int64_t wv[OPT], vk[OPT];
+#pragma unroll
+        for (int j = 0; j < OPT; j++) sl[j] = i0 + j * kBlock < nocc ? __ldcg(occ + i0 + j * kBlock) : -1;
+#pragma unroll
+        for (int j = 0; j < OPT; j++) {
+            ky[j] = -1;
+            wv[j] = 0;
+            if (sl[j] >= 0) tb.read(sl[j], ky[j], wv[j]);
+        }
+        if constexpr (!PLP) {
+#pragma unroll
+            for (int j = 0; j < OPT; j++) vk[j] = (sl[j] >= 0 && ky[j] != C) ? c.volc[ky[j]] : 0;
+#pragma unroll
+            for (int j = 0; j < OPT; j++)
+                if (sl[j] >= 0 && ky[j] != C)
+                    b.offer(plm_gain<BIG>(2 * c.g.W, c.res_q, c.res_p, wv[j], wC, vu, vk[j], volC), ky[j], wv[j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < OPT; j++)
+                if (sl[j] >= 0) b.offer(wv[j], fmix32((uint32_t)ky[j] ^ c.tie_salt), ky[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < OPT; j++)
+            if (sl[j] >= 0) tb.clear(sl[j]);   // each listed slot is read and cleared by one thread
     }
     b = block_best(b, s_best);
     if (threadIdx.x == 0) {
@@ -744,8 +800,7 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
                                (VT)edge_weight<WK>(c.g.w, beg + threadIdx.x + j * kBlock), &c.cnt->overflow);
     }
     __syncthreads();
-    int32_t *gk = c.hub_keys + hi.tab;
-    VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
+    const HubTable<ValT<BIG>> tb(c.hub_keys, c.hub_vals, hi.tab);
     const uint32_t gmask = (uint32_t)(hi.slots - 1);
     {
         // merge into the hub table; slots created here go to the occupied
@@ -769,13 +824,13 @@ __device__ __forceinline__ void role_hub_aggregate(const SweepCtx &c, int32_t rb
         for (uint32_t probe = 0; pend && probe <= gmask; probe++) {
             int32_t prev[PER];
 #pragma unroll
-            for (int i = 0; i < PER; i++) prev[i] = (pend >> i) & 1u ? atomicCAS(&gk[at[i]], -1, ky[i]) : 0;
+            for (int i = 0; i < PER; i++) prev[i] = (pend >> i) & 1u ? tb.claim(at[i], ky[i]) : 0;
 #pragma unroll
             for (int i = 0; i < PER; i++) {
                 if (!((pend >> i) & 1u)) continue;
-                if (prev[i] == -1 || prev[i] == ky[i]) {
-                    atomicAdd(&gv[at[i]], vl[i]);
-                    if (prev[i] == -1) fresh[i] = (int32_t)at[i];
+                const int r = tb.settle(at[i], ky[i], vl[i], prev[i]);
+                if (r >= 0) {
+                    if (r == 1) fresh[i] = (int32_t)at[i];
                     pend &= ~(1u << i);
                 } else {
                     at[i] = (at[i] + 1) & gmask;

@@ -84,8 +84,9 @@ struct PhaseArgs {
     // phase starts ([0]) and after the barrier of class k in sweep sw
     // ([1 + sw * ncol + k]); skipped (empty) classes keep 0
     unsigned long long *class_ns;
-    // with class_ns: per class step, the latest time any block finished its
-    // items, its hub-decide slices, and the finisher's work ([3 * step + i])
+    // with class_ns: STAGE_SLOTS words per class step (ST_* below): the latest
+    // time any block finished its items, its hub-decide slices and the
+    // finisher's work, and the longest single item of each kind
     unsigned long long *stage_max;
 };
 
@@ -159,8 +160,7 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
     if constexpr (PLP) {
         if (!hi.relax && !c.racy && !c.active[u]) return;
     }
-    int32_t *gk = c.hub_keys + hi.tab;
-    VT *gv = static_cast<VT *>(c.hub_vals) + hi.tab;
+    const HubTable<VT> tb(c.hub_keys, c.hub_vals, hi.tab);
     const int32_t *occ = c.hub_occ + hi.tab;
     const int64_t nocc = (int64_t)__ldcg(c.hub_nocc + h);
     const int64_t s0 = hi.s0, s1 = min(hi.s1, nocc);
@@ -171,21 +171,25 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
     unsigned ncand = 0;
     BT b;
     b.init();
-    if constexpr (!PLP) {
-        using T = typename GainT<BIG>::T;
-        const int64_t vu = c.g.vol[u], twoW = 2 * c.g.W;
-        // four occupied slots per thread and step: slot numbers, then keys and
-        // weights, then candidate volumes, then gains
-        for (int64_t i0 = s0 + threadIdx.x; i0 < s1; i0 += 4 * kBlock) {
-            int32_t sl[4], ky[4];
-            int64_t wv[4], vk[4];
+    int64_t vu = 0;
+    if constexpr (!PLP) vu = c.g.vol[u];
+    const int64_t twoW = 2 * c.g.W;
+    // four occupied slots per thread and step: slot numbers, then the slots,
+    // then candidate volumes, then gains (every slot of the list is read and
+    // emptied by one thread of one slice)
+    for (int64_t i0 = s0 + threadIdx.x; i0 < s1; i0 += 4 * kBlock) {
+        int32_t sl[4], ky[4];
+        int64_t wv[4], vk[4];
 #pragma unroll
-            for (int j = 0; j < 4; j++) sl[j] = i0 + j * kBlock < s1 ? __ldcg(occ + i0 + j * kBlock) : -1;
+        for (int j = 0; j < 4; j++) sl[j] = i0 + j * kBlock < s1 ? __ldcg(occ + i0 + j * kBlock) : -1;
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                ky[j] = sl[j] >= 0 ? __ldcg(gk + sl[j]) : -1;
-                wv[j] = sl[j] >= 0 ? (int64_t)__ldcg(gv + sl[j]) : 0;
-            }
+        for (int j = 0; j < 4; j++) {
+            ky[j] = -1;
+            wv[j] = 0;
+            if (sl[j] >= 0) tb.read(sl[j], ky[j], wv[j]);
+        }
+        if constexpr (!PLP) {
+            using T = typename GainT<BIG>::T;
 #pragma unroll
             for (int j = 0; j < 4; j++) vk[j] = (sl[j] >= 0 && ky[j] != C) ? c.volc[ky[j]] : 0;
 #pragma unroll
@@ -194,20 +198,17 @@ __device__ __forceinline__ void role_hub_decide(const SweepCtx &c, int32_t item,
                 ncand++;
                 if (ky[j] != C) b.offer((T)twoW * (T)c.res_q * (T)wv[j] - (T)c.res_p * (T)vu * (T)vk[j], ky[j], wv[j]);
                 else { *hwc = (VT)wv[j]; __threadfence(); }
-                gk[sl[j]] = -1;
-                gv[sl[j]] = 0;
+                tb.clear(sl[j]);
             }
-        }
-    } else {
-        for (int64_t i = s0 + threadIdx.x; i < s1; i += kBlock) {
-            const int32_t s = __ldcg(occ + i);
-            const int32_t key = __ldcg(gk + s);
-            ncand++;
-            const int64_t w = (int64_t)__ldcg(gv + s);
-            b.offer(w, fmix32((uint32_t)key ^ c.tie_salt), key);
-            if (key == C) { *hwc = (VT)w; __threadfence(); }
-            gk[s] = -1;
-            gv[s] = 0;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (sl[j] < 0) continue;
+                ncand++;
+                b.offer(wv[j], fmix32((uint32_t)ky[j] ^ c.tie_salt), ky[j]);
+                if (ky[j] == C) { *hwc = (VT)wv[j]; __threadfence(); }
+                tb.clear(sl[j]);
+            }
         }
     }
     ncand = __reduce_add_sync(0xffffffffu, ncand);
@@ -708,10 +709,16 @@ __device__ __forceinline__ void apply_deferred_labels(const SweepCtx &c) {
 // hub chunk that it holds itself).
 template <int WK, bool BIG, bool PLP, typename BT>
 __device__ __forceinline__ bool decide_pool(const Team &tm, const SweepCtx &c, int32_t nb2,
-                                            const BlockShared<BT> &sh) {
+                                            const BlockShared<BT> &sh, unsigned long long *smx = nullptr) {
     for (int32_t g = tm.rank; g < nb2; g += tm.size) {
+        const uint64_t ti = smx && threadIdx.x == 0 ? global_ns() : 0;
         if (!wait_hub_ready<PLP>(c, g, tm.bar, sh.ok)) return false;
+        const uint64_t tw = smx && threadIdx.x == 0 ? global_ns() : 0;
         role_hub_decide<WK, BIG, PLP>(c, g, sh.best, sh.cand, sh.last);
+        if (smx && threadIdx.x == 0) {
+            atomicMax(smx + ST_SLICE_WAIT, tw - ti);
+            atomicMax(smx + ST_SLICE, global_ns() - tw);
+        }
     }
     return true;
 }
@@ -801,16 +808,23 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
             // out of the shared tables of the next.  Items are taken from the
             // end: hub chunks first, so that the hubs' decide slices find
             // their tables complete, then blocks, then the lane groups.
-            for (int32_t b = tm.rank; b < c.bend[5]; b += tm.size) {
-                run_item<WK, BIG, false>(c, c.bend[5] - 1 - b, sh.smem, sh.best, sh.cand, sh.last);
-                __syncthreads();
-            }
             const int64_t step = (int64_t)sw * a.ncol + k;
-            if (a.stage_max && threadIdx.x == 0) atomicMax(a.stage_max + 3 * step, global_ns());
-            if (nb2 > 0) {
-                if (!decide_pool<WK, BIG, false>(tm, c, nb2, sh)) return false;
+            unsigned long long *smx = a.stage_max ? a.stage_max + STAGE_SLOTS * step : nullptr;
+            for (int32_t b = tm.rank; b < c.bend[5]; b += tm.size) {
+                const int32_t item = c.bend[5] - 1 - b;
+                const uint64_t ti = smx && threadIdx.x == 0 ? global_ns() : 0;
+                if (smx && threadIdx.x == 0 && b == tm.rank) atomicMax(smx + ST_FIRST_ITEM, ti);
+                run_item<WK, BIG, false>(c, item, sh.smem, sh.best, sh.cand, sh.last);
+                __syncthreads();
+                if (smx && threadIdx.x == 0)
+                    atomicMax(smx + (item < c.bend[2] ? ST_GROUP : item < c.bend[4] ? ST_BLOCK : ST_CHUNK),
+                              global_ns() - ti);
             }
-            if (a.stage_max && threadIdx.x == 0) atomicMax(a.stage_max + 3 * step + 1, global_ns());
+            if (smx && threadIdx.x == 0) atomicMax(smx + ST_ITEMS_END, global_ns());
+            if (nb2 > 0) {
+                if (!decide_pool<WK, BIG, false>(tm, c, nb2, sh, smx)) return false;
+            }
+            if (smx && threadIdx.x == 0) atomicMax(smx + ST_DECIDE_END, global_ns());
             if (late || c.nrelax > 0) {
                 // the block that finishes the class last re-checks its wanted
                 // moves (late sweeps) or writes the hubs' deferred labels
@@ -827,7 +841,7 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
                         recheck_block<BIG>(ra, sh.smem);
                         if (a.stage_ns && threadIdx.x == 0) atomicAdd(a.stage_ns + 2, global_ns() - r0);
                     }
-                    if (a.stage_max && threadIdx.x == 0) atomicMax(a.stage_max + 3 * step + 2, global_ns());
+                    if (smx && threadIdx.x == 0) atomicMax(smx + ST_FINISH_END, global_ns());
                 }
             }
             if (!late && !a.racy) {
@@ -837,7 +851,10 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
             }
             if (!team_sync(tm, sh.gen, sh.ok)) return false;
             if (timed) a.stage_ns[0] += global_ns() - t0;
-            if (tracer) a.class_ns[1 + (int64_t)sw * a.ncol + k] = global_ns();
+            if (tracer) {
+                a.class_ns[1 + (int64_t)sw * a.ncol + k] = global_ns();
+                smx[ST_MOVES] = late ? __ldcg(a.ncand + k) : __ldcg(a.nmv + par * a.ncol + k);
+            }
         }
         // the sweep's counters are complete once every block has added its sums
         flush_counters(sh.bcnt, a.cnt + sw);
