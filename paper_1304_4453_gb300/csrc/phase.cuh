@@ -2,8 +2,9 @@
 // (every sweep, every colour class) or whole PLP runs (every iteration) of
 // one or many graphs.  A team of blocks works on one graph at a time: colour
 // classes follow each other in order, one team barrier after each; inside a
-// class, the team's blocks take the work items in a strided loop (hub
-// chunks, block items, lane groups), then the hub-decide slices.  The block
+// class, the team's blocks take the work items in serpentine passes (hub
+// chunks, block items and lane groups first from the expensive end, then
+// alternating), then the hub-decide slices.  The block
 // that finishes the class last (a finish counter) writes the hubs' deferred
 // labels in early PLM sweeps and runs the sequential re-check in late ones,
 // before the class's barrier.
@@ -723,6 +724,18 @@ __device__ __forceinline__ bool decide_pool(const Team &tm, const SweepCtx &c, i
     return true;
 }
 
+// Item of pass p for team block `rank` (-1: none).  The items of a class are
+// ordered roughly by cost (lane groups, block items, hub chunks: the most
+// expensive at the end), and the team walks them in a serpentine: pass 0
+// hands the last `size` items out from the end, pass 1 the next `size` from
+// their low end, and so on, so that a block that drew an expensive item in
+// one pass draws a cheap one in the next.
+__device__ __forceinline__ int32_t serpentine_item(int32_t p, int32_t rank, int32_t size, int32_t nit) {
+    const int64_t hi = (int64_t)nit - (int64_t)p * size, lo = hi - size;
+    const int64_t i = (p & 1) == 0 ? hi - 1 - rank : lo + rank;
+    return i >= 0 && i < hi ? (int32_t)i : -1;
+}
+
 // ---------------------------------------------------------------------------
 // PLM move phase (Algorithm 2) of one graph, run by one team: sweeps until
 // no vertex wants to move.  Returns false when a barrier failed.
@@ -805,15 +818,17 @@ __device__ bool move_phase_body(const PhaseArgs &a, const Team &tm, const BlockS
             const bool timed = a.stage_ns && tm.rank == 0 && threadIdx.x == 0;
             const uint64_t t0 = timed ? global_ns() : 0;
             // a block walks several items; the barrier keeps one item's warps
-            // out of the shared tables of the next.  Items are taken from the
-            // end: hub chunks first, so that the hubs' decide slices find
-            // their tables complete, then blocks, then the lane groups.
+            // out of the shared tables of the next.  The first pass hands out
+            // items from the end: hub chunks first, so that the hubs' decide
+            // slices find their tables complete, then blocks, then the lane
+            // groups; later passes alternate direction (serpentine_item).
             const int64_t step = (int64_t)sw * a.ncol + k;
             unsigned long long *smx = a.stage_max ? a.stage_max + STAGE_SLOTS * step : nullptr;
-            for (int32_t b = tm.rank; b < c.bend[5]; b += tm.size) {
-                const int32_t item = c.bend[5] - 1 - b;
+            for (int32_t p = 0; (int64_t)p * tm.size < c.bend[5]; p++) {
+                const int32_t item = serpentine_item(p, tm.rank, tm.size, c.bend[5]);
+                if (item < 0) continue;
                 const uint64_t ti = smx && threadIdx.x == 0 ? global_ns() : 0;
-                if (smx && threadIdx.x == 0 && b == tm.rank) atomicMax(smx + ST_FIRST_ITEM, ti);
+                if (smx && threadIdx.x == 0 && p == 0) atomicMax(smx + ST_FIRST_ITEM, ti);
                 run_item<WK, BIG, false>(c, item, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
                 if (smx && threadIdx.x == 0)
@@ -904,8 +919,10 @@ __device__ bool plp_body(const PhaseArgs &a, const Team &tm, const BlockShared<P
             }
             __syncthreads();
             const int32_t nb2 = *sh.nb2;
-            for (int32_t b = tm.rank; b < c.bend[5]; b += tm.size) {
-                run_item<WK, BIG, true>(c, c.bend[5] - 1 - b, sh.smem, sh.best, sh.cand, sh.last);
+            for (int32_t p = 0; (int64_t)p * tm.size < c.bend[5]; p++) {
+                const int32_t item = serpentine_item(p, tm.rank, tm.size, c.bend[5]);
+                if (item < 0) continue;
+                run_item<WK, BIG, true>(c, item, sh.smem, sh.best, sh.cand, sh.last);
                 __syncthreads();
             }
             if (nb2 > 0) {
