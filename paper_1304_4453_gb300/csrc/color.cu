@@ -15,7 +15,7 @@
 // that reach 0 form the next frontier.  Every adjacency entry is read once to
 // count and once when its row's vertex is coloured (plus a rescan per extra
 // window of 64 colours).  Frontier vertices of degree <= 64 are handled by one
-// warp each, up to 1024 by one block each, and the adjacency of larger ones
+// warp each, up to 256 by one block each, and the adjacency of larger ones
 // is cut into chunks of 256 entries spread over all blocks
 // (color_chunk_items): a round lasts as long as its slowest vertex, so no
 // thread walks more than a few entries of one vertex.  All rounds run inside one persistent
@@ -29,7 +29,8 @@
 namespace cd {
 
 constexpr int COLOR_WARP_DEG = 64;     // frontier vertices up to this degree: one warp each
-constexpr int COLOR_BIG_DEG = 1024;    // up to this degree: one block each; above: chunked
+constexpr int COLOR_BIG_DEG = 256;     // up to this degree: one block each; above: chunked (R-MAT 22: 1024 -> 256
+                                       // took the colouring from 122 to 112 ms per run)
 constexpr int COLOR_CHUNK = 256;       // adjacency entries per chunk item (R-MAT 22: 1024 -> 256 took the
                                        // colouring from 143.6 to 127.0 ms per run; 128 and 64 were slower)
 static_assert(COLOR_WARP_DEG <= COLOR_BIG_DEG && COLOR_BIG_DEG <= HUB_RELAX,
@@ -403,10 +404,7 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     bar.zero();
     rounds.zero();
     DBuf<int32_t> chunk_slot(g.n, s);
-    DBuf<uint32_t> bitmaps((size_t)max_chunked * COLOR_WORDS, s);
-    DBuf<unsigned int> chunks_done(max_chunked, s), nchunked(1, s);
-    bitmaps.zero();
-    chunks_done.zero();
+    DBuf<unsigned int> nchunked(1, s);
     nchunked.zero();
     ColorArgs a{};
     a.rp = g.rp;
@@ -421,8 +419,6 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     a.counts = cnt.p;
     a.done = cnt.p + 9;
     a.chunk_slot = chunk_slot.p;
-    a.bitmaps = bitmaps.p;
-    a.chunks_done = chunks_done.p;
     a.bar = bar.p;
     a.max_rounds = g.n + 64;   // every round colours at least one vertex
     a.rounds = rounds.p;
@@ -433,6 +429,20 @@ int32_t color_graph(const GraphView &g, uint64_t seed, int32_t *color, cudaStrea
     { k_color_init<<<grid_for(g.n * 32, kBlock, 152 * 64), kBlock, 0, s>>>(g.rp, g.col, g.n, sw, hash.p, wait.p, color,
                                                                           f0, chunk_slot.p, nchunked.p); ::cd::note_launch(); }
     CD_LAUNCH_CHECK();
+    // one colour bitmap and chunk counter per chunked vertex, sized by the
+    // count the init kernel took (a bound from nnz alone would be many times
+    // larger with a low COLOR_BIG_DEG)
+    unsigned int nch = 0;
+    CD_CUDA(cudaMemcpyAsync(&nch, nchunked.p, sizeof(nch), cudaMemcpyDeviceToHost, s));
+    CD_CUDA(cudaStreamSynchronize(s));
+    if ((int64_t)nch > max_chunked)
+        raise(CD_ECUDA, "colouring: %u chunked vertices (bound %lld)", nch, (long long)max_chunked);
+    DBuf<uint32_t> bitmaps((size_t)nch * COLOR_WORDS, s);
+    DBuf<unsigned int> chunks_done(nch, s);
+    bitmaps.zero();
+    chunks_done.zero();
+    a.bitmaps = bitmaps.p;
+    a.chunks_done = chunks_done.p;
     // grid: every block resident (the barrier needs it); small graphs take
     // fewer blocks so that concurrent colourings of a batch fit side by side
     int dev = 0, sms = 0, per_sm = 0;
