@@ -14,7 +14,7 @@
 // free colour, and decrements wait of its lower-priority neighbours; those
 // that reach 0 form the next frontier.  Every adjacency entry is read once to
 // count and once when its row's vertex is coloured (plus a rescan per extra
-// window of 64 colours).  Frontier vertices of degree <= 64 are handled by one
+// window of 64 colours).  Frontier vertices of degree <= 32 are handled by one
 // warp each, up to 256 by one block each, and the adjacency of larger ones
 // is cut into chunks of 256 entries spread over all blocks
 // (color_chunk_items): a round lasts as long as its slowest vertex, so no
@@ -28,7 +28,8 @@
 
 namespace cd {
 
-constexpr int COLOR_WARP_DEG = 64;     // frontier vertices up to this degree: one warp each
+constexpr int COLOR_WARP_DEG = 32;     // frontier vertices up to this degree: one warp each (R-MAT 22: 64 -> 32
+                                       // took the colouring from 111 to 104 ms per run; 128 was slower)
 constexpr int COLOR_BIG_DEG = 256;     // up to this degree: one block each; above: chunked (R-MAT 22: 1024 -> 256
                                        // took the colouring from 122 to 112 ms per run)
 constexpr int COLOR_CHUNK = 256;       // adjacency entries per chunk item (R-MAT 22: 1024 -> 256 took the
@@ -133,7 +134,7 @@ __device__ __forceinline__ void color_warp_items(const int64_t *__restrict__ rp,
         uint32_t base = 0;
         while (bits == ~0ull) {
             base += 64;
-            bits = window_bits(rp, col, hash, color, v, hv, lane, 32, base, false);   // degree <= 64: no hub
+            bits = window_bits(rp, col, hash, color, v, hv, lane, 32, base, false);   // degree <= 32: no hub
             for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
         }
         if (lane == 0) {
